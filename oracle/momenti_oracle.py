@@ -1,0 +1,538 @@
+"""CPU oracle for the LSH top-k multidimensional motif search (MOMENTI,
+arXiv 2502.14446).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or
+execute this module: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it.  It shares no code with the CUDA
+library; the two meet only through the seeded inputs of
+``paper_2502_14446_gb300.synth``.
+
+Everything is float64 numpy, written to be read against the paper:
+
+* Section 3.1: the z-normalised Euclidean distance (Eq. zned) with the
+  population standard deviation, the d-dimensional distance ``dist_d``
+  (Definition distdims), ``dims_d``, ``dist_d^max`` (Eq. distdmax), trivial
+  matches with exclusion zone ``eps = w/2`` and the top-k motif set.
+* Section 3.2: the discretised random projection hash (Eq. drp), its
+  collision probability (Eq. eucl-collision-probability), concatenation K and
+  repetitions L.
+* Algorithm 1 (MOMENTI) and Algorithm 2 (STOP), in the paper's loop order.
+* Section 6.1: the heuristic for the quantisation width r.
+
+Readings of points the paper leaves open (each is listed with its reason in
+the design notes of the repository):
+
+* sigma is the population standard deviation (so dist lies in [0, 2 sqrt(w)]
+  and dist^2 = 2w(1 - corr), Section 2);
+* a window whose sigma is at most ``FLAT_REL * (1 + |mu|)`` is flat: its
+  z-normalised form is the zero vector;
+* trivial match iff ``|a - b| <= eps`` with ``eps = floor(w / 2)``;
+* the top-k set is built greedily in ascending (dist_d, a, b) order, a pair
+  being accepted iff none of its two indices is within eps of an index of an
+  already accepted pair (the matrix-profile procedure of Section 2);
+* TOP of Algorithm 1 is that greedy selection over every distinct pair
+  verified so far; TOP.max() is its k-th pair;
+* a hash value is floor((a . z + b) / r) of the z-normalised window z,
+  saturated to a signed byte; a composite key packs the K bytes big-endian,
+  concatenation 0 in the most significant byte, byte value h + 128;
+* r is (max - min) / 256 over projections of evenly spaced sample windows
+  onto the K vectors of repetition 0 of every dimension.
+
+Parity status of each function is stated in its docstring; every function
+here is pinned by a test against the paper or the mathematics (closed forms,
+brute force on tiny inputs, Monte Carlo, hand-evaluated tables).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+FLAT_REL = 1e-8          # flat-window threshold, relative to 1 + |mu|
+R_BUCKETS = 256          # Section 6.1: 256 equal-width buckets, one byte per value
+R_SAMPLE_WINDOWS = 4096  # sample windows per dimension for the r heuristic
+
+
+# ---------------------------------------------------------------------------
+# Section 3.1: distances
+# ---------------------------------------------------------------------------
+
+def exclusion_zone(w: int, excl: int | None = None) -> int:
+    """Trivial-match exclusion zone eps (Section 3.1: eps = w/2)."""
+    return int(w // 2) if excl is None or excl < 0 else int(excl)
+
+
+def window_stats(x: np.ndarray, w: int):
+    """Mean and population standard deviation of every length-w window of a
+    one-dimensional series, by the two-pass formula (Eq. zned's mu, sigma).
+    Returns (mu, sigma, flat) arrays of length n - w + 1."""
+    x = np.asarray(x, dtype=np.float64)
+    V = np.lib.stride_tricks.sliding_window_view(x, w)
+    mu = V.mean(axis=1)
+    sigma = np.sqrt(((V - mu[:, None]) ** 2).mean(axis=1))
+    flat = sigma <= FLAT_REL * (1.0 + np.abs(mu))
+    return mu, sigma, flat
+
+
+def znorm_windows(x: np.ndarray, w: int) -> np.ndarray:
+    """All z-normalised windows of a one-dimensional series, shape (M, w);
+    flat windows map to the zero vector."""
+    x = np.asarray(x, dtype=np.float64)
+    V = np.lib.stride_tricks.sliding_window_view(x, w)
+    mu, sigma, flat = window_stats(x, w)
+    s = np.where(flat, 1.0, sigma)
+    Z = (V - mu[:, None]) / s[:, None]
+    Z[flat] = 0.0
+    return Z
+
+
+def zned(u: np.ndarray, v: np.ndarray) -> float:
+    """Eq. (zned): z-normalised Euclidean distance of two equal-length
+    windows, population sigma, flat windows normalised to zero."""
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+
+    def z(x):
+        mu = x.mean()
+        sd = math.sqrt(((x - mu) ** 2).mean())
+        if sd <= FLAT_REL * (1.0 + abs(mu)):
+            return np.zeros_like(x)
+        return (x - mu) / sd
+
+    return float(math.sqrt(((z(u) - z(v)) ** 2).sum()))
+
+
+def per_dim_distances(T: np.ndarray, w: int, a: int, b: int) -> np.ndarray:
+    """dist(T_a^f, T_b^f) for every dimension f (Eq. zned per dimension)."""
+    return np.array([zned(T[f, a:a + w], T[f, b:b + w]) for f in range(T.shape[0])])
+
+
+def select_d(dists: np.ndarray, d: int):
+    """Definition distdims / Eq. distdmax on one pair's per-dimension
+    distances: returns (dist_d, dims_d, dist_d^max).  dist_d is the sum of
+    the d smallest distances (the minimum over all size-d subsets); ties go
+    to the lower dimension index."""
+    order = np.argsort(np.asarray(dists, dtype=np.float64), kind="stable")[:d]
+    dims = tuple(sorted(int(f) for f in order))
+    vals = np.asarray(dists, dtype=np.float64)[list(dims)]
+    return float(vals.sum()), dims, float(vals.max())
+
+
+def dims_mask(dims) -> int:
+    m = 0
+    for f in dims:
+        m |= 1 << int(f)
+    return m
+
+
+# ---------------------------------------------------------------------------
+# top-k under the trivial-match exclusion
+# ---------------------------------------------------------------------------
+
+def greedy_topk(cands, k: int, eps: int):
+    """Top-k motif set of Section 3.1 from candidate pairs.
+
+    ``cands`` is an iterable of (dist_d, a, b, payload) with a < b.  Pairs
+    are taken in ascending (dist_d, a, b) order and a pair is accepted iff
+    b - a > eps and both of its indices are more than eps away from both
+    indices of every accepted pair.  Returns the accepted tuples."""
+    acc = []
+    for c in sorted(cands, key=lambda t: (t[0], t[1], t[2])):
+        _, a, b = c[0], c[1], c[2]
+        if b - a <= eps:
+            continue
+        ok = True
+        for q in acc:
+            for x in (a, b):
+                for y in (q[1], q[2]):
+                    if abs(x - y) <= eps:
+                        ok = False
+        if ok:
+            acc.append(c)
+            if len(acc) == k:
+                break
+    return acc
+
+
+def naive_topk(T: np.ndarray, w: int, d: int, k: int, excl: int | None = None):
+    """Top-k d-dimensional motifs by plain enumeration of the definitions:
+    every pair of windows, Eq. (zned) per dimension, the minimum of the sum
+    over every size-d subset of dimensions (Definition distdims).  Only for
+    tiny inputs.  Returns [(dist_d, a, b, dims, dist_max)]."""
+    T = np.asarray(T, dtype=np.float64)
+    D, n = T.shape
+    M = n - w + 1
+    eps = exclusion_zone(w, excl)
+    subsets = list(itertools.combinations(range(D), d))
+    cands = []
+    for a in range(M):
+        for b in range(a + eps + 1, M):
+            dist = per_dim_distances(T, w, a, b)
+            best = None
+            for F in subsets:
+                s = float(sum(dist[f] for f in F))
+                if best is None or s < best[0]:
+                    best = (s, F)
+            F = best[1]
+            cands.append((best[0], a, b, (tuple(F), float(max(dist[f] for f in F)))))
+    out = greedy_topk(cands, k, eps)
+    return [(c[0], c[1], c[2], c[3][0], c[3][1]) for c in out]
+
+
+def _pair_distances(Z: list, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Per-dimension distances of many pairs from z-normalised windows:
+    sqrt(sum_t (z_a[t] - z_b[t])^2), shape (D, m)."""
+    out = np.empty((len(Z), a.size))
+    for f, Zf in enumerate(Z):
+        diff = Zf[a] - Zf[b]
+        out[f] = np.sqrt((diff * diff).sum(axis=1))
+    return out
+
+
+def _select_d_many(dist: np.ndarray, d: int):
+    """select_d over the columns of a (D, m) distance array."""
+    order = np.argsort(dist, axis=0, kind="stable")[:d]
+    order.sort(axis=0)
+    vals = np.take_along_axis(dist, order, axis=0)
+    masks = np.zeros(dist.shape[1], dtype=np.uint64)
+    for r in range(d):
+        masks |= np.left_shift(np.uint64(1), order[r].astype(np.uint64))
+    return vals.sum(axis=0), masks, vals.max(axis=0), order
+
+
+def exact_topk(T: np.ndarray, w: int, d: int, k: int, excl: int | None = None,
+               tau: float = math.inf, block: int = 512):
+    """Exact top-k d-dimensional motifs over all pairs (the quantity
+    Algorithm 1 returns with probability >= 1 - delta, and what its last
+    line computes when STOP never holds).
+
+    Per dimension, dist^2 = |z_a|^2 + |z_b|^2 - 2 z_a . z_b, the expanded
+    square of Eq. (zned) (the Pearson form of Section 2) with a library
+    matrix product for the dot products, enumerated in blocks of rows.
+    dist_d is the sum of the d smallest per-dimension distances.  Pairs with
+    dist_d > tau are not collected (tau = inf keeps all; a pair can only
+    have dist_d <= tau if at least d of its dimensions are <= tau).
+    Returns [(dist_d, a, b, dims, dist_max)] or None if fewer than k pairs
+    could be selected below tau."""
+    T = np.asarray(T, dtype=np.float64)
+    D, n = T.shape
+    M = n - w + 1
+    eps = exclusion_zone(w, excl)
+    Z = [znorm_windows(T[f], w) for f in range(D)]
+    nrm = [(Zf * Zf).sum(axis=1) for Zf in Z]
+    cand_a, cand_b, cand_dist = [], [], []
+    for a0 in range(0, M, block):
+        a1 = min(M, a0 + block)
+        rows = np.arange(a0, a1)
+        dist = np.empty((D, a1 - a0, M))
+        for f in range(D):
+            G = Z[f][a0:a1] @ Z[f].T
+            sq = nrm[f][a0:a1, None] + nrm[f][None, :] - 2.0 * G
+            dist[f] = np.sqrt(np.maximum(sq, 0.0))
+        valid = (np.arange(M)[None, :] - rows[:, None]) > eps
+        if math.isfinite(tau):
+            valid &= (dist <= tau).sum(axis=0) >= d
+        ia, ib = np.nonzero(valid)
+        if ia.size == 0:
+            continue
+        sel = dist[:, ia, ib]
+        dd = np.sort(sel, axis=0)[:d].sum(axis=0)
+        keep = dd <= tau
+        cand_a.append(ia[keep] + a0)
+        cand_b.append(ib[keep])
+        cand_dist.append(sel[:, keep])
+    if not cand_a:
+        return None
+    A = np.concatenate(cand_a)
+    B = np.concatenate(cand_b)
+    dist = np.concatenate(cand_dist, axis=1)
+    dd, masks, dmax, order = _select_d_many(dist, d)
+    idx = np.lexsort((B, A, dd))
+    # greedy selection of Section 3.1 over the sorted candidates
+    acc = []
+    for t in idx:
+        a, b = int(A[t]), int(B[t])
+        ok = True
+        for q in acc:
+            if (abs(a - q[1]) <= eps or abs(a - q[2]) <= eps
+                    or abs(b - q[1]) <= eps or abs(b - q[2]) <= eps):
+                ok = False
+                break
+        if ok:
+            acc.append((float(dd[t]), a, b, tuple(int(f) for f in order[:, t]), float(dmax[t])))
+            if len(acc) == k:
+                break
+    if len(acc) < k:
+        return None
+    return acc
+
+
+def exact_topk_auto(T, w, d, k, excl=None, tau0: float | None = None, block: int = 512):
+    """exact_topk with tau doubled until k pairs are selected (tau0 = None
+    means no threshold)."""
+    if tau0 is None:
+        return exact_topk(T, w, d, k, excl, math.inf, block)
+    tau = tau0
+    while True:
+        res = exact_topk(T, w, d, k, excl, tau, block)
+        if res is not None and res[-1][0] <= tau:
+            return res
+        tau *= 2.0
+
+
+# ---------------------------------------------------------------------------
+# Section 3.2: the hash family and its collision probability
+# ---------------------------------------------------------------------------
+
+def std_normal_cdf(x: float) -> float:
+    return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+
+def collision_probability(R: float, r: float) -> float:
+    """Eq. (eucl-collision-probability): Pr[h(x) = h(y)] for two vectors at
+    Euclidean distance R under h(x) = floor((a.x + b)/r)."""
+    if R <= 0.0:
+        return 1.0
+    c = r / R
+    return (1.0 - 2.0 * std_normal_cdf(-c)
+            - 2.0 / (math.sqrt(2.0 * math.pi) * c) * (1.0 - math.exp(-c * c / 2.0)))
+
+
+def stop_condition(dist_max: float, i: int, j: int, K: int, L: int, d: int,
+                   delta: float, r: float) -> bool:
+    """Algorithm 2: p = P(dist_d^max)^d; at i = K stop iff (1 - p^i)^j <= delta,
+    otherwise iff (1 - p^i)^j (1 - p^(i+1))^(L-j) <= delta.  i and j are
+    1-based, as in Algorithm 1."""
+    return failure_bound(dist_max, i, j, K, L, d, r) <= delta
+
+
+def failure_bound(dist_max: float, i: int, j: int, K: int, L: int, d: int, r: float) -> float:
+    """The miss-probability bound of Lemma stop (Eq. probnotcolliding)."""
+    p = collision_probability(dist_max, r) ** d
+    if i == K:
+        return (1.0 - p ** i) ** j
+    return (1.0 - p ** i) ** j * (1.0 - p ** (i + 1)) ** (L - j)
+
+
+def projections(T: np.ndarray, w: int, A: np.ndarray, f: int, windows=None) -> np.ndarray:
+    """a . z for z-normalised windows of dimension f and vectors A (..., w).
+    Returns shape (len(windows), prod(A.shape[:-1]))."""
+    Z = znorm_windows(T[f], w)
+    if windows is not None:
+        Z = Z[windows]
+    return Z @ np.asarray(A, dtype=np.float64).reshape(-1, w).T
+
+
+def estimate_r(T: np.ndarray, w: int, A: np.ndarray, samples: int = R_SAMPLE_WINDOWS) -> float:
+    """Section 6.1 heuristic: project sample windows on random Gaussian
+    vectors, split the observed range into 256 equal-width buckets and use
+    the bucket width as r.  The sample is min(M, samples) evenly spaced
+    windows per dimension; the vectors are the K vectors of repetition 0 of
+    each dimension (A has shape (D, L, K, w)); the range is pooled over all
+    dimensions."""
+    T = np.asarray(T, dtype=np.float64)
+    D, n = T.shape
+    M = n - w + 1
+    S = min(M, samples)
+    pos = sample_positions(M, S)
+    lo, hi = math.inf, -math.inf
+    for f in range(D):
+        v = projections(T, w, A[f, 0], f, pos)
+        lo = min(lo, float(v.min()))
+        hi = max(hi, float(v.max()))
+    if not hi > lo:
+        return 1.0
+    return (hi - lo) / R_BUCKETS
+
+
+def sample_positions(M: int, S: int) -> np.ndarray:
+    """Evenly spaced window positions: floor(q * (M - 1) / (S - 1)), q < S."""
+    if S <= 1:
+        return np.zeros(1, dtype=np.int64)
+    q = np.arange(S, dtype=np.int64)
+    return (q * (M - 1)) // (S - 1)
+
+
+def hash_values(T: np.ndarray, w: int, A: np.ndarray, U: np.ndarray, r: float, f: int):
+    """Eq. (drp) for every window of dimension f and every (j, k):
+    t = (a . z + b) / r with b = U r, h = floor(t) saturated to [-128, 127].
+    Returns (h int16 (M, L, K), t float64 (M, L, K))."""
+    L, K, w_ = A.shape[1:]
+    assert w_ == w
+    v = projections(T, w, A[f], f).reshape(-1, L, K)
+    b = U[f].astype(np.float64) * r
+    t = (v + b[None]) / r
+    h = np.clip(np.floor(t), -128, 127).astype(np.int16)
+    return h, t
+
+
+def pack_keys(h: np.ndarray) -> np.ndarray:
+    """Pack K hash bytes into one uint64, big-endian: concatenation 0 in the
+    most significant byte, byte value h + 128 (h saturated to a signed
+    byte).  Lexicographic order of keys is the order of the hash strings
+    (Section 4, index construction).  h has shape (..., K)."""
+    K = h.shape[-1]
+    key = np.zeros(h.shape[:-1], dtype=np.uint64)
+    for kk in range(K):
+        byte = (h[..., kk].astype(np.int64) + 128).astype(np.uint64)
+        key |= np.left_shift(byte, np.uint64(56 - 8 * kk))
+    return key
+
+
+def hash_all(T: np.ndarray, w: int, A: np.ndarray, U: np.ndarray, r: float):
+    """Algorithm 1, initialisation: the composite hash h_{K,j}^f of every
+    window, dimension and repetition.  Returns (keys uint64 (L, M, D),
+    t float64 (D, M, L, K))."""
+    T = np.asarray(T, dtype=np.float64)
+    D = T.shape[0]
+    L, K = A.shape[1], A.shape[2]
+    M = T.shape[1] - w + 1
+    keys = np.empty((L, M, D), dtype=np.uint64)
+    ts = np.empty((D, M, L, K))
+    for f in range(D):
+        h, t = hash_values(T, w, A, U, r, f)
+        keys[:, :, f] = pack_keys(h).T
+        ts[f] = t
+    return keys, ts
+
+
+def prefix(key, i: int):
+    """h_{i,j}: the first i hash values of a composite key."""
+    return np.right_shift(np.asarray(key, dtype=np.uint64), np.uint64(64 - 8 * i))
+
+
+def build_index(keys: np.ndarray):
+    """Section 4, index construction: for every (j, f) the windows in
+    lexicographic order of their hash strings (ties by window index), plus
+    the length of the common prefix (in hash values) of each entry with the
+    previous one.  Returns (order uint32 (L, D, M), lcp uint8 (L, D, M))."""
+    L, M, D = keys.shape
+    order = np.empty((L, D, M), dtype=np.uint32)
+    lcp = np.zeros((L, D, M), dtype=np.uint8)
+    for j in range(L):
+        for f in range(D):
+            o = np.argsort(keys[j, :, f], kind="stable")
+            order[j, f] = o
+            s = keys[j, o, f]
+            for p in range(1, M):
+                x = int(s[p - 1]) ^ int(s[p])
+                lcp[j, f, p] = 8 if x == 0 else (64 - x.bit_length()) // 8
+    return order, lcp
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 and Algorithm 2
+# ---------------------------------------------------------------------------
+
+def colliding_pairs(keys_jf: np.ndarray, i: int) -> np.ndarray:
+    """Algorithm 1, line 8: all pairs (a < b) whose hash strings share the
+    prefix of length i, for one (j, f).  Returns codes a * M + b (int64)."""
+    M = keys_jf.size
+    pre = prefix(keys_jf, i)
+    uniq, inv, cnt = np.unique(pre, return_inverse=True, return_counts=True)
+    out = []
+    for g in np.nonzero(cnt >= 2)[0]:
+        members = np.sort(np.nonzero(inv == g)[0]).astype(np.int64)
+        ia, ib = np.triu_indices(members.size, 1)
+        out.append(members[ia] * M + members[ib])
+    if not out:
+        return np.zeros(0, dtype=np.int64)
+    return np.concatenate(out)
+
+
+class _Pool:
+    """Every distinct verified pair, with the greedy TOP selection.
+
+    The greedy selection only changes when a new pair is closer than the
+    current k-th selected pair (pairs further away are visited after the
+    k-th acceptance), so it is recomputed only then."""
+
+    def __init__(self, k: int, eps: int):
+        self.k, self.eps = k, eps
+        self.pairs = {}
+        self._top = []
+
+    def add_many(self, a, b, dd, order, dmax):
+        kth = self._top[-1][0] if len(self._top) == self.k else math.inf
+        dirty = False
+        for t in range(len(a)):
+            key = (int(a[t]), int(b[t]))
+            if key in self.pairs:
+                continue
+            self.pairs[key] = (float(dd[t]), tuple(int(f) for f in order[:, t]), float(dmax[t]))
+            if float(dd[t]) <= kth:
+                dirty = True
+        if dirty:
+            cands = [(v[0], a_, b_, (v[1], v[2])) for (a_, b_), v in self.pairs.items()]
+            sel = greedy_topk(cands, self.k, self.eps)
+            self._top = [(c[0], c[1], c[2], c[3][0], c[3][1]) for c in sel]
+
+    def top(self):
+        return list(self._top)
+
+
+def momenti_traverse(keys: np.ndarray, pair_distances, d: int, k: int, delta: float,
+                     r: float, eps: int, K: int | None = None):
+    """Algorithm 1, lines 3-19, over given composite hash keys
+    (uint64, shape (L, M, D)): for i = K..1, for j = 1..L, W(a, b) counts the
+    dimensions in which a and b share the length-i prefix; every pair with
+    W >= d that is not a trivial match is verified with
+    ``pair_distances(a, b) -> (D, m)`` and offered to TOP; the loop returns
+    when |TOP| = k and STOP(TOP.max(), i, j, delta) (Algorithm 2).
+
+    Returns (top, (i, j) or None, n_dist, pool_size)."""
+    L, M, D = keys.shape
+    K = 8 if K is None else K
+    pool = _Pool(k, eps)
+    n_dist = 0
+    for i in range(K, 0, -1):
+        for j in range(1, L + 1):
+            codes = [colliding_pairs(keys[j - 1, :, f], i) for f in range(D)]
+            allc = np.concatenate(codes) if codes else np.zeros(0, np.int64)
+            uniq, W = np.unique(allc, return_counts=True)
+            sel = uniq[W >= d]
+            a = sel // M
+            b = sel % M
+            nt = (b - a) > eps
+            a, b = a[nt], b[nt]
+            if a.size:
+                dist = pair_distances(a, b)
+                n_dist += int(a.size)
+                dd, masks, dmax, order = _select_d_many(dist, d)
+                pool.add_many(a, b, dd, order, dmax)
+            top = pool.top()
+            if len(top) == k and stop_condition(top[-1][4], i, j, K, L, d, delta, r):
+                return top, (i, j), n_dist, len(pool.pairs)
+    return None, None, n_dist, len(pool.pairs)
+
+
+def momenti(T: np.ndarray, w: int, d: int, k: int, delta: float, A: np.ndarray,
+            U: np.ndarray, r: float, excl: int | None = None, all_k: bool = False,
+            fallback_tau: float | None = None):
+    """Algorithm 1 (MOMENTI) with Algorithm 2 (STOP), in the paper's order:
+    hash every window, dimension and repetition (line 2), traverse the
+    prefixes (lines 3-19, ``momenti_traverse``) and, if STOP never holds,
+    return the exact top-k over all pairs (line 20).
+
+    ``all_k`` uses delta / k (Lemma topkdip).  A has shape (D, L, K, w),
+    U (D, L, K).  Returns a dict with the motifs [(dist_d, a, b, dims,
+    dist_max)], the stopping (i, j) (None when the last line ran), the
+    number of distance computations (verified pairs, repeats included, as
+    the paper counts them), the failure bound at return and the number of
+    distinct verified pairs."""
+    T = np.asarray(T, dtype=np.float64)
+    D, n = T.shape
+    L, K = A.shape[1], A.shape[2]
+    eps = exclusion_zone(w, excl)
+    dlt = delta / k if all_k else delta
+    keys, _ = hash_all(T, w, A, U, r)
+    Z = [znorm_windows(T[f], w) for f in range(D)]
+    top, stop, n_dist, pool = momenti_traverse(
+        keys, lambda a, b: _pair_distances(Z, a, b), d, k, dlt, r, eps, K)
+    if stop is not None:
+        i, j = stop
+        return {"motifs": top, "stop": stop, "n_dist": n_dist,
+                "fail_bound": failure_bound(top[-1][4], i, j, K, L, d, r), "pool": pool}
+    return {"motifs": exact_topk_auto(T, w, d, k, excl, fallback_tau), "stop": None,
+            "n_dist": n_dist, "fail_bound": 0.0, "pool": pool}
