@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the motif-search hot path on one or more GB300s.
+
+One step = momenti_hash_all + momenti_topk on one synthetic series of the
+float32 plain-method workload: D=8, n=100,000, w=300, d=3, k=10,
+delta=0.05, 8 GB memory limit, paper defaults K=8, L=200, r automatic
+(random walk + 3 sinusoids + N(0, 0.1) noise, five motifs planted in 3
+dims each).  The series is resident in HBM when a timed step starts; the
+L2 is flushed (a 512 MB write) before every timed step, outside the timed
+interval.  Each rank of a multi-GPU run searches its own series (weak
+scaling, no collective on the data path).
+
+value  = subsequence hashes (windows x dims x repetitions) pushed through
+         the whole step per second, summed over ranks;
+e2e    = the same through host buffers (pinned series copied in, motifs
+         copied out, both inside the timed interval);
+roofline: the dominant kernel timed live with CUDA events on its stream;
+cpu_baseline: the CPU oracle (oracle/) on a bounded sample.
+
+--impl reference times the CPU oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# dominant kernels and their algorithmic work per launch
+DOMINANT = ("proj_hash_tc", "collide", "sort_scatter", "allpairs", "proj_hash_fp32", "verify_new")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="momenti", choices=["momenti", "reference"])
+    ap.add_argument("--precision", default="f16x2", choices=["f16x2", "fp32"])
+    ap.add_argument("--kernel", default="auto", help="kernel for the roofline object")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
+    return ap.parse_args()
+
+
+def workload(rank: int):
+    from paper_2502_14446_gb300 import synth
+    return synth.plain_fp32(seed=rank)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "tflops": d["bf16_tflops"],
+                "tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "tflops": 1900.0, "tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def params_for(mom, wl, precision):
+    return mom.default_params(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, mem_limit=wl.mem_limit,
+                              K=8, L=200, precision=precision)
+
+
+def algorithmic(kernel, info, st, wl):
+    """(bound, work per launch unit, unit label) of a kernel at this workload."""
+    M, D, L, K, w = info["M"], info["D"], info["L"], info["K"], wl.w
+    if kernel == "proj_hash_tc":
+        return "tensor", 2.0 * M * D * L * K * w, "TFLOP/s"     # one launch = all repetitions
+    if kernel == "proj_hash_fp32":
+        return "alu", 2.0 * M * D * L * K * w, "TFLOP/s"
+    if kernel == "sort_scatter":
+        # one launch = one 8-bit pass over a batch: read key+index, write key+index
+        return "hbm", None, "GB/s"
+    return None, None, None
+
+
+def run_momenti(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2502_14446_gb300 import build_ext
+    if rank == 0:
+        build_ext.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2502_14446_gb300 import momenti as mom
+
+    wl = workload(rank)
+    prec = mom.PREC_F16X2 if args.precision == "f16x2" else mom.PREC_FP32
+    series = torch.from_numpy(wl.series).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = mom.Momenti(params_for(mom, wl, prec))
+
+    def step():
+        h.hash_all(series, stream=stream.cuda_stream)
+        return h.topk()
+
+    for _ in range(args.warmup):
+        motifs, st = step()
+    torch.cuda.synchronize()
+    info = h.info()
+
+    # dominant kernel: the one with the largest device time in one step
+    kernel = args.kernel
+    if kernel == "auto":
+        best = (None, -1.0)
+        for kname in DOMINANT:
+            mom.time_kernel(kname)
+            step()
+            ms, n = mom.kernel_time()
+            if ms > best[1]:
+                best = (kname, ms)
+        kernel = best[0]
+    mom.time_kernel(kernel)
+
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = mom.launch_count()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        motifs, st = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = mom.launch_count() - launches0
+    k_ms, k_n = mom.kernel_time()
+    mom.time_kernel(None)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    units_step = info["M"] * info["D"] * info["L"]
+    value = world * units_step * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through host buffers ----
+    pinned = torch.from_numpy(wl.series).pin_memory().numpy()
+    e2e_times = []
+    for q in range(max(2, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.hash_all(pinned)
+        m2, _ = h.topk()
+        torch.cuda.synchronize()
+        if q >= 1:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+    h_bytes = wl.series.nbytes
+    d_bytes = wl.k * 48
+
+    out = None
+    if rank == 0:
+        pk = peaks()
+        roof = None
+        if k_n:
+            per_launch_s = (k_ms / k_n) / 1e3
+            bound, work, unit = algorithmic(kernel, info, st, wl)
+            if kernel == "proj_hash_tc":
+                achieved = work / per_launch_s / 1e12
+                peak = pk["tflops_sustained"]
+                roof = {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak_src": pk["src"] + " sustained bf16 (fp16 same rate)",
+                        "launches": k_n, "ms_per_launch": k_ms / k_n}
+            elif kernel == "proj_hash_fp32":
+                achieved = work / per_launch_s / 1e12
+                peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+                roof = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak_src": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                        "launches": k_n, "ms_per_launch": k_ms / k_n}
+            else:
+                roof = {"kernel": kernel, "bound": None, "achieved": None, "peak": None,
+                        "unit": None, "frac": None, "traffic": None, "launches": k_n,
+                        "ms_per_launch": k_ms / k_n}
+        plain = None
+        if not args.no_fp32 and prec != mom.PREC_FP32:
+            h32 = mom.Momenti(params_for(mom, wl, mom.PREC_FP32))
+            h32.hash_all(series, stream=stream.cuda_stream)
+            h32.topk()
+            ts = []
+            for _ in range(2):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h32.hash_all(series, stream=stream.cuda_stream)
+                _, st32 = h32.topk()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            plain = {"ms_per_step": statistics.mean(ts),
+                     "value": units_step / (statistics.mean(ts) / 1e3),
+                     "t_hash_ms": st32["t_hash_ms"]}
+            h32.close()
+        base = None if args.no_baseline else cpu_baseline(wl)
+        out = {
+            "metric": "time-to-top-k motifs (s) and subsequences hashed/s, BF16/batched vs plain FP32",
+            "value": value, "unit": "subsequences/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "time_to_topk_s": total_ms / args.steps / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x2+f32" if prec == mom.PREC_F16X2 else "f32",
+            "data": "synthetic",
+            "config": {"workload": "plain_fp32: D=8 n=100000 w=300 d=3 k=10 delta=0.05 "
+                                   "float32, 8 GB limit, K=8 L=200, r auto",
+                       "precision": args.precision, "L_used": info["L"], "K": info["K"],
+                       "r": info["r"], "windows": info["M"], "l2": "flushed (512 MB write) before each step",
+                       "parallelism": f"replicas x{world}"},
+            "step": {"t_hash_ms": st["t_hash_ms"], "t_sort_ms": st["t_sort_ms"],
+                     "t_traverse_ms": st["t_traverse_ms"], "t_fallback_ms": st["t_fallback_ms"],
+                     "stop": [st["stop_i"], st["stop_j"]], "fallback": st["fallback"],
+                     "n_candidates": st["n_candidates"], "n_verified": st["n_verified"],
+                     "n_rehashed": st["n_rehashed"], "precision_used": st["precision_used"],
+                     "max_rel_err_fp32": st["max_rel_err_fp32"],
+                     "hashed_per_s_hash_all": units_step / (st["t_hash_ms"] / 1e3)},
+            "motifs": [[m["a"], m["b"], round(m["dist_d"], 6), list(m["dims"])] for m in motifs],
+            "plain_fp32": plain,
+            "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
+                    "time_to_topk_s": e2e_s, "h2d_bytes_per_step": h_bytes,
+                    "d2h_bytes_per_step": d_bytes},
+            "roofline": roof,
+            "cpu_baseline": base,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    h.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(wl, budget_s: float = 20.0):
+    """The CPU oracle (Algorithm 1 rendering, float64 numpy) on a bounded
+    prefix of the same workload: n = 2,000 points of the same series, all 8
+    dims, w, d, k, delta as the workload, K=8, L=200 hash functions drawn by
+    the same generator."""
+    from oracle import momenti_oracle as O
+    from paper_2502_14446_gb300 import synth
+    n = 2000
+    T = wl.series[:, :n].astype("float64")
+    A, U = synth.hash_draws(wl.D, 200, 8, wl.w, 0)
+    t0 = time.perf_counter()
+    r = O.estimate_r(T, wl.w, A)
+    res = O.momenti(T, wl.w, wl.d, wl.k, wl.delta, A, U, r)
+    dt = time.perf_counter() - t0
+    M = n - wl.w + 1
+    units = M * wl.D * 200
+    return {"value": units / dt, "unit": "subsequences/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"first {n} points of the series (M={M} windows), all {wl.D} dims, "
+                      f"L=200, K=8: Algorithm 1 rendering in float64 numpy "
+                      f"(stop={res['stop']})"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(0)
+    times = []
+    base = None
+    for q in range(args.warmup + args.steps):
+        b = cpu_baseline(wl)
+        if q >= args.warmup:
+            times.append(b["seconds"])
+            base = b
+    mean = statistics.mean(times)
+    value = base["value"]
+    out = {"metric": "time-to-top-k motifs (s) and subsequences hashed/s, BF16/batched vs plain FP32",
+           "value": value, "unit": "subsequences/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "plain_fp32 prefix sample (see cpu_baseline.sample)"},
+           "cpu_baseline": {"value": value, "unit": "subsequences/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": base["sample"]},
+           "e2e": {"value": value, "unit": "subsequences/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_momenti(args)
+
+
+if __name__ == "__main__":
+    main()

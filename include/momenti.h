@@ -1,0 +1,234 @@
+/*
+ * momenti.h - C ABI of the GB300 (sm_103a) LSH top-k multidimensional motif
+ * search of MOMENTI (Ceccarello, Monaco, Silvestri; arXiv 2502.14446).
+ *
+ * Problem (Section 3.1, Definition of the top-k multidimensional motifs):
+ * given a D-dimensional series T of length n, a window length w, a motif
+ * dimensionality d and a count k, return the k pairs of length-w windows
+ * (a, b) with the smallest d-dimensional distance dist_d (Definition
+ * distdims: the sum of the d smallest per-dimension z-normalised Euclidean
+ * distances, Eq. zned), no two returned windows being trivial matches
+ * (|a - b| <= eps, eps = w/2).  The search is Algorithm 1 (MOMENTI) with the
+ * stopping rule of Algorithm 2: each returned motif is the exact one with
+ * probability at least 1 - delta (Lemma topk), or 1 - delta over all k in the
+ * ALL_K mode (Lemma topkdip).
+ *
+ * Conventions for every entry point:
+ *   - return value: MOMENTI_OK (0) or a negative MOMENTI_ERR_* code; no C++
+ *     exception crosses the ABI; momenti_last_error() gives a message;
+ *   - pointers are host pointers unless a parameter says otherwise; the
+ *     caller owns every buffer it passes and the handle owns everything it
+ *     allocates (released by momenti_destroy);
+ *   - a handle is single-threaded: calls on one handle must not overlap;
+ *   - all GPU work of a handle runs on the stream given to momenti_hash_all
+ *     (the legacy default stream when NULL); calls return after that stream
+ *     has finished the call's work, unless stated otherwise.
+ */
+#ifndef MOMENTI_H
+#define MOMENTI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MOMENTI_OK            0
+#define MOMENTI_ERR_ARG      (-1)  /* invalid argument (see each call)          */
+#define MOMENTI_ERR_MEMORY   (-2)  /* the memory limit cannot hold one repetition */
+#define MOMENTI_ERR_CUDA     (-3)  /* a CUDA runtime call failed               */
+#define MOMENTI_ERR_TIMEOUT  (-4)  /* a bounded device wait ran out            */
+#define MOMENTI_ERR_OVERFLOW (-5)  /* an internal buffer overflowed            */
+#define MOMENTI_ERR_STATE    (-6)  /* call out of order (e.g. topk before hash_all) */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define MOMENTI_F32 0              /* series element type float  */
+#define MOMENTI_F64 1              /* series element type double */
+
+#define MOMENTI_PREC_FP32  0       /* projections as plain FP32 FMAs on CUDA cores          */
+#define MOMENTI_PREC_F16X2 1       /* projections on tcgen05 tensor cores, FP16 hi+lo split
+                                      of the z-normalised windows, FP32 accumulation       */
+
+#define MOMENTI_DELTA_PER_MOTIF 0  /* Algorithm 2 with delta (Lemma topk)      */
+#define MOMENTI_DELTA_ALL_K     1  /* Algorithm 2 with delta / k (Lemma topkdip) */
+
+#define MOMENTI_MAX_D 64           /* dimensions per series (dims travel as a 64-bit mask) */
+#define MOMENTI_MAX_K 8            /* concatenations: one byte each in a 64-bit key */
+
+/* ---- parameters (Algorithm 1's inputs, Section 3.2 and Section 6.1) --- */
+typedef struct momenti_params {
+  int32_t  w;             /* window length, 2 <= w <= n                          */
+  int32_t  d;             /* motif dimensionality, 1 <= d <= D                   */
+  int32_t  k;             /* number of motifs, >= 1                              */
+  double   delta;         /* failure probability, 0 < delta < 1                  */
+  uint64_t mem_limit;     /* device bytes the handle may hold; 0 = 80% of free   */
+  int32_t  K;             /* concatenations, 1..8 (paper default 8)              */
+  int32_t  L;             /* maximum repetitions (paper default 200); 0 = as many
+                             as mem_limit allows, at most 4096. The memory planner
+                             may use fewer (momenti_stats.L).                      */
+  double   r;             /* quantisation width of Eq. drp; <= 0 selects the
+                             heuristic of Section 6.1                              */
+  int32_t  excl;          /* exclusion zone eps; < 0 selects w / 2 (Section 3.1) */
+  uint64_t seed;          /* seed of the hash functions drawn on the device      */
+  int32_t  precision;     /* MOMENTI_PREC_*                                      */
+  int32_t  delta_mode;    /* MOMENTI_DELTA_*                                     */
+} momenti_params;
+
+/* One motif: windows a < b (0-based), dist_d (Definition distdims),
+ * dist_d^max (Eq. distdmax), the dims_d set as a bit mask (bit f = dim f),
+ * and fail_bound = the miss-probability bound of Lemma stop at return
+ * (0 when the exact all-pairs path of Algorithm 1's last line produced it). */
+typedef struct momenti_motif {
+  int64_t  a, b;
+  double   dist_d;
+  double   dist_max;
+  double   fail_bound;
+  uint64_t dims_mask;
+} momenti_motif;
+
+/* Counters of one momenti_topk call. */
+typedef struct momenti_stats {
+  int32_t  stop_i, stop_j;   /* (i, j) at which STOP held, 1-based; 0, 0 = exact path */
+  int32_t  K, L;             /* concatenations and repetitions used                   */
+  double   r;                /* quantisation width used                               */
+  int64_t  n_windows;        /* M = n - w + 1                                         */
+  int64_t  n_candidates;     /* (pair, repetition) events with W >= d, first dim only */
+  int64_t  n_verified;       /* distinct pairs whose distances were computed          */
+  int64_t  n_pool;           /* distinct verified pairs held by TOP's pool            */
+  int32_t  fallback;         /* 1 if Algorithm 1's last line (all pairs) ran          */
+  int32_t  n_chunks;         /* device round trips of the traversal                   */
+  double   t_hash_ms;        /* momenti_hash_all: stats, r, projections, hashes       */
+  double   t_sort_ms;        /*   of which the index sort                             */
+  double   t_traverse_ms;    /* momenti_topk: collision counting, verification, STOP  */
+  double   t_fallback_ms;    /* momenti_topk: exact all-pairs path                     */
+  double   max_rel_err_fp32; /* max |FP32 - FP64| / FP64 of dist_d over the result    */
+  uint64_t device_bytes;     /* device bytes held by the handle                        */
+  int32_t  precision_used;   /* MOMENTI_PREC_* of the projections that ran            */
+  int32_t  reserved;
+  uint64_t n_rehashed;       /* tensor-core values re-hashed in FP32 (near a boundary) */
+} momenti_stats;
+
+typedef struct momenti_handle momenti_handle;
+
+/* Fills *p with the paper's defaults (Section 7, default parameter values:
+ * K = 8, L = 200, delta = 0.01, r automatic) and w = 100, d = 1, k = 1,
+ * eps = w/2, FP16x2 tensor-core projections.  Returns MOMENTI_ERR_ARG if p
+ * is NULL. */
+int momenti_default_params(momenti_params* p);
+
+/* Validates *p and creates a handle (no device memory yet).
+ * MOMENTI_ERR_ARG: out or p NULL, w < 2, d < 1, k < 1, delta not in (0,1),
+ * K not in 1..8, L < 0, unknown precision or delta_mode. */
+int momenti_create(momenti_handle** out, const momenti_params* p);
+
+/* Releases the handle and every device buffer it holds.  NULL is a no-op. */
+void momenti_destroy(momenti_handle* h);
+
+/* Message of the last failing call on h (static text when h is NULL). */
+const char* momenti_last_error(const momenti_handle* h);
+
+/* Optional: the random numbers of the D * L * K hash functions of Eq. drp,
+ * h(x) = floor((a . x + b) / r), instead of drawing them on the device.
+ * a: D*L*K*w floats, layout [f][j][k][t], N(0,1) draws; they are used
+ * rounded to IEEE half precision (pass half-representable values to make
+ * the rounding exact).  u: D*L*K floats in [0, 1), layout [f][j][k];
+ * b = u * r.  L here is the number of repetitions supplied; the memory
+ * planner uses the first L_used <= L of them.  Copied by the call.
+ * MOMENTI_ERR_ARG on NULL pointers, w / K mismatch with the parameters,
+ * D not in 1..64, or u outside [0, 1). */
+int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
+                            const float* a, const float* u);
+
+/* Algorithm 1, line 2 and the index of Section 4 ("Index construction"):
+ * rolling mean / std of every window (population sigma, float64 running
+ * sums), r by the heuristic of Section 6.1 unless fixed, the composite hash
+ * h_{K,j}^f of every window, dimension and repetition, and for every (j, f)
+ * the windows sorted lexicographically by hash string.
+ *   series : D rows of n elements, row f at series + f * ld (elements), of
+ *            type dtype (MOMENTI_F32 / MOMENTI_F64); a device pointer if
+ *            on_device != 0 (borrowed only during the call), else host.
+ *   stream : cudaStream_t for all work of this handle, or NULL.
+ * The index stays on the device, owned by the handle; a later call
+ * replaces it.  MOMENTI_ERR_ARG: NULL series, D not in 1..64 or not the D
+ * of set_hash_params, d > D, n < w, ld < n, n - w + 1 >= 2^31.
+ * MOMENTI_ERR_MEMORY: the limit cannot hold the series, its statistics and
+ * one repetition. */
+int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n,
+                     int32_t D, int64_t ld, int32_t on_device, void* stream);
+
+/* Algorithm 1, lines 3-20 with Algorithm 2: traverses prefixes i = K..1 and
+ * repetitions j = 1..L, counts per pair the dimensions sharing the length-i
+ * prefix (W), verifies pairs with W >= d, keeps TOP and stops when STOP
+ * holds; otherwise returns the exact top-k over all pairs.  Distances of
+ * the result are re-verified in float64.
+ *   out   : room for k motifs, sorted by (dist_d, a, b);
+ *   n_out : number written (k unless fewer than k non-trivial pairs exist);
+ *   stats : optional counters (may be NULL).
+ * MOMENTI_ERR_STATE before momenti_hash_all. */
+int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats);
+
+/* Algorithm 1, line 20 alone: the exact top-k over all pairs (the quantity
+ * of Definition top-k), on the GPU, float64 re-verified.  Same outputs and
+ * errors as momenti_topk. */
+int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out);
+
+/* Eq. zned per dimension and Definition distdims for m given pairs
+ * (pairs[2q], pairs[2q+1]), 0 <= a, b < M.  Outputs (host, caller-owned,
+ * any may be NULL): per_dim m*D distances [q][f], dist_d m values, dims_mask
+ * m masks of the d best dims.  fp64 != 0 computes in float64, else in the
+ * float32 form the traversal uses.  MOMENTI_ERR_ARG on an index outside
+ * [0, M); MOMENTI_ERR_STATE before momenti_hash_all. */
+int momenti_verify(momenti_handle* h, const int64_t* pairs, int64_t m, double* per_dim,
+                   double* dist_d, uint64_t* dims_mask, int32_t fp64);
+
+/* ---- inspection of the index (for tests and tools) ------------------- */
+
+/* Sizes of the current index: M windows, D dims, L_used repetitions, K, r. */
+int momenti_get_info(const momenti_handle* h, int64_t* M, int32_t* D, int32_t* L, int32_t* K,
+                     double* r);
+
+/* Window statistics, host arrays of D*M doubles, layout [f][a]. */
+int momenti_get_window_stats(momenti_handle* h, double* mu, double* sigma);
+
+/* Composite keys of repetition j (0-based): M*D uint64 [a][f]; byte 7-k
+ * (k = 0 most significant) holds h_k + 128, bytes beyond K are zero. */
+int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys);
+
+/* Sorted index of (j, f): order[p] = window at rank p (ties by window
+ * index), lcp[p] = hash values shared with rank p - 1 (lcp[0] = 0). */
+int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, uint8_t* lcp);
+
+/* Algorithm 1, lines 6-14 for one (i, j), 1-based i and 0-based j: the
+ * non-trivial pairs (a < b) with W >= d at prefix length i in repetition j,
+ * each once, without the cross-level and cross-repetition de-duplication
+ * of the traversal.  pairs: room for 2*cap int64; *count = total found
+ * (may exceed cap; only cap are written). */
+int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int64_t cap,
+                    int64_t* count);
+
+/* ---- launch accounting (for benchmarks) ------------------------------ */
+
+/* Number of CUDA kernels this library has launched in the process.
+ * (The paper has no counterpart: this is instrumentation.) */
+uint64_t momenti_launch_count(void);
+
+/* Starts timing every launch of the kernel called name with CUDA events on
+ * the launching stream, and clears the accumulated time; NULL stops timing.
+ * Kernel names: split_f32, split_f64, window_stats, r_sample, draw,
+ * layout_hash, layout_boff, proj_hash_fp32, proj_hash_tc, rehash,
+ * sort_hist, sort_scan, sort_scatter, sort_finish, chunk_agg, chunk_scan,
+ * scan_local, scan_top, scan_add, collide, hs_clear, collect_tag,
+ * verify_new, verify_pairs, allpairs. */
+int momenti_time_kernel(const char* name);
+
+/* Device time in milliseconds accumulated by the timed kernel since the
+ * last momenti_time_kernel call, and the number of timed launches.  Waits
+ * for the recorded events. */
+int momenti_kernel_time(double* total_ms, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOMENTI_H */

@@ -1,0 +1,152 @@
+// Internal declarations shared by the kernel translation units and the
+// host orchestration of the motif search.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+namespace momenti {
+
+// Window count above which a 32-bit window index would overflow.
+constexpr int64_t kMaxWindows = (int64_t(1) << 31) - 1;
+constexpr int kKeyBytes = 8;          // one byte per concatenated hash value
+constexpr int kRepStride = 8;         // projections per repetition in the layouts
+constexpr double kFlatRel = 1e-8;     // flat window: sigma <= kFlatRel (1 + |mu|)
+
+// Device-resident series, window statistics, hash functions and index.
+struct Index {
+  int64_t n = 0, M = 0;
+  int D = 0, w = 0, K = 0, L = 0, Wp = 0, excl = 0;
+  double r = 0.0;
+  float inv_r = 0.f;
+  bool has_lo = false;
+  float* xs_hi = nullptr;     // [D][n]  series, float32 part
+  float* xs_lo = nullptr;     // [D][n]  float64 input only: x - double(hi), as float
+  double* mu = nullptr;       // [D][M]
+  double* sig = nullptr;      // [D][M]
+  float* mu_hi = nullptr;     // [D][M]  float(mu)
+  float* mu_lo = nullptr;     // [D][M]  float(mu - double(mu_hi))
+  float* inv_sig = nullptr;   // [D][M]  1/sigma, 0 for flat windows
+  __half* a16 = nullptr;      // [D][N][Wp]   N = L * 8, K-major rows for tensor cores
+  float* a32 = nullptr;       // [D][Wp][N]   same values, float32, for CUDA cores
+  float* boff = nullptr;      // [D][N]       b = u * r
+  uint64_t* keys = nullptr;   // [L][M][D]
+  uint32_t* order = nullptr;  // [L][D][M]
+  uint8_t* lcp = nullptr;     // [L][D][M]
+};
+
+// One verified pair as it travels to the host.
+struct PairRec {
+  uint32_t a, b;      // a < b
+  int32_t j;          // 0-based repetition of first collision in the chunk
+  float dist_d;       // sum of the d smallest per-dimension distances
+  float dist_max;     // largest distance among the d selected dimensions
+  uint32_t pad;
+  uint64_t dims;      // mask of the d selected dimensions
+};
+static_assert(sizeof(PairRec) == 32, "PairRec layout");
+
+// ---- profile.cu ---------------------------------------------------------
+// Every launch is bracketed by prof_begin / prof_end (launch counter and,
+// for the selected kernel, CUDA events on the launching stream).
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(const char* name, cudaStream_t s);
+#define MOMENTI_LAUNCH(name, stream, ...)      \
+  do {                                         \
+    ::momenti::prof_begin(name, stream);       \
+    __VA_ARGS__;                               \
+    ::momenti::prof_end(name, stream);         \
+  } while (0)
+
+// ---- k_stats.cu ---------------------------------------------------------
+cudaError_t launch_split_series(const void* src, int dtype, int64_t n, int D, int64_t ld,
+                                float* hi, float* lo, cudaStream_t s);
+cudaError_t launch_window_stats(const Index& ix, cudaStream_t s);
+// min/max of the projections of S evenly spaced windows per dim onto the K
+// vectors of repetition 0; out2 = {min, max} (device, 2 floats).
+cudaError_t launch_r_sample(const Index& ix, int S, float* out2, cudaStream_t s);
+// Hash functions drawn on the device (Philox4x32-10 + Box-Muller):
+// a ~ N(0,1) rounded to half, u ~ U[0,1).  a_out [D][L][K][w], u_out [D][L][K].
+cudaError_t launch_draw_hash(uint64_t seed, int D, int L, int K, int w, float* a_out,
+                             float* u_out, cudaStream_t s);
+// Lay the draws out for the projection kernels: a16/a32 padded to 8 per
+// repetition and Wp columns (a rounded to half); boff = u * r (needs ix.r).
+cudaError_t launch_layout_hash(const Index& ix, const float* a_src, int L_src, cudaStream_t s);
+cudaError_t launch_layout_boff(const Index& ix, const float* u_src, int L_src, cudaStream_t s);
+
+// ---- k_hash_fp32.cu -----------------------------------------------------
+cudaError_t launch_proj_hash_fp32(const Index& ix, int j0, int j1, cudaStream_t s);
+
+// ---- k_hash_tc.cu -------------------------------------------------------
+// tcgen05 projection + hash for repetitions [j0, j1).  Values within 2^-11
+// of a bucket boundary are appended to flags as (f << 56 | n << 32 | a);
+// launch_rehash_fp32 recomputes them in the canonical FP32 form.  *err is
+// raised if a bounded wait ran out.
+bool tc_supported();
+size_t proj_hash_tc_smem(int Wp, bool lo);
+cudaError_t launch_proj_hash_tc(const Index& ix, int j0, int j1, uint64_t* flags,
+                                uint32_t flag_cap, uint32_t* flag_count, int* err, cudaStream_t s);
+cudaError_t launch_rehash_fp32(const Index& ix, const uint64_t* flags, const uint32_t* flag_count,
+                               uint32_t flag_cap, cudaStream_t s);
+
+// ---- k_sort.cu ----------------------------------------------------------
+struct SortScratch {
+  uint64_t* k0 = nullptr; uint64_t* k1 = nullptr;
+  uint32_t* v0 = nullptr; uint32_t* v1 = nullptr;
+  uint32_t* hist = nullptr;    // [segs][256][tiles]
+  int64_t cap_entries = 0;     // segs * M capacity of k0/k1/v0/v1
+  int64_t hist_entries = 0;
+};
+int64_t sort_hist_entries(int64_t M, int segs);
+// Sort repetitions [j0, j1): all D segments of each, writing order/lcp.
+cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch& sc,
+                             cudaStream_t s);
+
+// ---- k_collide.cu -------------------------------------------------------
+struct HashSet {
+  uint64_t* keys = nullptr;   // EMPTY = ~0ull
+  uint32_t* tag = nullptr;    // smallest repetition of first collision
+  uint64_t cap = 0;           // power of two
+};
+struct CollideScratch {
+  int32_t* cagg = nullptr;     // [segs][M/32+1] last bucket start in chunk, or -1
+  int32_t* cbs = nullptr;      // [segs][M/32+1] bucket start of the chunk's first position
+  uint64_t* ntile = nullptr;   // [segs*chunks + 1] tiles per chunk, then exclusive scan
+  uint64_t* scan_tmp = nullptr;   // [segs*chunks / 1024 + 1]
+  uint64_t* new_slots = nullptr;  // hash-set slots of new pairs
+  unsigned long long* counters = nullptr;  // [0] new (or plain) pairs, [1] candidates, [2] flags
+  uint64_t new_cap = 0;
+  int64_t seg_cap = 0;            // segments the arrays can hold
+  int64_t chunk_cap = 0;          // chunks per segment
+};
+// Collision counting at prefix length i for repetitions [j0, j1): inserts
+// every non-trivial pair with W >= d (first colliding dim, not already
+// colliding at length i+1) into the set, appending new ones to new_slots.
+// mode_plain != 0: no level / set de-duplication; pairs go to out_pairs.
+cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const HashSet& hs,
+                           const CollideScratch& cs, int mode_plain, uint64_t* out_pairs,
+                           uint64_t out_cap, cudaStream_t s);
+cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s);
+// Slots whose tag lies in [t0, t1) (the new pairs of a chunk, when the
+// append list overflowed).
+cudaError_t launch_collect_tag(const HashSet& hs, uint32_t t0, uint32_t t1, uint64_t* slots,
+                               uint64_t cap, unsigned long long* count, cudaStream_t s);
+
+// ---- k_verify.cu --------------------------------------------------------
+// Verify the new pairs of the set: records to rec (count = counters[0]).
+cudaError_t launch_verify_new(const Index& ix, int d, const HashSet& hs, const CollideScratch& cs,
+                              PairRec* rec, uint64_t rec_cap, cudaStream_t s, int i);
+// Verify explicit pairs (a,b) packed as a << 32 | b; per_dim optional [m][D].
+cudaError_t launch_verify_pairs(const Index& ix, int d, const uint64_t* pairs, int64_t m,
+                                int fp64, double* per_dim, double* dist_d, uint64_t* dims,
+                                cudaStream_t s);
+// Exact all-pairs: every non-trivial pair with approximate dist_d <= tau
+// appended to out (a << 32 | b) with count in *count (may exceed cap).
+cudaError_t launch_allpairs(const Index& ix, int d, float tau, uint64_t* out, uint64_t cap,
+                            unsigned long long* count, cudaStream_t s);
+// Row minima of dist_d over non-trivial partners (approximate), for the
+// first threshold of the all-pairs path; rowmin [M].
+cudaError_t launch_allpairs_rowmin(const Index& ix, int d, float* rowmin, cudaStream_t s);
+
+}  // namespace momenti

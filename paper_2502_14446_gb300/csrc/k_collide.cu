@@ -1,0 +1,387 @@
+// Index traversal of Algorithm 1 (lines 6-14) on the sorted index: at
+// prefix length i, in repetition j, every pair of windows sharing the
+// length-i prefix in some dimension is a collision; W(a, b) is the number
+// of dimensions in which they collide, and pairs with W >= d become
+// candidates.  As in Section 6.2 ("comparisons on the fly"), W is computed
+// when a collision is seen, from the keys of the two windows in all D
+// dimensions, so no quadratic W table is kept.  De-duplication that leaves
+// the candidate set of Algorithm 1 unchanged:
+//   - a pair is handled only from its lowest colliding dimension;
+//   - a pair already colliding in >= d dimensions at prefix i+1 in the same
+//     repetition was a candidate then (Section 6.2, duplicate collisions);
+//   - a device hash set of every pair seen so far keeps each pair's first
+//     (i, j) and lets only new pairs reach verification.
+//
+// Enumeration: within one (j, f) segment the windows of a bucket are a run
+// of ranks p with lcp[p] >= i after the run's first rank.  Ranks are cut in
+// chunks of 32; a tile is a pair of chunks (c1 <= c2) that can hold two
+// ranks of one bucket, handled by one warp with both chunks' keys in shared
+// memory.  The tiles of a launch are numbered through a scan, so work is
+// balanced however skewed the bucket sizes are.
+#include "internal.h"
+
+namespace momenti {
+
+namespace {
+
+constexpr uint64_t kEmpty = ~0ull;
+constexpr int kMaxProbe = 512;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // splitmix64 finalizer (Steele, Lea, Flood 2014)
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+struct Seg {
+  int64_t M;
+  int D, j0, C;
+  __device__ __forceinline__ int64_t base(int seg) const {
+    int j = j0 + seg / D, f = seg - (seg / D) * D;
+    return (int64_t(j) * D + f) * M;
+  }
+};
+
+// One warp per (segment, chunk): the last bucket start in the chunk (or -1)
+// and whether any rank of the chunk continues the bucket of its predecessor.
+__global__ void k_chunk_agg(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i,
+                            int32_t* __restrict__ cagg, uint64_t* __restrict__ ntile) {
+  const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= int64_t(segs) * sg.C) return;
+  const int seg = int(gw / sg.C);
+  const int64_t c = gw - int64_t(seg) * sg.C;
+  const uint8_t* L = lcp + sg.base(seg);
+  const int64_t p = c * 32 + lane;
+  const bool valid = p < sg.M;
+  const int l = valid ? int(L[p]) : 0;
+  const unsigned st = __ballot_sync(0xffffffffu, valid && l < i);
+  const unsigned jn = __ballot_sync(0xffffffffu, valid && l >= i);
+  if (lane == 0) {
+    cagg[gw] = st ? int32_t(c * 32 + 31 - __clz(int(st))) : -1;
+    ntile[gw] = jn ? 1u : 0u;
+  }
+}
+
+// One block per segment: bucket start of each chunk's first rank (exclusive
+// max-scan of the chunk aggregates) and the number of tiles whose column
+// chunk is this chunk: row chunks from the bucket start's chunk up to itself.
+__global__ void __launch_bounds__(1024)
+k_chunk_scan(const uint8_t* __restrict__ lcp, Seg sg, int i, const int32_t* __restrict__ cagg,
+             int32_t* __restrict__ cbs, uint64_t* __restrict__ ntile) {
+  __shared__ int32_t wtot[32];
+  __shared__ int32_t carry_s;
+  const int seg = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint8_t* L = lcp + sg.base(seg);
+  const int64_t off = int64_t(seg) * sg.C;
+  if (threadIdx.x == 0) carry_s = -1;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < sg.C; b0 += blockDim.x) {
+    const int64_t c = b0 + threadIdx.x;
+    int32_t v = c < sg.C ? cagg[off + c] : -1;
+    int32_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl = max(incl, u);
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t t = wtot[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t = max(t, u);
+      }
+      wtot[lane] = t;
+    }
+    __syncthreads();
+    const int32_t carry = carry_s;
+    int32_t before = wid ? wtot[wid - 1] : -1;
+    int32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = -1;
+    excl = max(max(excl, before), carry);
+    if (c < sg.C) {
+      const int64_t p0 = c * 32;
+      const int32_t bs = (int(L[p0]) < i) ? int32_t(p0) : excl;
+      cbs[off + c] = bs;
+      const uint64_t has = ntile[off + c];
+      ntile[off + c] = has ? uint64_t(c - bs / 32 + 1) : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = max(carry, wtot[31]);
+    __syncthreads();
+  }
+}
+
+// Device-wide exclusive scan of n uint64 values in place; v[n] = total.
+constexpr int kScanBlock = 1024;
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_local(uint64_t* __restrict__ v, int64_t n, uint64_t* __restrict__ bsum) {
+  __shared__ uint64_t wt[32];
+  const int64_t q = blockIdx.x * int64_t(kScanBlock) + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t x = q < n ? v[q] : 0;
+  uint64_t incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wt[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t t = wt[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    wt[lane] = t;
+  }
+  __syncthreads();
+  uint64_t before = wid ? wt[wid - 1] : 0;
+  if (q < n) v[q] = before + incl - x;
+  if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = before + incl;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_top(uint64_t* __restrict__ bsum, int64_t nb, uint64_t* __restrict__ total_out) {
+  __shared__ uint64_t wt[32];
+  __shared__ uint64_t carry_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanBlock) {
+    const int64_t q = b0 + threadIdx.x;
+    uint64_t x = q < nb ? bsum[q] : 0;
+    uint64_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wt[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t t = wt[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint64_t u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
+      }
+      wt[lane] = t;
+    }
+    __syncthreads();
+    const uint64_t carry = carry_s;
+    uint64_t before = wid ? wt[wid - 1] : 0;
+    if (q < nb) bsum[q] = carry + before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + wt[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total_out = carry_s;
+}
+
+__global__ void k_scan_add(uint64_t* __restrict__ v, int64_t n, const uint64_t* __restrict__ bsum) {
+  const int64_t q = blockIdx.x * int64_t(kScanBlock) + threadIdx.x;
+  if (q < n) v[q] += bsum[blockIdx.x];
+}
+
+struct CollideArgs {
+  const uint32_t* order;
+  const uint8_t* lcp;
+  const uint64_t* keys;
+  Seg sg;
+  int segs, i, K, d, excl;
+  const int32_t* cbs;
+  const uint64_t* toff;    // exclusive scan, toff[E] = total tiles
+  HashSet hs;
+  uint32_t seq_base;       // tag of repetition 0 at this prefix length
+  uint64_t* new_slots;
+  uint64_t new_cap;
+  unsigned long long* counters;   // [0] new / plain count, [1] candidates, [2] flags
+  uint64_t* out_pairs;
+  uint64_t out_cap;
+};
+
+template <bool PLAIN>
+__global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
+  extern __shared__ uint64_t smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int D = g.sg.D, Dp = D + 1;
+  uint64_t* sk = smem + int64_t(wib) * (64 * Dp + 32);
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(sk + 64 * Dp);
+  const int64_t E = int64_t(g.segs) * g.sg.C;
+  const uint64_t T = g.toff[E];
+  const uint64_t nw = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  const int sh = 64 - 8 * g.i;
+  const int sh1 = 64 - 8 * (g.i + 1);
+  const bool lvl_dup = !PLAIN && g.i < g.K;
+  for (uint64_t t = uint64_t(blockIdx.x) * (blockDim.x >> 5) + wib; t < T; t += nw) {
+    // largest e with toff[e] <= t
+    int64_t lo = 0, hi = E - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (g.toff[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const int64_t e = lo;
+    const int seg = int(e / g.sg.C);
+    const int64_t c2 = e - int64_t(seg) * g.sg.C;
+    const int32_t bs0 = g.cbs[e];
+    const int64_t c1 = bs0 / 32 + int64_t(t - g.toff[e]);
+    const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
+    const int64_t sbase = g.sg.base(seg);
+    const uint32_t* O = g.order + sbase;
+    const uint8_t* Lc = g.lcp + sbase;
+    const uint64_t* Kj = g.keys + int64_t(j) * g.sg.M * D;
+    // bucket start of each column rank
+    const int64_t p2 = c2 * 32 + lane;
+    const bool v2 = p2 < g.sg.M;
+    int32_t s = (v2 && int(Lc[p2]) < g.i) ? int32_t(p2) : -1;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s = max(s, u);
+    }
+    const int32_t bs2 = max(s, bs0);
+    const int64_t p1 = c1 * 32 + lane;
+    const bool v1 = p1 < g.sg.M;
+    __syncwarp();
+    sidx[lane] = v1 ? O[p1] : 0u;
+    sidx[32 + lane] = v2 ? O[p2] : 0u;
+    __syncwarp();
+    for (int q = lane; q < 64 * D; q += 32) {
+      const int r = q / D, ff = q - r * D;
+      const bool ok = r < 32 ? (c1 * 32 + r < g.sg.M) : (c2 * 32 + (r - 32) < g.sg.M);
+      sk[r * Dp + ff] = ok ? Kj[int64_t(sidx[r]) * D + ff] : 0ull;
+    }
+    __syncwarp();
+    const uint32_t wa = sidx[lane];
+    const uint64_t* ka = sk + lane * Dp;
+    for (int cc = 0; cc < 32; ++cc) {
+      const int64_t pc = c2 * 32 + cc;
+      if (pc >= g.sg.M) break;
+      const int32_t bsc = __shfl_sync(0xffffffffu, bs2, cc);
+      if (!(p1 >= bsc && p1 < pc)) continue;
+      const uint32_t wb = sidx[32 + cc];
+      const uint32_t a = min(wa, wb), b = max(wa, wb);
+      if (int64_t(b) - int64_t(a) <= g.excl) continue;
+      const uint64_t* kb = sk + (32 + cc) * Dp;
+      int W = 0, W1 = 0;
+      bool skip = false;
+      for (int ff = 0; ff < D; ++ff) {
+        const uint64_t x = ka[ff] ^ kb[ff];
+        if ((x >> sh) == 0) {
+          if (ff < f) { skip = true; break; }
+          ++W;
+          if (lvl_dup && (x >> sh1) == 0) ++W1;
+        }
+      }
+      if (skip || W < g.d) continue;
+      if (lvl_dup && W1 >= g.d) continue;
+      const uint64_t key = (uint64_t(a) << 32) | b;
+      if (PLAIN) {
+        unsigned long long pos = atomicAdd(&g.counters[0], 1ull);
+        if (pos < g.out_cap) g.out_pairs[pos] = key;
+        continue;
+      }
+      atomicAdd(&g.counters[1], 1ull);
+      const uint32_t tagv = g.seq_base + uint32_t(j);
+      uint64_t h = mix64(key) & (g.hs.cap - 1);
+      bool done = false;
+      for (int probe = 0; probe < kMaxProbe && !done; ++probe) {
+        uint64_t cur = g.hs.keys[h];
+        if (cur == kEmpty) {
+          cur = atomicCAS(reinterpret_cast<unsigned long long*>(&g.hs.keys[h]), kEmpty, key);
+          if (cur == kEmpty) {
+            atomicMin(&g.hs.tag[h], tagv);
+            unsigned long long pos = atomicAdd(&g.counters[0], 1ull);
+            if (pos < g.new_cap) g.new_slots[pos] = h;
+            done = true;
+            break;
+          }
+        }
+        if (cur == key) {
+          atomicMin(&g.hs.tag[h], tagv);
+          done = true;
+          break;
+        }
+        h = (h + 1) & (g.hs.cap - 1);
+      }
+      if (!done) atomicOr(&g.counters[2], 1ull);
+    }
+  }
+}
+
+__global__ void k_hs_clear(uint64_t* __restrict__ keys, uint32_t* __restrict__ tag, uint64_t cap) {
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < cap;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    keys[q] = kEmpty;
+    tag[q] = 0xffffffffu;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {
+  MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<152 * 8, 256, 0, s>>>(hs.keys, hs.tag, hs.cap));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const HashSet& hs,
+                           const CollideScratch& cs, int mode_plain, uint64_t* out_pairs,
+                           uint64_t out_cap, cudaStream_t s) {
+  const int segs = (j1 - j0) * ix.D;
+  const int64_t C = (ix.M + 31) / 32;
+  if (segs > cs.seg_cap || C > cs.chunk_cap) return cudaErrorInvalidValue;
+  Seg sg{ix.M, ix.D, j0, int(C)};
+  const int64_t E = int64_t(segs) * C;
+  uint64_t* toff = cs.ntile;
+  MOMENTI_LAUNCH("chunk_agg", s, k_chunk_agg<<<unsigned((E * 32 + 255) / 256), 256, 0, s>>>(ix.lcp, sg, segs, i, cs.cagg, toff));
+  MOMENTI_LAUNCH("chunk_scan", s, k_chunk_scan<<<segs, 1024, 0, s>>>(ix.lcp, sg, i, cs.cagg, cs.cbs, toff));
+  const int64_t nb = (E + kScanBlock - 1) / kScanBlock;
+  uint64_t* bsum = cs.scan_tmp;
+  MOMENTI_LAUNCH("scan_local", s, k_scan_local<<<unsigned(nb), kScanBlock, 0, s>>>(toff, E, bsum));
+  MOMENTI_LAUNCH("scan_top", s, k_scan_top<<<1, kScanBlock, 0, s>>>(bsum, nb, toff + E));
+  MOMENTI_LAUNCH("scan_add", s, k_scan_add<<<unsigned(nb), kScanBlock, 0, s>>>(toff, E, bsum));
+  CollideArgs g{ix.order, ix.lcp, ix.keys, sg, segs, i, ix.K, d, ix.excl, cs.cbs, toff, hs,
+                uint32_t((ix.K - i) * ix.L), cs.new_slots, cs.new_cap, cs.counters, out_pairs,
+                out_cap};
+  size_t smem = size_t(4) * (64 * (ix.D + 1) + 32) * sizeof(uint64_t);
+  cudaError_t e;
+  if (mode_plain) {
+    e = cudaFuncSetAttribute(k_collide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("collide", s, k_collide<true><<<152 * 8, 128, smem, s>>>(g));
+  } else {
+    e = cudaFuncSetAttribute(k_collide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("collide", s, k_collide<false><<<152 * 8, 128, smem, s>>>(g));
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace momenti
+
+namespace momenti {
+namespace {
+__global__ void k_collect_tag(const HashSet hs, uint32_t t0, uint32_t t1, uint64_t* __restrict__ slots,
+                              uint64_t cap, unsigned long long* __restrict__ count) {
+  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < hs.cap;
+       q += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t t = hs.tag[q];
+    if (hs.keys[q] != kEmpty && t >= t0 && t < t1) {
+      unsigned long long pos = atomicAdd(count, 1ull);
+      if (pos < cap) slots[pos] = q;
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_collect_tag(const HashSet& hs, uint32_t t0, uint32_t t1, uint64_t* slots,
+                               uint64_t cap, unsigned long long* count, cudaStream_t s) {
+  MOMENTI_LAUNCH("collect_tag", s, k_collect_tag<<<152 * 8, 256, 0, s>>>(hs, t0, t1, slots, cap, count));
+  return cudaGetLastError();
+}
+}  // namespace momenti

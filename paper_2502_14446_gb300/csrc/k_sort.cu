@@ -1,0 +1,201 @@
+// Index construction of Section 4: for every (repetition j, dimension f)
+// the windows ordered lexicographically by their K-value hash strings, so
+// that every prefix length i groups colliding windows into contiguous runs.
+//
+// A batched, stable least-significant-digit radix sort over the K key bytes
+// (8-bit digits, last concatenation first), one segment per (j, f), all
+// segments of a batch of repetitions in the same launches.  Each pass is
+// three kernels: per-tile digit histograms, a per-segment scan of
+// (digit, tile) counts, and a stable scatter that ranks equal digits with
+// warp-level match masks.  The final kernel writes the sorted window order
+// and, per rank, the number of hash values shared with the previous rank
+// (the longest common prefix, 0..K), which is all the traversal needs.
+#include "internal.h"
+
+#include <algorithm>
+
+namespace momenti {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;                      // per thread
+constexpr int kTile = kThreads * kItems;       // 2048 entries per CTA
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpSpan = kTile / kWarps;      // 256 entries per warp
+constexpr int kRounds = kWarpSpan / 32;        // 8
+
+struct Src {
+  // pass 0 reads keys [j][a][f] and the implicit value a; later passes read
+  // the ping-pong buffers [seg][M]
+  const uint64_t* keys;
+  const uint64_t* kin;
+  const uint32_t* vin;
+  int64_t M;
+  int D, j0;
+  bool first;
+  __device__ __forceinline__ void load(int seg, int64_t p, uint64_t& k, uint32_t& v) const {
+    if (first) {
+      int j = j0 + seg / D, f = seg - (seg / D) * D;
+      k = keys[(int64_t(j) * M + p) * D + f];
+      v = uint32_t(p);
+    } else {
+      k = kin[int64_t(seg) * M + p];
+      v = vin[int64_t(seg) * M + p];
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kThreads)
+k_hist(Src src, int shift, int tiles, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  const int seg = blockIdx.y, tile = blockIdx.x;
+  for (int d = threadIdx.x; d < 256; d += kThreads) h[d] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(tile) * kTile;
+  for (int q = threadIdx.x; q < kTile; q += kThreads) {
+    int64_t p = base + q;
+    if (p < src.M) {
+      uint64_t k;
+      uint32_t v;
+      src.load(seg, p, k, v);
+      atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t* out = hist + int64_t(seg) * 256 * tiles;
+  for (int d = threadIdx.x; d < 256; d += kThreads) out[int64_t(d) * tiles + tile] = h[d];
+}
+
+// Exclusive scan over the digit-major (digit, tile) counts of one segment.
+__global__ void __launch_bounds__(256) k_scan(int tiles, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t tot[256];
+  const int seg = blockIdx.x, d = threadIdx.x;
+  uint32_t* hs = hist + int64_t(seg) * 256 * tiles + int64_t(d) * tiles;
+  uint32_t s = 0;
+  for (int t = 0; t < tiles; ++t) s += hs[t];
+  tot[d] = s;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the 256 digit totals
+  for (int off = 1; off < 256; off <<= 1) {
+    uint32_t v = d >= off ? tot[d - off] : 0u;
+    __syncthreads();
+    tot[d] += v;
+    __syncthreads();
+  }
+  uint32_t run = tot[d] - s;   // exclusive
+  for (int t = 0; t < tiles; ++t) {
+    uint32_t c = hs[t];
+    hs[t] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
+          uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+  __shared__ uint32_t wh[kWarps][256];
+  const int seg = blockIdx.y, tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = threadIdx.x; q < kWarps * 256; q += kThreads) (&wh[0][0])[q] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(tile) * kTile + int64_t(warp) * kWarpSpan;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint64_t key[kRounds];
+  uint32_t val[kRounds], dig[kRounds], loc[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    int64_t p = base + r * 32 + lane;
+    uint32_t dg = 256u + lane;           // out of range: a digit no valid item has
+    key[r] = 0;
+    val[r] = 0;
+    if (p < src.M) {
+      src.load(seg, p, key[r], val[r]);
+      dg = uint32_t(key[r] >> shift) & 255u;
+    }
+    dig[r] = dg;
+    uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t rank = __popc(peers & lt);
+    uint32_t cnt = __popc(peers);
+    uint32_t b = 0;
+    if (dg < 256u) b = wh[warp][dg];
+    __syncwarp();
+    if (dg < 256u && rank == 0) wh[warp][dg] = b + cnt;
+    __syncwarp();
+    loc[r] = b + rank;
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kThreads) {
+    uint32_t run = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      uint32_t c = wh[w][d];
+      wh[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  const uint32_t* hs = hist + int64_t(seg) * 256 * tiles;
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    if (dig[r] < 256u) {
+      uint32_t dst = hs[int64_t(dig[r]) * tiles + tile] + wh[warp][dig[r]] + loc[r];
+      kout[int64_t(seg) * src.M + dst] = key[r];
+      vout[int64_t(seg) * src.M + dst] = val[r];
+    }
+  }
+}
+
+__global__ void k_finish(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                         int64_t M, int D, int j0, int segs, int K, uint32_t* __restrict__ order,
+                         uint8_t* __restrict__ lcp) {
+  int64_t total = int64_t(segs) * M;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    int64_t seg = q / M, p = q - seg * M;
+    int64_t j = j0 + seg / D, f = seg % D;
+    int64_t o = (j * D + f) * M + p;
+    order[o] = vin[q];
+    uint32_t l = 0;
+    if (p > 0) {
+      uint64_t x = kin[q] ^ kin[q - 1];
+      l = x == 0 ? 8u : uint32_t(__clzll(x)) / 8u;
+      if (l > uint32_t(K)) l = uint32_t(K);
+    }
+    lcp[o] = uint8_t(l);
+  }
+}
+
+}  // namespace
+
+int64_t sort_hist_entries(int64_t M, int segs) {
+  int64_t tiles = (M + kTile - 1) / kTile;
+  return int64_t(segs) * 256 * tiles;
+}
+
+cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch& sc,
+                             cudaStream_t s) {
+  if (j1 <= j0) return cudaSuccess;
+  const int segs = (j1 - j0) * ix.D;
+  if (int64_t(segs) * ix.M > sc.cap_entries || sort_hist_entries(ix.M, segs) > sc.hist_entries)
+    return cudaErrorInvalidValue;
+  const int tiles = int((ix.M + kTile - 1) / kTile);
+  dim3 grid{unsigned(tiles), unsigned(segs), 1u};
+  uint64_t* kb[2] = {sc.k0, sc.k1};
+  uint32_t* vb[2] = {sc.v0, sc.v1};
+  for (int pass = 0; pass < ix.K; ++pass) {
+    const int byte = ix.K - 1 - pass;          // 0 = most significant hash value
+    const int shift = 56 - 8 * byte;
+    Src src{ix.keys, pass ? kb[(pass - 1) & 1] : nullptr, pass ? vb[(pass - 1) & 1] : nullptr,
+            ix.M, ix.D, j0, pass == 0};
+    MOMENTI_LAUNCH("sort_hist", s, k_hist<<<grid, kThreads, 0, s>>>(src, shift, tiles, sc.hist));
+    MOMENTI_LAUNCH("sort_scan", s, k_scan<<<segs, 256, 0, s>>>(tiles, sc.hist));
+    MOMENTI_LAUNCH("sort_scatter", s, k_scatter<<<grid, kThreads, 0, s>>>(src, shift, tiles, sc.hist, kb[pass & 1], vb[pass & 1]));
+  }
+  const int last = (ix.K - 1) & 1;
+  int64_t total = int64_t(segs) * ix.M;
+  int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
+  MOMENTI_LAUNCH("sort_finish", s, k_finish<<<g, 256, 0, s>>>(kb[last], vb[last], ix.M, ix.D, j0, segs, ix.K, ix.order, ix.lcp));
+  return cudaGetLastError();
+}
+
+}  // namespace momenti

@@ -1,0 +1,937 @@
+// Host side of the C ABI declared in include/momenti.h: argument checks,
+// the memory planner, the hash-all pipeline (Algorithm 1, line 2, and the
+// index of Section 4), the traversal driver with TOP and STOP (Algorithm 1,
+// lines 3-19, Algorithm 2), the exact all-pairs path (line 20) and the
+// float64 re-verification of the result.
+//
+// TOP: Algorithm 1 keeps a bounded priority queue; with the trivial-match
+// rule of the top-k definition (Section 3.1) one new pair can displace two
+// kept ones, so TOP here is the greedy selection (ascending dist_d, then a,
+// then b; a pair is taken iff both of its windows are more than eps away
+// from both windows of every taken pair) over every distinct pair verified
+// so far, recomputed only when a new pair lands below the current k-th.
+//
+// Repetitions are processed in chunks on the device; the host replays the
+// chunk's new pairs in the paper's order (by repetition, as each pair is
+// tagged with the first repetition in which it became a candidate) and
+// evaluates STOP after each repetition, so the result and the stopping
+// point are those of the sequential Algorithm 1.
+#include "../../include/momenti.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+using namespace momenti;
+
+constexpr int kChunkReps = 32;   // repetitions per device round trip of the traversal
+
+namespace {
+
+struct PoolEntry {
+  double dd;        // dist_d
+  double dmax;      // dist_d^max
+  uint32_t a, b;
+  uint64_t dims;
+};
+
+bool pair_less(const PoolEntry& x, const PoolEntry& y) {
+  if (x.dd != y.dd) return x.dd < y.dd;
+  if (x.a != y.a) return x.a < y.a;
+  return x.b < y.b;
+}
+
+// Greedy top-k under the trivial-match exclusion over entries sorted by
+// pair_less; returns indices of the accepted entries.
+std::vector<size_t> greedy(const std::vector<PoolEntry>& sorted, int k, int64_t eps) {
+  std::vector<size_t> acc;
+  for (size_t q = 0; q < sorted.size() && int(acc.size()) < k; ++q) {
+    const PoolEntry& c = sorted[q];
+    if (int64_t(c.b) - int64_t(c.a) <= eps) continue;
+    bool ok = true;
+    for (size_t t : acc) {
+      const PoolEntry& s = sorted[t];
+      int64_t xs[2] = {c.a, c.b}, ys[2] = {s.a, s.b};
+      for (int u = 0; u < 2 && ok; ++u)
+        for (int v = 0; v < 2 && ok; ++v)
+          if (std::llabs(xs[u] - ys[v]) <= eps) ok = false;
+      if (!ok) break;
+    }
+    if (ok) acc.push_back(q);
+  }
+  return acc;
+}
+
+double std_normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+// Eq. (eucl-collision-probability).
+double collision_probability(double R, double r) {
+  if (R <= 0.0) return 1.0;
+  const double c = r / R;
+  return 1.0 - 2.0 * std_normal_cdf(-c) -
+         2.0 / (std::sqrt(2.0 * M_PI) * c) * (1.0 - std::exp(-c * c / 2.0));
+}
+
+// Lemma stop (Eq. probnotcolliding) / Algorithm 2; i, j 1-based.
+double failure_bound(double dist_max, int i, int j, int K, int L, int d, double r) {
+  const double p = std::pow(collision_probability(dist_max, r), d);
+  const double first = std::pow(1.0 - std::pow(p, i), j);
+  if (i == K) return first;
+  return first * std::pow(1.0 - std::pow(p, i + 1), L - j);
+}
+
+struct Pool {
+  std::vector<PoolEntry> items;   // unsorted store
+  std::unordered_set<uint64_t> seen;
+  std::vector<PoolEntry> top;     // current greedy selection
+  double tau_trunc = INFINITY;    // every pair with dist_d < tau_trunc is held
+  size_t cap = size_t(1) << 22;
+  int k = 1;
+  int64_t eps = 0;
+
+  double kth() const { return int(top.size()) == k ? top.back().dd : INFINITY; }
+  bool valid() const { return int(top.size()) == k && top.back().dd < tau_trunc; }
+
+  void recompute() {
+    std::vector<PoolEntry> s = items;
+    std::sort(s.begin(), s.end(), pair_less);
+    auto acc = greedy(s, k, eps);
+    top.clear();
+    for (size_t q : acc) top.push_back(s[q]);
+  }
+  void truncate() {
+    if (items.size() <= cap) return;
+    size_t keep = cap / 2;
+    std::nth_element(items.begin(), items.begin() + keep, items.end(), pair_less);
+    double cut = INFINITY;
+    for (size_t q = keep; q < items.size(); ++q) cut = std::min(cut, items[q].dd);
+    tau_trunc = std::min(tau_trunc, cut);
+    items.resize(keep);
+  }
+  // Adds a batch; returns true if the greedy selection was recomputed.
+  bool add(const PairRec* r, size_t m) {
+    const double kt = kth();
+    bool dirty = false;
+    for (size_t q = 0; q < m; ++q) {
+      uint64_t key = (uint64_t(r[q].a) << 32) | r[q].b;
+      if (double(r[q].dist_d) >= tau_trunc) continue;
+      if (!seen.insert(key).second) continue;
+      items.push_back(PoolEntry{double(r[q].dist_d), double(r[q].dist_max), r[q].a, r[q].b, r[q].dims});
+      if (double(r[q].dist_d) <= kt) dirty = true;
+    }
+    if (items.size() > cap) {
+      truncate();
+      dirty = true;
+    }
+    if (dirty) recompute();
+    return dirty;
+  }
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct momenti_handle {
+  momenti_params p{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  std::vector<float> user_a, user_u;
+  int user_D = 0, user_L = 0, user_K = 0;
+  Index ix;
+  bool ready = false;
+  std::vector<DevBuf> bufs;
+  uint64_t device_bytes = 0;
+  SortScratch sort;
+  CollideScratch cs;
+  HashSet hs;
+  PairRec* rec_dev = nullptr;
+  PairRec* rec_host = nullptr;
+  unsigned long long* cnt_host = nullptr;
+  int chunk_reps = 32;
+  double t_hash_ms = 0, t_sort_ms = 0;
+  bool used_tc = false;
+  uint64_t n_flagged = 0;
+  int sort_reps = 1;
+  uint64_t hp_gen = 0, built_gen = ~0ull;   // hash-parameter generations
+  float* draw_a = nullptr;                  // device copies of the hash draws
+  float* draw_u = nullptr;
+  uint64_t* flags = nullptr;                // near-boundary list of the tensor-core form
+  uint32_t flag_cap = 0;
+  uint32_t* small = nullptr;                // r min/max, flag count, error flag
+};
+
+namespace {
+
+int fail(momenti_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, MOMENTI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(momenti_handle* h, T** ptr, size_t count) {
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return e;
+  h->bufs.push_back(DevBuf{p, bytes});
+  h->device_bytes += bytes;
+  *ptr = static_cast<T*>(p);
+  return cudaSuccess;
+}
+
+void free_all(momenti_handle* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (auto& b : h->bufs) cudaFree(b.p);
+  h->bufs.clear();
+  h->device_bytes = 0;
+  if (h->rec_host) cudaFreeHost(h->rec_host);
+  if (h->cnt_host) cudaFreeHost(h->cnt_host);
+  h->rec_host = nullptr;
+  h->cnt_host = nullptr;
+  h->rec_dev = nullptr;
+  h->draw_a = h->draw_u = nullptr;
+  h->flags = nullptr;
+  h->small = nullptr;
+  h->ix = Index{};
+  h->sort = SortScratch{};
+  h->cs = CollideScratch{};
+  h->hs = HashSet{};
+  h->ready = false;
+}
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// Re-verifies in float64 every pool pair whose float32 dist_d is within
+// tolerance of the k-th selected one, and selects the top-k again on the
+// float64 distances.  fills out/n_out; returns the max relative float32
+// error over the result.
+int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out, int32_t* n_out,
+             double fail_bound, double* max_err) {
+  const Index& ix = h->ix;
+  const int k = h->p.k;
+  std::sort(cand.begin(), cand.end(), pair_less);
+  auto acc = greedy(cand, k, ix.excl);
+  double kth = acc.empty() ? INFINITY : cand[acc.back()].dd;
+  double lim = std::isfinite(kth) ? kth * (1.0 + 1e-4) + 1e-6 : INFINITY;
+  std::vector<PoolEntry> near;
+  for (auto& c : cand)
+    if (c.dd <= lim) near.push_back(c);
+  const int64_t m = int64_t(near.size());
+  *max_err = 0.0;
+  if (m > 0) {
+    std::vector<uint64_t> pk(m);
+    for (int64_t q = 0; q < m; ++q) pk[q] = (uint64_t(near[q].a) << 32) | near[q].b;
+    uint64_t* dp = nullptr;
+    double *dpd = nullptr, *ddd = nullptr;
+    uint64_t* dmask = nullptr;
+    CK(cudaMallocAsync(&dp, m * 8, h->stream));
+    CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
+    CK(cudaMallocAsync(&ddd, m * 8, h->stream));
+    CK(cudaMallocAsync(&dmask, m * 8, h->stream));
+    CK(cudaMemcpyAsync(dp, pk.data(), m * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_verify_pairs(ix, h->p.d, dp, m, 1, dpd, ddd, dmask, h->stream));
+    std::vector<double> per(m * ix.D), dd(m);
+    std::vector<uint64_t> mk(m);
+    CK(cudaMemcpyAsync(per.data(), dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(dd.data(), ddd, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(mk.data(), dmask, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(dp, h->stream));
+    CK(cudaFreeAsync(dpd, h->stream));
+    CK(cudaFreeAsync(ddd, h->stream));
+    CK(cudaFreeAsync(dmask, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int64_t q = 0; q < m; ++q) {
+      double mx = 0;
+      for (int f = 0; f < ix.D; ++f)
+        if (mk[q] >> f & 1) mx = std::max(mx, per[q * ix.D + f]);
+      near[q].dd = dd[q];
+      near[q].dmax = mx;
+      near[q].dims = mk[q];
+    }
+    std::sort(near.begin(), near.end(), pair_less);
+    acc = greedy(near, k, ix.excl);
+    cand = near;
+  }
+  int cnt = 0;
+  for (size_t q : acc) {
+    const PoolEntry& c = cand[q];
+    out[cnt].a = c.a;
+    out[cnt].b = c.b;
+    out[cnt].dist_d = c.dd;
+    out[cnt].dist_max = c.dmax;
+    out[cnt].fail_bound = fail_bound;
+    out[cnt].dims_mask = c.dims;
+    ++cnt;
+  }
+  *n_out = cnt;
+  return MOMENTI_OK;
+}
+
+// Exact all-pairs top-k (Algorithm 1, line 20).  tau0 <= 0: derive the
+// first threshold from per-window nearest distances.
+int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_out, double* max_err) {
+  Index& ix = h->ix;
+  const int k = h->p.k;
+  double tau = tau0;
+  if (!(tau > 0)) {
+    float* rowmin = nullptr;
+    CK(cudaMallocAsync(&rowmin, ix.M * 4, h->stream));
+    CK(cudaMemsetAsync(rowmin, 0x7f, ix.M * 4, h->stream));
+    CK(launch_allpairs_rowmin(ix, h->p.d, rowmin, h->stream));
+    std::vector<float> rm(ix.M);
+    CK(cudaMemcpyAsync(rm.data(), rowmin, ix.M * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(rowmin, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // 2k-th smallest nearest distance among windows spaced more than eps
+    std::vector<std::pair<float, int64_t>> v;
+    for (int64_t a = 0; a < ix.M; ++a)
+      if (std::isfinite(rm[a])) v.push_back({rm[a], a});
+    std::sort(v.begin(), v.end());
+    std::vector<int64_t> picked;
+    double val = 0;
+    for (auto& pr : v) {
+      bool ok = true;
+      for (int64_t q : picked)
+        if (std::llabs(q - pr.second) <= ix.excl) { ok = false; break; }
+      if (!ok) continue;
+      picked.push_back(pr.second);
+      val = pr.first;
+      if (int(picked.size()) >= 2 * k) break;
+    }
+    if (picked.empty()) {
+      *n_out = 0;
+      return MOMENTI_OK;
+    }
+    tau = std::max(val * 1.2, 1e-3);
+  }
+  uint64_t cap = uint64_t(1) << 22;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    uint64_t* dout = nullptr;
+    unsigned long long* dcnt = nullptr;
+    CK(cudaMallocAsync(&dout, cap * 8, h->stream));
+    CK(cudaMallocAsync(&dcnt, 8, h->stream));
+    CK(cudaMemsetAsync(dcnt, 0, 8, h->stream));
+    CK(launch_allpairs(ix, h->p.d, float(tau), dout, cap, dcnt, h->stream));
+    unsigned long long cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (cnt > cap) {
+      CK(cudaFreeAsync(dout, h->stream));
+      CK(cudaFreeAsync(dcnt, h->stream));
+      if (cnt > (uint64_t(1) << 28)) {
+        tau *= 0.5;
+        continue;
+      }
+      cap = next_pow2(cnt);
+      --attempt;
+      continue;
+    }
+    const int64_t m = int64_t(cnt);
+    std::vector<PoolEntry> cand;
+    if (m > 0) {
+      double *dpd = nullptr, *ddd = nullptr;
+      uint64_t* dmask = nullptr;
+      CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
+      CK(cudaMallocAsync(&ddd, m * 8, h->stream));
+      CK(cudaMallocAsync(&dmask, m * 8, h->stream));
+      CK(launch_verify_pairs(ix, h->p.d, dout, m, 0, dpd, ddd, dmask, h->stream));
+      std::vector<uint64_t> pk(m), mk(m);
+      std::vector<double> per(m * ix.D), dd(m);
+      CK(cudaMemcpyAsync(pk.data(), dout, m * 8, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(per.data(), dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(dd.data(), ddd, m * 8, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(mk.data(), dmask, m * 8, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaFreeAsync(dpd, h->stream));
+      CK(cudaFreeAsync(ddd, h->stream));
+      CK(cudaFreeAsync(dmask, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      cand.reserve(m);
+      for (int64_t q = 0; q < m; ++q) {
+        if (dd[q] > tau) continue;
+        double mx = 0;
+        for (int f = 0; f < ix.D; ++f)
+          if (mk[q] >> f & 1) mx = std::max(mx, per[q * ix.D + f]);
+        cand.push_back(PoolEntry{dd[q], mx, uint32_t(pk[q] >> 32), uint32_t(pk[q]), mk[q]});
+      }
+    }
+    CK(cudaFreeAsync(dout, h->stream));
+    CK(cudaFreeAsync(dcnt, h->stream));
+    std::sort(cand.begin(), cand.end(), pair_less);
+    auto acc = greedy(cand, k, ix.excl);
+    // every pair with dist_d <= tau is held, so the greedy prefix is exact
+    // once k pairs are taken at or below tau; the float64 re-check keeps a
+    // margin for pairs near tau
+    if (int(acc.size()) == k && cand[acc.back()].dd * (1.0 + 1e-4) + 1e-6 <= tau)
+      return finalize(h, cand, out, n_out, 0.0, max_err);
+    if (int(acc.size()) < k && tau > 4.0 * std::sqrt(double(ix.w)) * h->p.d) {
+      // every pair is below tau: fewer than k non-trivial motifs exist
+      return finalize(h, cand, out, n_out, 0.0, max_err);
+    }
+    tau *= 2.0;
+  }
+  return fail(h, MOMENTI_ERR_OVERFLOW, "exact path: threshold search did not converge");
+}
+
+}  // namespace
+
+extern "C" {
+
+int momenti_default_params(momenti_params* p) {
+  if (!p) return MOMENTI_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->w = 100;
+  p->d = 1;
+  p->k = 1;
+  p->delta = 0.01;
+  p->mem_limit = 0;
+  p->K = 8;
+  p->L = 200;
+  p->r = 0.0;
+  p->excl = -1;
+  p->seed = 0;
+  p->precision = MOMENTI_PREC_F16X2;
+  p->delta_mode = MOMENTI_DELTA_PER_MOTIF;
+  return MOMENTI_OK;
+}
+
+int momenti_create(momenti_handle** out, const momenti_params* p) {
+  if (!out || !p) return MOMENTI_ERR_ARG;
+  *out = nullptr;
+  if (p->w < 2 || p->d < 1 || p->k < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->K < 1 ||
+      p->K > MOMENTI_MAX_K || p->L < 0 ||
+      (p->precision != MOMENTI_PREC_FP32 && p->precision != MOMENTI_PREC_F16X2) ||
+      (p->delta_mode != MOMENTI_DELTA_PER_MOTIF && p->delta_mode != MOMENTI_DELTA_ALL_K))
+    return MOMENTI_ERR_ARG;
+  auto* h = new momenti_handle();
+  h->p = *p;
+  *out = h;
+  return MOMENTI_OK;
+}
+
+void momenti_destroy(momenti_handle* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+const char* momenti_last_error(const momenti_handle* h) {
+  if (!h) return "no handle";
+  return h->err.c_str();
+}
+
+int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
+                            const float* a, const float* u) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!a || !u || D < 1 || D > MOMENTI_MAX_D || L < 1 || K != h->p.K || w != h->p.w)
+    return fail(h, MOMENTI_ERR_ARG, "set_hash_params: bad sizes");
+  const size_t na = size_t(D) * L * K * w, nu = size_t(D) * L * K;
+  for (size_t q = 0; q < nu; ++q)
+    if (!(u[q] >= 0.f && u[q] < 1.f)) return fail(h, MOMENTI_ERR_ARG, "set_hash_params: u outside [0,1)");
+  h->user_a.assign(a, a + na);
+  h->user_u.assign(u, u + nu);
+  h->user_D = D;
+  h->user_L = L;
+  h->user_K = K;
+  ++h->hp_gen;
+  return MOMENTI_OK;
+}
+
+int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n, int32_t D,
+                     int64_t ld, int32_t on_device, void* stream) {
+  if (!h) return MOMENTI_ERR_ARG;
+  const auto& p = h->p;
+  if (!series || D < 1 || D > MOMENTI_MAX_D || p.d > D || n < p.w || ld < n ||
+      (dtype != MOMENTI_F32 && dtype != MOMENTI_F64))
+    return fail(h, MOMENTI_ERR_ARG, "hash_all: bad arguments");
+  const int64_t M = n - p.w + 1;
+  if (M >= kMaxWindows) return fail(h, MOMENTI_ERR_ARG, "hash_all: too many windows");
+  if (!h->user_a.empty() && h->user_D != D)
+    return fail(h, MOMENTI_ERR_ARG, "hash_all: D differs from set_hash_params");
+  // a series of the same shape reuses every buffer of the previous index
+  const bool reuse = h->ready && h->ix.n == n && h->ix.D == D &&
+                     h->ix.has_lo == (dtype == MOMENTI_F64) && h->built_gen == h->hp_gen;
+  if (!reuse) free_all(h);
+  h->ready = false;
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = h->stream;
+  Index& ix = h->ix;
+  const int w = p.w, K = p.K;
+  const size_t elem = dtype == MOMENTI_F64 ? 8 : 4;
+
+  if (!reuse) {
+    // ---- memory planner ----
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t limit = p.mem_limit ? p.mem_limit : uint64_t(0.8 * double(free_b));
+    const int Wp = ((w + 63) / 64) * 64;
+    const uint64_t fixed = uint64_t(D) * n * (dtype == MOMENTI_F64 ? 8 : 4)  // series hi/lo
+                           + uint64_t(D) * n * elem                          // transient staging
+                           + uint64_t(D) * M * (8 + 8 + 4 + 4 + 4)           // stats
+                           + (uint64_t(64) << 20);                           // small scratch
+    const uint64_t per_rep = uint64_t(M) * D * (8 + 4 + 1)                   // keys, order, lcp
+                             + uint64_t(D) * kRepStride * Wp * (2 + 4)       // a16, a32
+                             + uint64_t(D) * kRepStride * 4                  // boff
+                             + uint64_t(D) * K * (w + 1) * 4                 // draws
+                             + uint64_t(D) * M * kRepStride * 8 / 100;       // rehash flags
+    const int L_cap = p.L > 0 ? p.L : 4096;
+    const int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
+    // sort scratch: a batch of repetitions whose ping-pong buffers stay near L2 size
+    const uint64_t seg_bytes = uint64_t(M) * (8 + 8 + 4 + 4);
+    int sort_reps = int(std::max<uint64_t>(1, (uint64_t(96) << 20) / (seg_bytes * D)));
+    // traversal scratch
+    const int64_t C = (M + 31) / 32;
+    int chunk = std::min(kChunkReps, L_user);
+    const uint64_t new_cap = uint64_t(1) << 21;
+    const uint64_t hs_cap = std::min<uint64_t>(
+        uint64_t(1) << 25, std::max<uint64_t>(uint64_t(1) << 20, next_pow2(uint64_t(M) * 64)));
+    auto scratch_bytes = [&](int sreps, int creps) {
+      return uint64_t(sreps) * D * seg_bytes + sort_hist_entries(M, sreps * D) * 4 +
+             uint64_t(creps) * D * (C + 1) * (4 + 4 + 8) + new_cap * (8 + 32) + hs_cap * 12;
+    };
+    auto total_bytes = [&](int LL) {
+      return fixed + scratch_bytes(std::min(sort_reps, LL), std::min(chunk, LL)) +
+             uint64_t(LL) * per_rep;
+    };
+    if (total_bytes(1) > limit)
+      return fail(h, MOMENTI_ERR_MEMORY, "hash_all: memory limit below one repetition");
+    int L = L_user;
+    if (total_bytes(L) > limit) {
+      int lo = 1, hi = L;          // largest L that fits
+      while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (total_bytes(mid) <= limit) lo = mid;
+        else hi = mid - 1;
+      }
+      L = lo;
+    }
+    sort_reps = std::max(1, std::min(sort_reps, L));
+    chunk = std::max(1, std::min(chunk, L));
+    h->chunk_reps = chunk;
+    h->sort_reps = sort_reps;
+
+    ix.n = n;
+    ix.M = M;
+    ix.D = D;
+    ix.w = w;
+    ix.K = K;
+    ix.L = L;
+    ix.Wp = Wp;
+    ix.excl = p.excl < 0 ? w / 2 : p.excl;
+    ix.has_lo = dtype == MOMENTI_F64;
+    const int N = L * kRepStride;
+    CK(dalloc(h, &ix.xs_hi, size_t(D) * n));
+    if (ix.has_lo) CK(dalloc(h, &ix.xs_lo, size_t(D) * n));
+    CK(dalloc(h, &ix.mu, size_t(D) * M));
+    CK(dalloc(h, &ix.sig, size_t(D) * M));
+    CK(dalloc(h, &ix.mu_hi, size_t(D) * M));
+    CK(dalloc(h, &ix.mu_lo, size_t(D) * M));
+    CK(dalloc(h, &ix.inv_sig, size_t(D) * M));
+    CK(dalloc(h, &ix.a16, size_t(D) * N * Wp));
+    CK(dalloc(h, &ix.a32, size_t(D) * N * Wp));
+    CK(dalloc(h, &ix.boff, size_t(D) * N));
+    CK(dalloc(h, &ix.keys, size_t(L) * M * D));
+    CK(dalloc(h, &ix.order, size_t(L) * M * D));
+    CK(dalloc(h, &ix.lcp, size_t(L) * M * D));
+    h->draw_a = nullptr;
+    h->draw_u = nullptr;
+    const size_t na = h->user_a.empty() ? size_t(D) * L * K * w : h->user_a.size();
+    const size_t nu = h->user_a.empty() ? size_t(D) * L * K : h->user_u.size();
+    CK(dalloc(h, &h->draw_a, na));
+    CK(dalloc(h, &h->draw_u, nu));
+    h->flag_cap = uint32_t(std::min<uint64_t>(uint64_t(1) << 24,
+                                              std::max<uint64_t>(uint64_t(1) << 16, uint64_t(D) * M * N / 100)));
+    CK(dalloc(h, &h->flags, size_t(h->flag_cap)));
+    CK(dalloc(h, &h->small, 16));
+    // index sort scratch
+    SortScratch& sc = h->sort;
+    const int64_t sent = int64_t(sort_reps) * D * M;
+    CK(dalloc(h, &sc.k0, size_t(sent)));
+    CK(dalloc(h, &sc.k1, size_t(sent)));
+    CK(dalloc(h, &sc.v0, size_t(sent)));
+    CK(dalloc(h, &sc.v1, size_t(sent)));
+    sc.hist_entries = sort_hist_entries(M, sort_reps * D);
+    CK(dalloc(h, &sc.hist, size_t(sc.hist_entries)));
+    sc.cap_entries = sent;
+    // traversal scratch
+    CollideScratch& cs = h->cs;
+    cs.seg_cap = int64_t(chunk) * D;
+    cs.chunk_cap = C;
+    const int64_t E = cs.seg_cap * C;
+    CK(dalloc(h, &cs.cagg, size_t(E)));
+    CK(dalloc(h, &cs.cbs, size_t(E)));
+    CK(dalloc(h, &cs.ntile, size_t(E + 1)));
+    CK(dalloc(h, &cs.scan_tmp, size_t(E / 1024 + 2)));
+    CK(dalloc(h, &cs.new_slots, size_t(new_cap)));
+    CK(dalloc(h, &cs.counters, 4));
+    cs.new_cap = new_cap;
+    CK(dalloc(h, &h->rec_dev, size_t(new_cap)));
+    HashSet& hs = h->hs;
+    hs.cap = hs_cap;
+    CK(dalloc(h, &hs.keys, size_t(hs_cap)));
+    CK(dalloc(h, &hs.tag, size_t(hs_cap)));
+    CK(cudaMallocHost(&h->rec_host, new_cap * sizeof(PairRec)));
+    CK(cudaMallocHost(&h->cnt_host, 4 * sizeof(unsigned long long)));
+    h->built_gen = h->hp_gen;
+  }
+  const int L = ix.L, Wp = ix.Wp, N = L * kRepStride;
+  (void)Wp;
+
+  Timer t_all(s);
+  // ---- series: device split into float32 hi (+ lo for float64 input) ----
+  const void* src = series;
+  void* staging = nullptr;
+  if (!on_device) {
+    CK(cudaMallocAsync(&staging, size_t(D) * n * elem, s));
+    CK(cudaMemcpy2DAsync(staging, n * elem, series, ld * elem, n * elem, D, cudaMemcpyHostToDevice, s));
+    src = staging;
+    ld = n;
+  }
+  CK(launch_split_series(src, dtype, n, D, ld, ix.xs_hi, ix.xs_lo, s));
+  if (staging) CK(cudaFreeAsync(staging, s));
+  CK(launch_window_stats(ix, s));
+
+  // ---- hash functions ----
+  int L_src = L;
+  if (!h->user_a.empty()) {
+    L_src = h->user_L;
+    CK(cudaMemcpyAsync(h->draw_a, h->user_a.data(), h->user_a.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->draw_u, h->user_u.data(), h->user_u.size() * 4, cudaMemcpyHostToDevice, s));
+  } else {
+    CK(launch_draw_hash(p.seed, D, L, K, w, h->draw_a, h->draw_u, s));
+  }
+  CK(launch_layout_hash(ix, h->draw_a, L_src, s));
+
+  // ---- r: fixed, or Section 6.1's heuristic ----
+  if (p.r > 0) {
+    ix.r = p.r;
+  } else {
+    float* mm = reinterpret_cast<float*>(h->small);
+    const float init[2] = {INFINITY, -INFINITY};
+    CK(cudaMemcpyAsync(mm, init, 8, cudaMemcpyHostToDevice, s));
+    const int S = int(std::min<int64_t>(M, 4096));
+    CK(launch_r_sample(ix, S, mm, s));
+    float res[2];
+    CK(cudaMemcpyAsync(res, mm, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rr = (double(res[1]) - double(res[0])) / 256.0;
+    ix.r = (rr > 0 && std::isfinite(rr)) ? rr : 1.0;
+  }
+  ix.inv_r = float(1.0 / ix.r);
+  CK(launch_layout_boff(ix, h->draw_u, L_src, s));
+
+  // ---- projections and hashes of all repetitions ----
+  h->used_tc = false;
+  h->n_flagged = 0;
+  if (p.precision == MOMENTI_PREC_F16X2 && tc_supported() &&
+      proj_hash_tc_smem(ix.Wp, ix.has_lo) <= size_t(227) * 1024) {
+    uint32_t* fcount = reinterpret_cast<uint32_t*>(h->small) + 2;
+    int* err = reinterpret_cast<int*>(h->small) + 3;
+    CK(cudaMemsetAsync(fcount, 0, 8, s));
+    CK(launch_proj_hash_tc(ix, 0, L, h->flags, h->flag_cap, fcount, err, s));
+    CK(launch_rehash_fp32(ix, h->flags, fcount, h->flag_cap, s));
+    uint32_t hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hc, fcount, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hc[1]) return fail(h, MOMENTI_ERR_TIMEOUT, "hash_all: tensor-core projection wait timed out");
+    h->n_flagged = hc[0];
+    if (hc[0] > h->flag_cap) CK(launch_proj_hash_fp32(ix, 0, L, s));   // flag list overflowed
+    else h->used_tc = true;
+  } else {
+    CK(launch_proj_hash_fp32(ix, 0, L, s));
+  }
+  (void)N;
+
+  // ---- index: sort every (j, f) ----
+  Timer t_sort(s);
+  for (int j0 = 0; j0 < L; j0 += h->sort_reps)
+    CK(launch_sort_reps(ix, j0, std::min(L, j0 + h->sort_reps), h->sort, s));
+  h->t_sort_ms = t_sort.stop();
+  h->t_hash_ms = t_all.stop();
+  CK(cudaGetLastError());
+  h->ready = true;
+  return MOMENTI_OK;
+}
+
+int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk before hash_all");
+  Index& ix = h->ix;
+  const auto& p = h->p;
+  cudaStream_t s = h->stream;
+  const int K = ix.K, L = ix.L, d = p.d, k = p.k;
+  const double delta = p.delta_mode == MOMENTI_DELTA_ALL_K ? p.delta / k : p.delta;
+  momenti_stats st{};
+  st.K = K;
+  st.L = L;
+  st.r = ix.r;
+  st.n_windows = ix.M;
+
+  Pool pool;
+  pool.k = k;
+  pool.eps = ix.excl;
+  CK(launch_hashset_clear(h->hs, s));
+  Timer t_trav(s);
+  int stop_i = 0, stop_j = 0;
+  double fb = 1.0;
+  std::vector<std::vector<PairRec>> by_rep(h->chunk_reps);
+  for (int i = K; i >= 1 && !stop_i; --i) {
+    for (int j0 = 0; j0 < L && !stop_i; j0 += h->chunk_reps) {
+      const int j1 = std::min(L, j0 + h->chunk_reps);
+      for (int retry = 0; retry < 4; ++retry) {
+        CK(cudaMemsetAsync(h->cs.counters, 0, 4 * sizeof(unsigned long long), s));
+        CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
+        CK(cudaMemcpyAsync(h->cnt_host, h->cs.counters, 4 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->cnt_host[2] & 1ull) {
+          // set full: start a fresh set and redo the chunk; pairs seen
+          // before come back as new and the host pool drops repeats
+          CK(launch_hashset_clear(h->hs, s));
+          continue;
+        }
+        break;
+      }
+      if (h->cnt_host[2] & 1ull) return fail(h, MOMENTI_ERR_OVERFLOW, "topk: pair set overflow");
+      st.n_candidates += int64_t(h->cnt_host[1]);
+      uint64_t nnew = h->cnt_host[0];
+      if (nnew > h->cs.new_cap) {
+        // grow the append list and collect the chunk's new pairs by tag
+        uint64_t cap = next_pow2(nnew);
+        uint64_t* slots = nullptr;
+        PairRec* rec = nullptr;
+        CK(dalloc(h, &slots, size_t(cap)));
+        CK(dalloc(h, &rec, size_t(cap)));
+        PairRec* rh = nullptr;
+        CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
+        cudaFreeHost(h->rec_host);
+        h->rec_host = rh;
+        h->cs.new_slots = slots;
+        h->cs.new_cap = cap;
+        h->rec_dev = rec;
+        CK(cudaMemsetAsync(h->cs.counters, 0, 8, s));
+        const uint32_t base = uint32_t((K - i) * L);
+        CK(launch_collect_tag(h->hs, base + j0, base + j1, slots, cap, h->cs.counters, s));
+      }
+      CK(launch_verify_new(ix, d, h->hs, h->cs, h->rec_dev, h->cs.new_cap, s, i));
+      if (nnew) {
+        CK(cudaMemcpyAsync(h->rec_host, h->rec_dev, nnew * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
+      st.n_verified += int64_t(nnew);
+      ++st.n_chunks;
+      for (auto& v : by_rep) v.clear();
+      for (uint64_t q = 0; q < nnew; ++q) {
+        int jj = h->rec_host[q].j - j0;
+        if (jj < 0 || jj >= j1 - j0) return fail(h, MOMENTI_ERR_CUDA, "topk: bad repetition tag");
+        by_rep[jj].push_back(h->rec_host[q]);
+      }
+      for (int j = j0; j < j1; ++j) {
+        auto& v = by_rep[j - j0];
+        if (!v.empty()) pool.add(v.data(), v.size());
+        if (pool.valid()) {
+          fb = failure_bound(pool.top.back().dmax, i, j + 1, K, L, d, ix.r);
+          if (fb <= delta) {
+            stop_i = i;
+            stop_j = j + 1;
+            break;
+          }
+        }
+      }
+    }
+  }
+  st.t_traverse_ms = t_trav.stop();
+  st.n_pool = int64_t(pool.items.size());
+  double max_err = 0;
+  int rc;
+  if (stop_i) {
+    st.stop_i = stop_i;
+    st.stop_j = stop_j;
+    // every pool pair at or below the k-th, for the float64 re-check
+    std::vector<PoolEntry> cand;
+    const double lim = pool.kth() * (1.0 + 1e-3) + 1e-5;
+    for (auto& c : pool.items)
+      if (c.dd <= lim) cand.push_back(c);
+    rc = finalize(h, cand, out, n_out, fb, &max_err);
+  } else {
+    st.fallback = 1;
+    Timer t_fb(s);
+    double tau0 = (int(pool.top.size()) == k) ? pool.kth() * 1.05 + 1e-6 : 0.0;
+    rc = exact_path(h, tau0, out, n_out, &max_err);
+    st.t_fallback_ms = t_fb.stop();
+  }
+  if (rc != MOMENTI_OK) return rc;
+  // float32 traversal distances vs the float64 result
+  for (int q = 0; q < *n_out; ++q) {
+    uint64_t key = (uint64_t(out[q].a) << 32) | uint64_t(out[q].b);
+    for (auto& c : pool.items)
+      if (((uint64_t(c.a) << 32) | c.b) == key && out[q].dist_d > 0)
+        max_err = std::max(max_err, std::fabs(c.dd - out[q].dist_d) / out[q].dist_d);
+  }
+  st.max_rel_err_fp32 = max_err;
+  st.t_hash_ms = h->t_hash_ms;
+  st.t_sort_ms = h->t_sort_ms;
+  st.device_bytes = h->device_bytes;
+  st.precision_used = h->used_tc ? MOMENTI_PREC_F16X2 : MOMENTI_PREC_FP32;
+  st.n_rehashed = h->n_flagged;
+  if (stats) *stats = st;
+  return MOMENTI_OK;
+}
+
+int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk_exact: NULL output");
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk_exact before hash_all");
+  double err = 0;
+  return exact_path(h, 0.0, out, n_out, &err);
+}
+
+int momenti_verify(momenti_handle* h, const int64_t* pairs, int64_t m, double* per_dim,
+                   double* dist_d, uint64_t* dims_mask, int32_t fp64) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "verify before hash_all");
+  if (m < 0 || (m > 0 && !pairs)) return fail(h, MOMENTI_ERR_ARG, "verify: bad pairs");
+  if (m == 0) return MOMENTI_OK;
+  const Index& ix = h->ix;
+  std::vector<uint64_t> pk(m);
+  for (int64_t q = 0; q < m; ++q) {
+    int64_t a = pairs[2 * q], b = pairs[2 * q + 1];
+    if (a < 0 || b < 0 || a >= ix.M || b >= ix.M) return fail(h, MOMENTI_ERR_ARG, "verify: index outside [0, M)");
+    pk[q] = (uint64_t(a) << 32) | uint64_t(b);
+  }
+  cudaStream_t s = h->stream;
+  uint64_t* dp = nullptr;
+  double *dpd = nullptr, *ddd = nullptr;
+  uint64_t* dmask = nullptr;
+  CK(cudaMallocAsync(&dp, m * 8, s));
+  CK(cudaMallocAsync(&dpd, m * ix.D * 8, s));
+  CK(cudaMallocAsync(&ddd, m * 8, s));
+  CK(cudaMallocAsync(&dmask, m * 8, s));
+  CK(cudaMemcpyAsync(dp, pk.data(), m * 8, cudaMemcpyHostToDevice, s));
+  CK(launch_verify_pairs(ix, h->p.d, dp, m, fp64, dpd, ddd, dmask, s));
+  if (per_dim) CK(cudaMemcpyAsync(per_dim, dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, s));
+  if (dist_d) CK(cudaMemcpyAsync(dist_d, ddd, m * 8, cudaMemcpyDeviceToHost, s));
+  if (dims_mask) CK(cudaMemcpyAsync(dims_mask, dmask, m * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(dp, s));
+  CK(cudaFreeAsync(dpd, s));
+  CK(cudaFreeAsync(ddd, s));
+  CK(cudaFreeAsync(dmask, s));
+  CK(cudaStreamSynchronize(s));
+  return MOMENTI_OK;
+}
+
+int momenti_get_info(const momenti_handle* h, int64_t* M, int32_t* D, int32_t* L, int32_t* K,
+                     double* r) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return MOMENTI_ERR_STATE;
+  if (M) *M = h->ix.M;
+  if (D) *D = h->ix.D;
+  if (L) *L = h->ix.L;
+  if (K) *K = h->ix.K;
+  if (r) *r = h->ix.r;
+  return MOMENTI_OK;
+}
+
+int momenti_get_window_stats(momenti_handle* h, double* mu, double* sigma) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "get_window_stats before hash_all");
+  const size_t cnt = size_t(h->ix.D) * h->ix.M;
+  if (mu) CK(cudaMemcpyAsync(mu, h->ix.mu, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (sigma) CK(cudaMemcpyAsync(sigma, h->ix.sig, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MOMENTI_OK;
+}
+
+int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "get_keys before hash_all");
+  if (!keys || j < 0 || j >= h->ix.L) return fail(h, MOMENTI_ERR_ARG, "get_keys: bad arguments");
+  const size_t cnt = size_t(h->ix.D) * h->ix.M;
+  CK(cudaMemcpyAsync(keys, h->ix.keys + size_t(j) * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MOMENTI_OK;
+}
+
+int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, uint8_t* lcp) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "get_index before hash_all");
+  if (j < 0 || j >= h->ix.L || f < 0 || f >= h->ix.D) return fail(h, MOMENTI_ERR_ARG, "get_index: bad (j, f)");
+  const size_t off = (size_t(j) * h->ix.D + f) * h->ix.M;
+  if (order) CK(cudaMemcpyAsync(order, h->ix.order + off, h->ix.M * 4, cudaMemcpyDeviceToHost, h->stream));
+  if (lcp) CK(cudaMemcpyAsync(lcp, h->ix.lcp + off, h->ix.M, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MOMENTI_OK;
+}
+
+int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int64_t cap,
+                    int64_t* count) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "collide before hash_all");
+  if (i < 1 || i > h->ix.K || j < 0 || j >= h->ix.L || cap < 0 || !count || (cap > 0 && !pairs))
+    return fail(h, MOMENTI_ERR_ARG, "collide: bad arguments");
+  cudaStream_t s = h->stream;
+  uint64_t* dout = nullptr;
+  const uint64_t dcap = uint64_t(std::max<int64_t>(cap, 1));
+  CK(cudaMallocAsync(&dout, dcap * 8, s));
+  CK(cudaMemsetAsync(h->cs.counters, 0, 4 * sizeof(unsigned long long), s));
+  CK(launch_collide(h->ix, i, j, j + 1, h->p.d, h->hs, h->cs, 1, dout, uint64_t(cap), s));
+  unsigned long long c = 0;
+  CK(cudaMemcpyAsync(&c, h->cs.counters, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t got = std::min<int64_t>(int64_t(c), cap);
+  std::vector<uint64_t> tmp(got);
+  if (got) CK(cudaMemcpyAsync(tmp.data(), dout, got * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(dout, s));
+  CK(cudaStreamSynchronize(s));
+  for (int64_t q = 0; q < got; ++q) {
+    pairs[2 * q] = int64_t(tmp[q] >> 32);
+    pairs[2 * q + 1] = int64_t(tmp[q] & 0xffffffffu);
+  }
+  *count = int64_t(c);
+  return MOMENTI_OK;
+}
+
+}  // extern "C"

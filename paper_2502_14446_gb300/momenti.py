@@ -1,0 +1,276 @@
+"""Thin Python binding of the C ABI in ``include/momenti.h`` (ctypes).
+
+Argument marshalling only: every step of the search runs in the CUDA
+library ``libmomenti.so``.  The module raises at import if the library is
+missing: there is no CPU fallback.  Series may be numpy arrays (host) or
+CUDA torch tensors (device pointers are passed through, with the tensor's
+current stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmomenti.so")
+
+OK = 0
+ERR_ARG, ERR_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_STATE = -1, -2, -3, -4, -5, -6
+F32, F64 = 0, 1
+PREC_FP32, PREC_F16X2 = 0, 1
+DELTA_PER_MOTIF, DELTA_ALL_K = 0, 1
+MAX_D, MAX_K = 64, 8
+
+# every symbol include/momenti.h declares
+EXPORTS = (
+    "momenti_default_params", "momenti_create", "momenti_destroy", "momenti_last_error",
+    "momenti_set_hash_params", "momenti_hash_all", "momenti_topk", "momenti_topk_exact",
+    "momenti_verify", "momenti_get_info", "momenti_get_window_stats", "momenti_get_keys",
+    "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
+    "momenti_kernel_time",
+)
+
+
+class momenti_params(C.Structure):
+    _fields_ = [("w", C.c_int32), ("d", C.c_int32), ("k", C.c_int32), ("delta", C.c_double),
+                ("mem_limit", C.c_uint64), ("K", C.c_int32), ("L", C.c_int32), ("r", C.c_double),
+                ("excl", C.c_int32), ("seed", C.c_uint64), ("precision", C.c_int32),
+                ("delta_mode", C.c_int32)]
+
+
+class momenti_motif(C.Structure):
+    _fields_ = [("a", C.c_int64), ("b", C.c_int64), ("dist_d", C.c_double),
+                ("dist_max", C.c_double), ("fail_bound", C.c_double), ("dims_mask", C.c_uint64)]
+
+
+class momenti_stats(C.Structure):
+    _fields_ = [("stop_i", C.c_int32), ("stop_j", C.c_int32), ("K", C.c_int32), ("L", C.c_int32),
+                ("r", C.c_double), ("n_windows", C.c_int64), ("n_candidates", C.c_int64),
+                ("n_verified", C.c_int64), ("n_pool", C.c_int64), ("fallback", C.c_int32),
+                ("n_chunks", C.c_int32), ("t_hash_ms", C.c_double), ("t_sort_ms", C.c_double),
+                ("t_traverse_ms", C.c_double), ("t_fallback_ms", C.c_double),
+                ("max_rel_err_fp32", C.c_double), ("device_bytes", C.c_uint64),
+                ("precision_used", C.c_int32), ("reserved", C.c_int32),
+                ("n_rehashed", C.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "paper_2502_14446_gb300.build_ext.build() (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    vp = C.c_void_p
+    sig = {
+        "momenti_default_params": (C.c_int, [P(momenti_params)]),
+        "momenti_create": (C.c_int, [P(vp), P(momenti_params)]),
+        "momenti_destroy": (None, [vp]),
+        "momenti_last_error": (C.c_char_p, [vp]),
+        "momenti_set_hash_params": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                              vp, vp]),
+        "momenti_hash_all": (C.c_int, [vp, vp, C.c_int32, C.c_int64, C.c_int32, C.c_int64,
+                                       C.c_int32, vp]),
+        "momenti_topk": (C.c_int, [vp, P(momenti_motif), P(C.c_int32), P(momenti_stats)]),
+        "momenti_topk_exact": (C.c_int, [vp, P(momenti_motif), P(C.c_int32)]),
+        "momenti_verify": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, C.c_int32]),
+        "momenti_get_info": (C.c_int, [vp, P(C.c_int64), P(C.c_int32), P(C.c_int32),
+                                       P(C.c_int32), P(C.c_double)]),
+        "momenti_get_window_stats": (C.c_int, [vp, vp, vp]),
+        "momenti_get_keys": (C.c_int, [vp, C.c_int32, vp]),
+        "momenti_get_index": (C.c_int, [vp, C.c_int32, C.c_int32, vp, vp]),
+        "momenti_collide": (C.c_int, [vp, C.c_int32, C.c_int32, vp, C.c_int64, P(C.c_int64)]),
+        "momenti_launch_count": (C.c_uint64, []),
+        "momenti_time_kernel": (C.c_int, [C.c_char_p]),
+        "momenti_kernel_time": (C.c_int, [P(C.c_double), P(C.c_uint64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class MomentiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"momenti error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_params(**kw) -> momenti_params:
+    p = momenti_params()
+    lib.momenti_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process."""
+    return int(lib.momenti_launch_count())
+
+
+def time_kernel(name: str | None):
+    """Time every launch of one kernel (CUDA events on its stream)."""
+    lib.momenti_time_kernel(name.encode() if name else None)
+
+
+def kernel_time():
+    """(total ms, launches) of the timed kernel since time_kernel()."""
+    ms, n = C.c_double(), C.c_uint64()
+    rc = lib.momenti_kernel_time(C.byref(ms), C.byref(n))
+    if rc != OK:
+        raise MomentiError(rc, "momenti_kernel_time")
+    return ms.value, int(n.value)
+
+
+class Momenti:
+    """One search handle: ``hash_all`` builds the index, ``topk`` searches."""
+
+    def __init__(self, params: momenti_params | None = None, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        if params is not None:
+            for k, v in kw.items():
+                setattr(self.params, k, v)
+        h = C.c_void_p()
+        rc = lib.momenti_create(C.byref(h), C.byref(self.params))
+        if rc != OK:
+            raise MomentiError(rc, "momenti_create: invalid parameters")
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if self.h:
+            lib.momenti_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = lib.momenti_last_error(self.h)
+            raise MomentiError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_hash_params(self, A: np.ndarray, U: np.ndarray):
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        U = np.ascontiguousarray(U, dtype=np.float32)
+        D, L, K, w = A.shape
+        assert U.shape == (D, L, K)
+        self._check(lib.momenti_set_hash_params(self.h, D, L, K, w, _ptr(A), _ptr(U)),
+                    "momenti_set_hash_params")
+
+    def hash_all(self, series, stream=None):
+        """series: (D, n) numpy array (host) or CUDA torch tensor (device)."""
+        if hasattr(series, "is_cuda") and series.is_cuda:
+            import torch
+            assert series.dim() == 2 and series.stride(1) == 1
+            dtype = F64 if series.dtype == torch.float64 else F32
+            assert series.dtype in (torch.float32, torch.float64)
+            D, n = series.shape
+            if stream is None:
+                stream = torch.cuda.current_stream(series.device).cuda_stream
+            self._keep = series
+            rc = lib.momenti_hash_all(self.h, C.c_void_p(series.data_ptr()), dtype, n, D,
+                                      series.stride(0), 1, C.c_void_p(stream))
+        else:
+            arr = np.asarray(series)
+            if arr.dtype not in (np.float32, np.float64):
+                arr = arr.astype(np.float64)
+            arr = np.ascontiguousarray(arr)
+            D, n = arr.shape
+            dtype = F64 if arr.dtype == np.float64 else F32
+            rc = lib.momenti_hash_all(self.h, _ptr(arr), dtype, n, D, n, 0,
+                                      C.c_void_p(stream or 0))
+        self._check(rc, "momenti_hash_all")
+
+    def info(self):
+        M, D, L, K, r = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        self._check(lib.momenti_get_info(self.h, C.byref(M), C.byref(D), C.byref(L), C.byref(K),
+                                         C.byref(r)), "momenti_get_info")
+        return {"M": M.value, "D": D.value, "L": L.value, "K": K.value, "r": r.value}
+
+    @staticmethod
+    def _motifs(buf, n):
+        out = []
+        for q in range(n):
+            m = buf[q]
+            dims = tuple(f for f in range(64) if m.dims_mask >> f & 1)
+            out.append({"a": m.a, "b": m.b, "dist_d": m.dist_d, "dist_max": m.dist_max,
+                        "fail_bound": m.fail_bound, "dims": dims})
+        return out
+
+    def topk(self):
+        k = self.params.k
+        buf = (momenti_motif * k)()
+        n = C.c_int32()
+        st = momenti_stats()
+        self._check(lib.momenti_topk(self.h, buf, C.byref(n), C.byref(st)), "momenti_topk")
+        stats = {name: getattr(st, name) for name, _ in momenti_stats._fields_}
+        return self._motifs(buf, n.value), stats
+
+    def topk_exact(self):
+        k = self.params.k
+        buf = (momenti_motif * k)()
+        n = C.c_int32()
+        self._check(lib.momenti_topk_exact(self.h, buf, C.byref(n)), "momenti_topk_exact")
+        return self._motifs(buf, n.value)
+
+    def verify(self, pairs, fp64: bool = False):
+        pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        m = pairs.shape[0]
+        D = self.info()["D"]
+        per = np.zeros((m, D))
+        dd = np.zeros(m)
+        mask = np.zeros(m, dtype=np.uint64)
+        self._check(lib.momenti_verify(self.h, _ptr(pairs), m, _ptr(per), _ptr(dd), _ptr(mask),
+                                       1 if fp64 else 0), "momenti_verify")
+        return per, dd, mask
+
+    def window_stats(self):
+        inf = self.info()
+        mu = np.zeros((inf["D"], inf["M"]))
+        sd = np.zeros((inf["D"], inf["M"]))
+        self._check(lib.momenti_get_window_stats(self.h, _ptr(mu), _ptr(sd)),
+                    "momenti_get_window_stats")
+        return mu, sd
+
+    def keys(self, j: int) -> np.ndarray:
+        inf = self.info()
+        out = np.zeros((inf["M"], inf["D"]), dtype=np.uint64)
+        self._check(lib.momenti_get_keys(self.h, j, _ptr(out)), "momenti_get_keys")
+        return out
+
+    def index(self, j: int, f: int):
+        M = self.info()["M"]
+        order = np.zeros(M, dtype=np.uint32)
+        lcp = np.zeros(M, dtype=np.uint8)
+        self._check(lib.momenti_get_index(self.h, j, f, _ptr(order), _ptr(lcp)),
+                    "momenti_get_index")
+        return order, lcp
+
+    def collide(self, i: int, j: int, cap: int = 1 << 22) -> np.ndarray:
+        out = np.zeros((cap, 2), dtype=np.int64)
+        cnt = C.c_int64()
+        self._check(lib.momenti_collide(self.h, i, j, _ptr(out), cap, C.byref(cnt)),
+                    "momenti_collide")
+        if cnt.value > cap:
+            return self.collide(i, j, int(cnt.value))
+        return out[:cnt.value]

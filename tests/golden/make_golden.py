@@ -1,0 +1,48 @@
+"""Writes the stored expected values of the parity tests.
+
+Calls only the CPU oracle (oracle/momenti_oracle.py) on the seeded
+synthetic inputs of paper_2502_14446_gb300.synth.  Each output file is a
+small JSON record: the workload name and seed, the exact top-k motifs of
+Definition (top-k multidimensional motifs, Section 3.1) as
+[dist_d, a, b, dims, dist_max], and the oracle's wall time.
+
+Usage: python tests/golden/make_golden.py plain_small plain_fp32
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import momenti_oracle as O  # noqa: E402
+from paper_2502_14446_gb300 import synth  # noqa: E402
+
+OUT = os.path.dirname(os.path.abspath(__file__))
+
+# first threshold for the doubling search of exact_topk_auto; any value
+# gives the same answer, a good one only saves passes
+TAU0 = {"plain_small": None, "plain_fp32": 8.0}
+
+
+def make(name: str, seed: int = 0):
+    wl = getattr(synth, name)(seed)
+    t0 = time.time()
+    res = O.exact_topk_auto(wl.series, wl.w, wl.d, wl.k, tau0=TAU0.get(name), block=256)
+    dt = time.time() - t0
+    rec = {
+        "workload": name, "seed": seed, "D": wl.D, "n": wl.n, "w": wl.w, "d": wl.d, "k": wl.k,
+        "planted": [[a, b, list(dims)] for a, b, dims in wl.planted],
+        "motifs": [[m[0], m[1], m[2], list(m[3]), m[4]] for m in res],
+        "oracle_seconds": dt,
+    }
+    path = os.path.join(OUT, f"exact_{name}_seed{seed}.json")
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(path, f"{dt:.1f}s")
+
+
+if __name__ == "__main__":
+    for nm in sys.argv[1:] or ["plain_small"]:
+        make(nm)

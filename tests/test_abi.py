@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every symbol include/momenti.h
+declares; argument checks that need no GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mom():
+    from paper_2502_14446_gb300 import build_ext
+    build_ext.build()
+    from paper_2502_14446_gb300 import momenti
+    return momenti
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "momenti.h")).read()
+    return sorted(set(re.findall(r"\b(momenti_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("momenti_create", "momenti_hash_all", "momenti_verify", "momenti_topk"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(mom):
+    for name in declared_symbols():
+        assert hasattr(mom.lib, name), name
+    assert sorted(mom.EXPORTS) == declared_symbols()
+
+
+def test_struct_layouts(mom):
+    assert C.sizeof(mom.momenti_motif) == 48
+    assert C.sizeof(mom.momenti_params) == 72
+
+
+def test_default_params_are_the_papers(mom):
+    p = mom.default_params()
+    assert (p.K, p.L, p.delta, p.r) == (8, 200, 0.01, 0.0)
+    assert p.excl == -1
+
+
+@pytest.mark.parametrize("bad", [dict(w=1), dict(d=0), dict(k=0), dict(delta=0.0),
+                                 dict(delta=1.0), dict(K=9), dict(K=0), dict(L=-1),
+                                 dict(precision=7), dict(delta_mode=3)])
+def test_create_rejects_bad_parameters(mom, bad):
+    p = mom.default_params(**bad)
+    h = C.c_void_p()
+    assert mom.lib.momenti_create(C.byref(h), C.byref(p)) == mom.ERR_ARG
+
+
+def test_calls_out_of_order(mom):
+    p = mom.default_params(w=10, d=1, k=1)
+    h = C.c_void_p()
+    assert mom.lib.momenti_create(C.byref(h), C.byref(p)) == mom.OK
+    out = (mom.momenti_motif * 1)()
+    n = C.c_int32()
+    assert mom.lib.momenti_topk(h, out, C.byref(n), None) == mom.ERR_STATE
+    assert mom.lib.momenti_verify(h, None, 0, None, None, None, 0) == mom.ERR_STATE
+    assert mom.lib.momenti_set_hash_params(h, 1, 1, 8, 11, None, None) == mom.ERR_ARG
+    assert b"set_hash_params" in mom.lib.momenti_last_error(h)
+    assert mom.lib.momenti_hash_all(h, None, 0, 100, 1, 100, 0, None) == mom.ERR_ARG
+    mom.lib.momenti_destroy(h)
+    mom.lib.momenti_destroy(None)
