@@ -104,39 +104,58 @@ cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch&
                              cudaStream_t s);
 
 // ---- k_collide.cu -------------------------------------------------------
+constexpr uint64_t kSetEmpty = ~0ull;
+constexpr int kSetMaxProbe = 512;
+// splitmix64 finalizer (Steele, Lea, Flood 2014): slot hash of a pair key
+__device__ __forceinline__ uint64_t set_hash(uint64_t x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+// Device set of close pairs verified so far (open addressing, keys only):
+// a cache that spares re-verifying them; cleared by the host when half full.
 struct HashSet {
-  uint64_t* keys = nullptr;   // EMPTY = ~0ull
-  uint32_t* tag = nullptr;    // smallest repetition of first collision
+  uint64_t* keys = nullptr;   // a << 32 | b, EMPTY = ~0ull
   uint64_t cap = 0;           // power of two
 };
+// A candidate of Algorithm 1, line 14: pair (a < b) with W >= d in repetition j.
+struct Event {
+  uint32_t a, b;
+  int32_t j;
+  uint32_t pad;
+};
 struct CollideScratch {
-  int32_t* cagg = nullptr;     // [segs][M/32+1] last bucket start in chunk, or -1
-  int32_t* cbs = nullptr;      // [segs][M/32+1] bucket start of the chunk's first position
+  int32_t* cagg = nullptr;     // [segs][chunks] last bucket start in chunk, or -1
+  int32_t* cbs = nullptr;      // [segs][chunks] bucket start of the chunk's first rank
   uint64_t* ntile = nullptr;   // [segs*chunks + 1] tiles per chunk, then exclusive scan
-  uint64_t* scan_tmp = nullptr;   // [segs*chunks / 1024 + 1]
-  uint64_t* new_slots = nullptr;  // hash-set slots of new pairs
-  unsigned long long* counters = nullptr;  // [0] new (or plain) pairs, [1] candidates, [2] flags
-  uint64_t new_cap = 0;
+  uint64_t* scan_tmp = nullptr;   // [segs*chunks / 1024 + 2]
+  Event* events = nullptr;
+  uint64_t ev_cap = 0;
+  // [0] events (or plain pairs), [1] close records, [2] set inserts,
+  // [3] verified pairs dropped at or above the threshold
+  unsigned long long* counters = nullptr;
   int64_t seg_cap = 0;            // segments the arrays can hold
   int64_t chunk_cap = 0;          // chunks per segment
 };
-// Collision counting at prefix length i for repetitions [j0, j1): inserts
-// every non-trivial pair with W >= d (first colliding dim, not already
-// colliding at length i+1) into the set, appending new ones to new_slots.
-// mode_plain != 0: no level / set de-duplication; pairs go to out_pairs.
+// Collision counting at prefix length i for repetitions [j0, j1): every
+// non-trivial pair with W >= d (handled from its first colliding dim, not
+// already a candidate at length i+1 in the same repetition, not yet in the
+// set) becomes an event.  mode_plain != 0: every such pair once, without
+// the level and set checks, to out_pairs (a << 32 | b).
 cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const HashSet& hs,
                            const CollideScratch& cs, int mode_plain, uint64_t* out_pairs,
                            uint64_t out_cap, cudaStream_t s);
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s);
-// Slots whose tag lies in [t0, t1) (the new pairs of a chunk, when the
-// append list overflowed).
-cudaError_t launch_collect_tag(const HashSet& hs, uint32_t t0, uint32_t t1, uint64_t* slots,
-                               uint64_t cap, unsigned long long* count, cudaStream_t s);
 
 // ---- k_verify.cu --------------------------------------------------------
-// Verify the new pairs of the set: records to rec (count = counters[0]).
-cudaError_t launch_verify_new(const Index& ix, int d, const HashSet& hs, const CollideScratch& cs,
-                              PairRec* rec, uint64_t rec_cap, cudaStream_t s, int i);
+// Verifies every event of the chunk: pairs with dist_d < tau are written to
+// rec (count counters[1], may exceed rec_cap) and offered to the set.
+cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
+                                 const CollideScratch& cs, float tau, PairRec* rec,
+                                 uint64_t rec_cap, cudaStream_t s);
 // Verify explicit pairs (a,b) packed as a << 32 | b; per_dim optional [m][D].
 cudaError_t launch_verify_pairs(const Index& ix, int d, const uint64_t* pairs, int64_t m,
                                 int fp64, double* per_dim, double* dist_d, uint64_t* dims,

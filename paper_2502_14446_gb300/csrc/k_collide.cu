@@ -24,18 +24,8 @@ namespace momenti {
 
 namespace {
 
-constexpr uint64_t kEmpty = ~0ull;
-constexpr int kMaxProbe = 512;
-
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
-  // splitmix64 finalizer (Steele, Lea, Flood 2014)
-  x ^= x >> 30;
-  x *= 0xbf58476d1ce4e5b9ull;
-  x ^= x >> 27;
-  x *= 0x94d049bb133111ebull;
-  x ^= x >> 31;
-  return x;
-}
+constexpr uint64_t kEmpty = kSetEmpty;
+constexpr int kMaxProbe = kSetMaxProbe;
 
 struct Seg {
   int64_t M;
@@ -48,7 +38,7 @@ struct Seg {
 
 // One warp per (segment, chunk): the last bucket start in the chunk (or -1)
 // and whether any rank of the chunk continues the bucket of its predecessor.
-__global__ void k_chunk_agg(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i,
+__global__ void k_chunk_agg(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i, int d,
                             int32_t* __restrict__ cagg, uint64_t* __restrict__ ntile) {
   const int64_t gw = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -60,7 +50,10 @@ __global__ void k_chunk_agg(const uint8_t* __restrict__ lcp, Seg sg, int segs, i
   const bool valid = p < sg.M;
   const int l = valid ? int(L[p]) : 0;
   const unsigned st = __ballot_sync(0xffffffffu, valid && l < i);
-  const unsigned jn = __ballot_sync(0xffffffffu, valid && l >= i);
+  // a pair handled from dim f needs d - 1 more colliding dims above f
+  const int f = seg - (seg / sg.D) * sg.D;
+  const bool useful = f <= sg.D - d;
+  const unsigned jn = __ballot_sync(0xffffffffu, valid && l >= i && useful);
   if (lane == 0) {
     cagg[gw] = st ? int32_t(c * 32 + 31 - __clz(int(st))) : -1;
     ntile[gw] = jn ? 1u : 0u;
@@ -197,27 +190,50 @@ struct CollideArgs {
   const int32_t* cbs;
   const uint64_t* toff;    // exclusive scan, toff[E] = total tiles
   HashSet hs;
-  uint32_t seq_base;       // tag of repetition 0 at this prefix length
-  uint64_t* new_slots;
-  uint64_t new_cap;
-  unsigned long long* counters;   // [0] new / plain count, [1] candidates, [2] flags
+  Event* events;
+  uint64_t ev_cap;
+  unsigned long long* counters;
   uint64_t* out_pairs;
   uint64_t out_cap;
 };
 
+// true if key is in the set (read-only probe)
+__device__ __forceinline__ bool set_contains(const HashSet& hs, uint64_t key) {
+  uint64_t h = set_hash(key) & (hs.cap - 1);
+  for (int probe = 0; probe < kMaxProbe; ++probe) {
+    const uint64_t cur = hs.keys[h];
+    if (cur == key) return true;
+    if (cur == kEmpty) return false;
+    h = (h + 1) & (hs.cap - 1);
+  }
+  return false;
+}
+
+// 0x80 in every byte of x that is zero (exact, no carries across bytes)
+__device__ __forceinline__ uint64_t zero_bytes(uint64_t x) {
+  const uint64_t L7 = 0x7F7F7F7F7F7F7F7Full;
+  const uint64_t y = (x & L7) + L7;
+  return ~(y | x | L7);
+}
+
+// Per warp: the 64 windows of a tile (32 row ranks, 32 column ranks) as
+// byte planes: word (t, g) of a window holds byte t (hash value t) of the
+// keys of dims 8g .. 8g+7, dim 8g+e in byte e.  Equality of the length-i
+// prefixes of all dims of two windows is then i XORs and zero-byte masks.
 template <bool PLAIN>
 __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
   extern __shared__ uint64_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int D = g.sg.D, Dp = D + 1;
-  uint64_t* sk = smem + int64_t(wib) * (64 * Dp + 32);
-  uint32_t* sidx = reinterpret_cast<uint32_t*>(sk + 64 * Dp);
+  const int D = g.sg.D;
+  const int G = (D + 7) >> 3;
+  const bool lvl_dup = !PLAIN && g.i < g.K;
+  const int NP = lvl_dup ? g.i + 1 : g.i;          // planes needed
+  uint64_t* sp = smem + int64_t(wib) * (64 * G * NP + 32);
+  uint32_t* sidx = reinterpret_cast<uint32_t*>(sp + 64 * G * NP);
   const int64_t E = int64_t(g.segs) * g.sg.C;
   const uint64_t T = g.toff[E];
   const uint64_t nw = uint64_t(gridDim.x) * (blockDim.x >> 5);
-  const int sh = 64 - 8 * g.i;
-  const int sh1 = 64 - 8 * (g.i + 1);
-  const bool lvl_dup = !PLAIN && g.i < g.K;
+  const uint32_t lt = (1u << lane) - 1u;
   for (uint64_t t = uint64_t(blockIdx.x) * (blockDim.x >> 5) + wib; t < T; t += nw) {
     // largest e with toff[e] <= t
     int64_t lo = 0, hi = E - 1;
@@ -232,6 +248,7 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
     const int32_t bs0 = g.cbs[e];
     const int64_t c1 = bs0 / 32 + int64_t(t - g.toff[e]);
     const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
+    const int gf = f >> 3, ef = f & 7;
     const int64_t sbase = g.sg.base(seg);
     const uint32_t* O = g.order + sbase;
     const uint8_t* Lc = g.lcp + sbase;
@@ -239,93 +256,101 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
     // bucket start of each column rank
     const int64_t p2 = c2 * 32 + lane;
     const bool v2 = p2 < g.sg.M;
-    int32_t s = (v2 && int(Lc[p2]) < g.i) ? int32_t(p2) : -1;
+    int32_t sv = (v2 && int(Lc[p2]) < g.i) ? int32_t(p2) : -1;
     for (int o = 1; o < 32; o <<= 1) {
-      int32_t u = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s = max(s, u);
+      int32_t u = __shfl_up_sync(0xffffffffu, sv, o);
+      if (lane >= o) sv = max(sv, u);
     }
-    const int32_t bs2 = max(s, bs0);
+    const int32_t bs2 = max(sv, bs0);
     const int64_t p1 = c1 * 32 + lane;
     const bool v1 = p1 < g.sg.M;
+    const uint32_t wa = v1 ? O[p1] : 0u;
+    const uint32_t wbl = v2 ? O[p2] : 0u;
     __syncwarp();
-    sidx[lane] = v1 ? O[p1] : 0u;
-    sidx[32 + lane] = v2 ? O[p2] : 0u;
-    __syncwarp();
-    for (int q = lane; q < 64 * D; q += 32) {
-      const int r = q / D, ff = q - r * D;
-      const bool ok = r < 32 ? (c1 * 32 + r < g.sg.M) : (c2 * 32 + (r - 32) < g.sg.M);
-      sk[r * Dp + ff] = ok ? Kj[int64_t(sidx[r]) * D + ff] : 0ull;
+    sidx[lane] = wa;
+    sidx[32 + lane] = wbl;
+    // byte planes of this lane's two windows
+    for (int half = 0; half < 2; ++half) {
+      const bool ok = half ? v2 : v1;
+      const uint64_t* kw = Kj + int64_t(half ? wbl : wa) * D;
+      const int r = half * 32 + lane;
+      for (int gg = 0; gg < G; ++gg) {
+        uint64_t pw[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) pw[q] = 0;
+        for (int ee = 0; ee < 8; ++ee) {
+          const int ff = gg * 8 + ee;
+          if (ff >= D || !ok) break;
+          const uint64_t key = kw[ff];
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            if (q < NP) pw[q] |= ((key >> (56 - 8 * q)) & 0xFFull) << (8 * ee);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          if (q < NP) sp[(q * G + gg) * 64 + r] = pw[q];
+      }
     }
     __syncwarp();
-    const uint32_t wa = sidx[lane];
-    const uint64_t* ka = sk + lane * Dp;
     for (int cc = 0; cc < 32; ++cc) {
       const int64_t pc = c2 * 32 + cc;
-      if (pc >= g.sg.M) break;
+      if (pc >= g.sg.M) break;                       // warp-uniform
       const int32_t bsc = __shfl_sync(0xffffffffu, bs2, cc);
-      if (!(p1 >= bsc && p1 < pc)) continue;
-      const uint32_t wb = sidx[32 + cc];
-      const uint32_t a = min(wa, wb), b = max(wa, wb);
-      if (int64_t(b) - int64_t(a) <= g.excl) continue;
-      const uint64_t* kb = sk + (32 + cc) * Dp;
-      int W = 0, W1 = 0;
-      bool skip = false;
-      for (int ff = 0; ff < D; ++ff) {
-        const uint64_t x = ka[ff] ^ kb[ff];
-        if ((x >> sh) == 0) {
-          if (ff < f) { skip = true; break; }
-          ++W;
-          if (lvl_dup && (x >> sh1) == 0) ++W1;
-        }
+      bool emit = p1 >= bsc && p1 < pc;
+      uint32_t a = 0, b = 0;
+      if (emit) {
+        const uint32_t wb = sidx[32 + cc];
+        a = min(wa, wb);
+        b = max(wa, wb);
+        emit = int64_t(b) - int64_t(a) > g.excl;
       }
-      if (skip || W < g.d) continue;
-      if (lvl_dup && W1 >= g.d) continue;
+      if (emit) {
+        int W = 0, W1 = 0;
+        bool low = false;
+        for (int gg = 0; gg < G && !low; ++gg) {
+          const int nvalid = min(8, D - gg * 8);
+          uint64_t m = nvalid == 8 ? 0x8080808080808080ull
+                                   : (0x8080808080808080ull & ((1ull << (8 * nvalid)) - 1));
+          for (int q = 0; q < g.i; ++q)
+            m &= zero_bytes(sp[(q * G + gg) * 64 + lane] ^ sp[(q * G + gg) * 64 + 32 + cc]);
+          if (gg < gf) low = m != 0;
+          else if (gg == gf) low = (m & ((1ull << (8 * ef)) - 1)) != 0;
+          W += __popcll(m);
+          if (lvl_dup && m)
+            W1 += __popcll(m & zero_bytes(sp[(g.i * G + gg) * 64 + lane] ^
+                                          sp[(g.i * G + gg) * 64 + 32 + cc]));
+        }
+        emit = !low && W >= g.d && !(lvl_dup && W1 >= g.d);
+      }
       const uint64_t key = (uint64_t(a) << 32) | b;
-      if (PLAIN) {
-        unsigned long long pos = atomicAdd(&g.counters[0], 1ull);
-        if (pos < g.out_cap) g.out_pairs[pos] = key;
-        continue;
-      }
-      atomicAdd(&g.counters[1], 1ull);
-      const uint32_t tagv = g.seq_base + uint32_t(j);
-      uint64_t h = mix64(key) & (g.hs.cap - 1);
-      bool done = false;
-      for (int probe = 0; probe < kMaxProbe && !done; ++probe) {
-        uint64_t cur = g.hs.keys[h];
-        if (cur == kEmpty) {
-          cur = atomicCAS(reinterpret_cast<unsigned long long*>(&g.hs.keys[h]), kEmpty, key);
-          if (cur == kEmpty) {
-            atomicMin(&g.hs.tag[h], tagv);
-            unsigned long long pos = atomicAdd(&g.counters[0], 1ull);
-            if (pos < g.new_cap) g.new_slots[pos] = h;
-            done = true;
-            break;
-          }
+      if (!PLAIN && emit) emit = !set_contains(g.hs, key);
+      const unsigned m = __ballot_sync(0xffffffffu, emit);
+      if (m == 0) continue;
+      unsigned long long base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(&g.counters[0], (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (emit) {
+        const unsigned long long pos = base + __popc(m & lt);
+        if (PLAIN) {
+          if (pos < g.out_cap) g.out_pairs[pos] = key;
+        } else if (pos < g.ev_cap) {
+          g.events[pos] = Event{a, b, int32_t(j), 0u};
         }
-        if (cur == key) {
-          atomicMin(&g.hs.tag[h], tagv);
-          done = true;
-          break;
-        }
-        h = (h + 1) & (g.hs.cap - 1);
       }
-      if (!done) atomicOr(&g.counters[2], 1ull);
     }
   }
 }
 
-__global__ void k_hs_clear(uint64_t* __restrict__ keys, uint32_t* __restrict__ tag, uint64_t cap) {
+__global__ void k_hs_clear(uint64_t* __restrict__ keys, uint64_t cap) {
   for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < cap;
-       q += uint64_t(gridDim.x) * blockDim.x) {
+       q += uint64_t(gridDim.x) * blockDim.x)
     keys[q] = kEmpty;
-    tag[q] = 0xffffffffu;
-  }
 }
 
 }  // namespace
 
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {
-  MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<152 * 8, 256, 0, s>>>(hs.keys, hs.tag, hs.cap));
+  MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<152 * 8, 256, 0, s>>>(hs.keys, hs.cap));
   return cudaGetLastError();
 }
 
@@ -338,7 +363,7 @@ cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const 
   Seg sg{ix.M, ix.D, j0, int(C)};
   const int64_t E = int64_t(segs) * C;
   uint64_t* toff = cs.ntile;
-  MOMENTI_LAUNCH("chunk_agg", s, k_chunk_agg<<<unsigned((E * 32 + 255) / 256), 256, 0, s>>>(ix.lcp, sg, segs, i, cs.cagg, toff));
+  MOMENTI_LAUNCH("chunk_agg", s, k_chunk_agg<<<unsigned((E * 32 + 255) / 256), 256, 0, s>>>(ix.lcp, sg, segs, i, d, cs.cagg, toff));
   MOMENTI_LAUNCH("chunk_scan", s, k_chunk_scan<<<segs, 1024, 0, s>>>(ix.lcp, sg, i, cs.cagg, cs.cbs, toff));
   const int64_t nb = (E + kScanBlock - 1) / kScanBlock;
   uint64_t* bsum = cs.scan_tmp;
@@ -346,9 +371,10 @@ cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const 
   MOMENTI_LAUNCH("scan_top", s, k_scan_top<<<1, kScanBlock, 0, s>>>(bsum, nb, toff + E));
   MOMENTI_LAUNCH("scan_add", s, k_scan_add<<<unsigned(nb), kScanBlock, 0, s>>>(toff, E, bsum));
   CollideArgs g{ix.order, ix.lcp, ix.keys, sg, segs, i, ix.K, d, ix.excl, cs.cbs, toff, hs,
-                uint32_t((ix.K - i) * ix.L), cs.new_slots, cs.new_cap, cs.counters, out_pairs,
-                out_cap};
-  size_t smem = size_t(4) * (64 * (ix.D + 1) + 32) * sizeof(uint64_t);
+                cs.events, cs.ev_cap, cs.counters, out_pairs, out_cap};
+  const int G = (ix.D + 7) / 8;
+  const int NP = (!mode_plain && i < ix.K) ? i + 1 : i;
+  size_t smem = size_t(4) * (64 * G * NP + 32) * sizeof(uint64_t);
   cudaError_t e;
   if (mode_plain) {
     e = cudaFuncSetAttribute(k_collide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -364,24 +390,3 @@ cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const 
 
 }  // namespace momenti
 
-namespace momenti {
-namespace {
-__global__ void k_collect_tag(const HashSet hs, uint32_t t0, uint32_t t1, uint64_t* __restrict__ slots,
-                              uint64_t cap, unsigned long long* __restrict__ count) {
-  for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < hs.cap;
-       q += uint64_t(gridDim.x) * blockDim.x) {
-    uint32_t t = hs.tag[q];
-    if (hs.keys[q] != kEmpty && t >= t0 && t < t1) {
-      unsigned long long pos = atomicAdd(count, 1ull);
-      if (pos < cap) slots[pos] = q;
-    }
-  }
-}
-}  // namespace
-
-cudaError_t launch_collect_tag(const HashSet& hs, uint32_t t0, uint32_t t1, uint64_t* slots,
-                               uint64_t cap, unsigned long long* count, cudaStream_t s) {
-  MOMENTI_LAUNCH("collect_tag", s, k_collect_tag<<<152 * 8, 256, 0, s>>>(hs, t0, t1, slots, cap, count));
-  return cudaGetLastError();
-}
-}  // namespace momenti

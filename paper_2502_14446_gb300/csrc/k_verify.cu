@@ -101,31 +101,52 @@ __device__ VerifyOut select_d(const T dist[2], int D, int d) {
   return VerifyOut{double(sum), double(mx), m0 | (m1 << 32)};
 }
 
+// One warp per candidate event: distances; a pair with dist_d < tau is
+// recorded (with its repetition) and offered to the set of close pairs.
 __global__ void __launch_bounds__(256)
-k_verify_new(Index ix, int d, HashSet hs, const uint64_t* __restrict__ slots,
-             const unsigned long long* __restrict__ counters, uint32_t seq_level, PairRec* rec,
-             uint64_t rec_cap) {
+k_verify_events(Index ix, int d, HashSet hs, const Event* __restrict__ ev,
+                unsigned long long* __restrict__ counters, uint64_t ev_cap, float tau,
+                PairRec* __restrict__ rec, uint64_t rec_cap) {
   const int lane = threadIdx.x & 31;
   uint64_t cnt = counters[0];
-  if (cnt > rec_cap) cnt = rec_cap;
+  if (cnt > ev_cap) cnt = ev_cap;
   const uint64_t nw = uint64_t(gridDim.x) * (blockDim.x >> 5);
   for (uint64_t q = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; q < cnt; q += nw) {
-    const uint64_t slot = slots[q];
-    const uint64_t key = hs.keys[slot];
-    const uint32_t a = uint32_t(key >> 32), b = uint32_t(key);
+    const Event e = ev[q];
     float dist[2];
-    pair_distances<float>(ix, a, b, dist);
+    pair_distances<float>(ix, e.a, e.b, dist);
     VerifyOut v = select_d<float>(dist, ix.D, d);
-    if (lane == 0) {
+    if (lane != 0) continue;
+    if (!(float(v.dist_d) < tau)) {
+      atomicAdd(&counters[3], 1ull);
+      continue;
+    }
+    const unsigned long long pos = atomicAdd(&counters[1], 1ull);
+    if (pos < rec_cap) {
       PairRec r;
-      r.a = a;
-      r.b = b;
-      r.j = int32_t(hs.tag[slot] - seq_level);
+      r.a = e.a;
+      r.b = e.b;
+      r.j = e.j;
       r.dist_d = float(v.dist_d);
       r.dist_max = float(v.dist_max);
       r.pad = 0;
       r.dims = v.mask;
-      rec[q] = r;
+      rec[pos] = r;
+    }
+    const uint64_t key = (uint64_t(e.a) << 32) | e.b;
+    uint64_t h = set_hash(key) & (hs.cap - 1);
+    for (int probe = 0; probe < kSetMaxProbe; ++probe) {
+      uint64_t cur = hs.keys[h];
+      if (cur == key) break;
+      if (cur == kSetEmpty) {
+        cur = atomicCAS(reinterpret_cast<unsigned long long*>(&hs.keys[h]), kSetEmpty, key);
+        if (cur == kSetEmpty) {
+          atomicAdd(&counters[2], 1ull);
+          break;
+        }
+        if (cur == key) break;
+      }
+      h = (h + 1) & (hs.cap - 1);
     }
   }
 }
@@ -292,10 +313,10 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, 
 
 }  // namespace
 
-cudaError_t launch_verify_new(const Index& ix, int d, const HashSet& hs, const CollideScratch& cs,
-                              PairRec* rec, uint64_t rec_cap, cudaStream_t s, int i) {
-  MOMENTI_LAUNCH("verify_new", s, k_verify_new<<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.new_slots, cs.counters,
-                                       uint32_t((ix.K - i) * ix.L), rec, rec_cap));
+cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
+                                 const CollideScratch& cs, float tau, PairRec* rec,
+                                 uint64_t rec_cap, cudaStream_t s) {
+  MOMENTI_LAUNCH("verify_events", s, k_verify_events<<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap));
   return cudaGetLastError();
 }
 

@@ -87,7 +87,7 @@ double failure_bound(double dist_max, int i, int j, int K, int L, int d, double 
 }
 
 struct Pool {
-  std::vector<PoolEntry> items;   // unsorted store
+  std::vector<PoolEntry> items;   // sorted by pair_less
   std::unordered_set<uint64_t> seen;
   std::vector<PoolEntry> top;     // current greedy selection
   double tau_trunc = INFINITY;    // every pair with dist_d < tau_trunc is held
@@ -98,39 +98,36 @@ struct Pool {
   double kth() const { return int(top.size()) == k ? top.back().dd : INFINITY; }
   bool valid() const { return int(top.size()) == k && top.back().dd < tau_trunc; }
 
-  void recompute() {
-    std::vector<PoolEntry> s = items;
-    std::sort(s.begin(), s.end(), pair_less);
-    auto acc = greedy(s, k, eps);
-    top.clear();
-    for (size_t q : acc) top.push_back(s[q]);
-  }
-  void truncate() {
-    if (items.size() <= cap) return;
-    size_t keep = cap / 2;
-    std::nth_element(items.begin(), items.begin() + keep, items.end(), pair_less);
-    double cut = INFINITY;
-    for (size_t q = keep; q < items.size(); ++q) cut = std::min(cut, items[q].dd);
-    tau_trunc = std::min(tau_trunc, cut);
-    items.resize(keep);
-  }
-  // Adds a batch; returns true if the greedy selection was recomputed.
-  bool add(const PairRec* r, size_t m) {
+  // Adds a batch (merged into the sorted store); the greedy selection is
+  // recomputed only if a new pair is not after the current k-th.
+  void add(const PairRec* r, size_t m) {
     const double kt = kth();
     bool dirty = false;
+    std::vector<PoolEntry> fresh;
     for (size_t q = 0; q < m; ++q) {
-      uint64_t key = (uint64_t(r[q].a) << 32) | r[q].b;
       if (double(r[q].dist_d) >= tau_trunc) continue;
+      const uint64_t key = (uint64_t(r[q].a) << 32) | r[q].b;
       if (!seen.insert(key).second) continue;
-      items.push_back(PoolEntry{double(r[q].dist_d), double(r[q].dist_max), r[q].a, r[q].b, r[q].dims});
+      fresh.push_back(PoolEntry{double(r[q].dist_d), double(r[q].dist_max), r[q].a, r[q].b, r[q].dims});
       if (double(r[q].dist_d) <= kt) dirty = true;
     }
+    if (fresh.empty()) return;
+    std::sort(fresh.begin(), fresh.end(), pair_less);
+    const size_t old = items.size();
+    items.insert(items.end(), fresh.begin(), fresh.end());
+    std::inplace_merge(items.begin(), items.begin() + old, items.end(), pair_less);
     if (items.size() > cap) {
-      truncate();
+      const size_t keep = cap / 2;
+      tau_trunc = std::min(tau_trunc, items[keep].dd);
+      items.resize(keep);
       dirty = true;
     }
-    if (dirty) recompute();
-    return dirty;
+    if (int(top.size()) < k) dirty = true;
+    if (dirty) {
+      auto acc = greedy(items, k, eps);
+      top.clear();
+      for (size_t q : acc) top.push_back(items[q]);
+    }
   }
 };
 
@@ -156,6 +153,9 @@ struct momenti_handle {
   HashSet hs;
   PairRec* rec_dev = nullptr;
   PairRec* rec_host = nullptr;
+  uint64_t rec_cap = 0;
+  uint64_t set_fill = 0;
+  uint64_t ev_budget = uint64_t(1) << 30;
   unsigned long long* cnt_host = nullptr;
   int chunk_reps = 32;
   double t_hash_ms = 0, t_sort_ms = 0;
@@ -529,7 +529,8 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
         uint64_t(1) << 25, std::max<uint64_t>(uint64_t(1) << 20, next_pow2(uint64_t(M) * 64)));
     auto scratch_bytes = [&](int sreps, int creps) {
       return uint64_t(sreps) * D * seg_bytes + sort_hist_entries(M, sreps * D) * 4 +
-             uint64_t(creps) * D * (C + 1) * (4 + 4 + 8) + new_cap * (8 + 32) + hs_cap * 12;
+             uint64_t(creps) * D * (C + 1) * (4 + 4 + 8) + new_cap * 32 + hs_cap * 8 +
+             (uint64_t(1) << 22) * sizeof(Event);
     };
     auto total_bytes = [&](int LL) {
       return fixed + scratch_bytes(std::min(sort_reps, LL), std::min(chunk, LL)) +
@@ -604,14 +605,15 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     CK(dalloc(h, &cs.cbs, size_t(E)));
     CK(dalloc(h, &cs.ntile, size_t(E + 1)));
     CK(dalloc(h, &cs.scan_tmp, size_t(E / 1024 + 2)));
-    CK(dalloc(h, &cs.new_slots, size_t(new_cap)));
     CK(dalloc(h, &cs.counters, 4));
-    cs.new_cap = new_cap;
+    h->rec_cap = new_cap;
     CK(dalloc(h, &h->rec_dev, size_t(new_cap)));
     HashSet& hs = h->hs;
     hs.cap = hs_cap;
     CK(dalloc(h, &hs.keys, size_t(hs_cap)));
-    CK(dalloc(h, &hs.tag, size_t(hs_cap)));
+    cs.ev_cap = uint64_t(1) << 22;
+    h->ev_budget = std::max<uint64_t>(uint64_t(1) << 28, limit / 8);
+    CK(dalloc(h, &cs.events, size_t(cs.ev_cap)));
     CK(cudaMallocHost(&h->rec_host, new_cap * sizeof(PairRec)));
     CK(cudaMallocHost(&h->cnt_host, 4 * sizeof(unsigned long long)));
     h->built_gen = h->hp_gen;
@@ -714,57 +716,74 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
   pool.k = k;
   pool.eps = ix.excl;
   CK(launch_hashset_clear(h->hs, s));
+  h->set_fill = 0;
   Timer t_trav(s);
   int stop_i = 0, stop_j = 0;
   double fb = 1.0;
+  // Verified pairs at or above tau are dropped on the device; tau only
+  // decreases and TOP is valid while its k-th pair is below it (every pair
+  // below the k-th is then held).
+  float tau = INFINITY;
   std::vector<std::vector<PairRec>> by_rep(h->chunk_reps);
+  unsigned long long* cnt = h->cnt_host;
   for (int i = K; i >= 1 && !stop_i; --i) {
-    for (int j0 = 0; j0 < L && !stop_i; j0 += h->chunk_reps) {
-      const int j1 = std::min(L, j0 + h->chunk_reps);
-      for (int retry = 0; retry < 4; ++retry) {
+    int j1 = 0;
+    for (int j0 = 0; j0 < L && !stop_i; j0 = j1) {
+      j1 = std::min(L, j0 + h->chunk_reps);
+      // collision counting; halve the chunk while the event list overflows
+      for (;;) {
         CK(cudaMemsetAsync(h->cs.counters, 0, 4 * sizeof(unsigned long long), s));
         CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
-        CK(cudaMemcpyAsync(h->cnt_host, h->cs.counters, 4 * sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(cnt, h->cs.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (h->cnt_host[2] & 1ull) {
-          // set full: start a fresh set and redo the chunk; pairs seen
-          // before come back as new and the host pool drops repeats
-          CK(launch_hashset_clear(h->hs, s));
+        if (cnt[0] <= h->cs.ev_cap) break;
+        // grow the event list up to an eighth of the memory limit, beyond
+        // that split the chunk
+        const uint64_t cap = next_pow2(cnt[0]);
+        if (cap * sizeof(Event) > h->ev_budget && j1 - j0 > 1) {
+          j1 = j0 + (j1 - j0) / 2;
           continue;
         }
-        break;
+        Event* ev = nullptr;
+        CK(dalloc(h, &ev, size_t(cap)));
+        h->cs.events = ev;
+        h->cs.ev_cap = cap;
       }
-      if (h->cnt_host[2] & 1ull) return fail(h, MOMENTI_ERR_OVERFLOW, "topk: pair set overflow");
-      st.n_candidates += int64_t(h->cnt_host[1]);
-      uint64_t nnew = h->cnt_host[0];
-      if (nnew > h->cs.new_cap) {
-        // grow the append list and collect the chunk's new pairs by tag
-        uint64_t cap = next_pow2(nnew);
-        uint64_t* slots = nullptr;
-        PairRec* rec = nullptr;
-        CK(dalloc(h, &slots, size_t(cap)));
-        CK(dalloc(h, &rec, size_t(cap)));
-        PairRec* rh = nullptr;
-        CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
-        cudaFreeHost(h->rec_host);
-        h->rec_host = rh;
-        h->cs.new_slots = slots;
-        h->cs.new_cap = cap;
-        h->rec_dev = rec;
-        CK(cudaMemsetAsync(h->cs.counters, 0, 8, s));
-        const uint32_t base = uint32_t((K - i) * L);
-        CK(launch_collect_tag(h->hs, base + j0, base + j1, slots, cap, h->cs.counters, s));
+      st.n_candidates += int64_t(cnt[0]);
+      st.n_verified += int64_t(cnt[0]);
+      uint64_t nrec = 0;
+      if (cnt[0]) {
+        for (;;) {
+          CK(launch_verify_events(ix, d, h->hs, h->cs, tau, h->rec_dev, h->rec_cap, s));
+          CK(cudaMemcpyAsync(cnt, h->cs.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          if (cnt[1] <= h->rec_cap) break;
+          // grow the record buffers and verify the chunk's events again
+          const uint64_t cap = next_pow2(cnt[1]);
+          PairRec* rec = nullptr;
+          CK(dalloc(h, &rec, size_t(cap)));
+          PairRec* rh = nullptr;
+          CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
+          cudaFreeHost(h->rec_host);
+          h->rec_host = rh;
+          h->rec_dev = rec;
+          h->rec_cap = cap;
+          CK(cudaMemsetAsync(h->cs.counters + 1, 0, 3 * sizeof(unsigned long long), s));
+        }
+        nrec = cnt[1];
+        h->set_fill += cnt[2];
+        if (nrec) {
+          CK(cudaMemcpyAsync(h->rec_host, h->rec_dev, nrec * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+        }
       }
-      CK(launch_verify_new(ix, d, h->hs, h->cs, h->rec_dev, h->cs.new_cap, s, i));
-      if (nnew) {
-        CK(cudaMemcpyAsync(h->rec_host, h->rec_dev, nnew * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+      if (h->set_fill * 2 > h->hs.cap) {
+        CK(launch_hashset_clear(h->hs, s));
+        h->set_fill = 0;
       }
-      st.n_verified += int64_t(nnew);
       ++st.n_chunks;
       for (auto& v : by_rep) v.clear();
-      for (uint64_t q = 0; q < nnew; ++q) {
+      for (uint64_t q = 0; q < nrec; ++q) {
         int jj = h->rec_host[q].j - j0;
         if (jj < 0 || jj >= j1 - j0) return fail(h, MOMENTI_ERR_CUDA, "topk: bad repetition tag");
         by_rep[jj].push_back(h->rec_host[q]);
@@ -780,6 +799,11 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
             break;
           }
         }
+      }
+      if (int(pool.top.size()) == k) {
+        const float t2 = float(1.1 * pool.kth() + 1e-6);
+        if (t2 < tau) tau = t2;
+        pool.tau_trunc = std::min(pool.tau_trunc, double(tau));
       }
     }
   }
