@@ -48,12 +48,28 @@ def parse():
     ap.add_argument("--kernel", default="auto", help="kernel for the roofline object")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--n", type=int, default=100_000,
+                    help="series length (smaller values only for profiler captures)")
     return ap.parse_args()
 
 
-def workload(rank: int):
+def workload(rank: int, n: int = 100_000):
     from paper_2502_14446_gb300 import synth
-    return synth.plain_fp32(seed=rank)
+    return synth.plain_fp32(seed=rank, n=n)
+
+
+def combine(local_ms: float, units_per_step: int, steps: int, world: int, device=None) -> tuple:
+    """Whole-job value over ranks: every rank pushes units_per_step through
+    each of its steps; the job time is the slowest rank's.  Returns
+    (value in units/s, max milliseconds)."""
+    import torch
+    import torch.distributed as dist
+    total_ms = float(local_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * units_per_step * steps / (total_ms / 1e3), total_ms
 
 
 def peaks():
@@ -150,7 +166,7 @@ def run_momenti(args):
         dist.barrier()
     from paper_2502_14446_gb300 import momenti as mom
 
-    wl = workload(rank)
+    wl = workload(rank, args.n)
     prec = mom.PREC_F16X2 if args.precision == "f16x2" else mom.PREC_FP32
     series = torch.from_numpy(wl.series).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -200,14 +216,10 @@ def run_momenti(args):
     launches = mom.launch_count() - launches0
     k_ms, k_n = mom.kernel_time()
     mom.time_kernel(None)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
     units_step = info["M"] * info["D"] * info["L"]
-    value = world * units_step * args.steps / (total_ms / 1e3)
+    value, total_ms = combine(sum(times), units_step, args.steps, world, dev)
+    if world > 1:
+        dist.barrier()
 
     # ---- end to end through host buffers ----
     pinned = torch.from_numpy(wl.series).pin_memory().numpy()
@@ -278,7 +290,7 @@ def run_momenti(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16x2+f32" if prec == mom.PREC_F16X2 else "f32",
             "data": "synthetic",
-            "config": {"workload": "plain_fp32: D=8 n=100000 w=300 d=3 k=10 delta=0.05 "
+            "config": {"workload": f"plain_fp32: D=8 n={wl.n} w=300 d=3 k=10 delta=0.05 "
                                    "float32, 8 GB limit, K=8 L=200, r auto",
                        "precision": args.precision, "L_used": info["L"], "K": info["K"],
                        "r": info["r"], "windows": info["M"], "l2": "flushed (512 MB write) before each step",

@@ -220,107 +220,164 @@ __device__ __forceinline__ uint64_t zero_bytes(uint64_t x) {
 // byte planes: word (t, g) of a window holds byte t (hash value t) of the
 // keys of dims 8g .. 8g+7, dim 8g+e in byte e.  Equality of the length-i
 // prefixes of all dims of two windows is then i XORs and zero-byte masks.
-template <bool PLAIN>
+// I = prefix length (compile time, so every per-hash-value loop is exact)
+template <bool PLAIN, int I>
 __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
   extern __shared__ uint64_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int D = g.sg.D;
   const int G = (D + 7) >> 3;
-  const bool lvl_dup = !PLAIN && g.i < g.K;
-  const int NP = lvl_dup ? g.i + 1 : g.i;          // planes needed
+  const bool lvl_dup = !PLAIN && I < g.K;
+  constexpr int NPMAX = (!PLAIN && I < 8) ? I + 1 : I;   // planes loaded
+  const int NP = lvl_dup ? I + 1 : I;
   uint64_t* sp = smem + int64_t(wib) * (64 * G * NP + 32);
   uint32_t* sidx = reinterpret_cast<uint32_t*>(sp + 64 * G * NP);
   const int64_t E = int64_t(g.segs) * g.sg.C;
   const uint64_t T = g.toff[E];
   const uint64_t nw = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  const uint64_t w = uint64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  // a contiguous range of tiles per warp: one search, then a forward walk
+  const uint64_t t_begin = T * w / nw, t_end = T * (w + 1) / nw;
+  if (t_begin >= t_end) return;
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint64_t t = uint64_t(blockIdx.x) * (blockDim.x >> 5) + wib; t < T; t += nw) {
-    // largest e with toff[e] <= t
-    int64_t lo = 0, hi = E - 1;
+  auto find = [&](int64_t lo, uint64_t t) {     // largest e >= lo with toff[e] <= t
+    int64_t hi = E - 1;
     while (lo < hi) {
       int64_t mid = (lo + hi + 1) >> 1;
       if (g.toff[mid] <= t) lo = mid;
       else hi = mid - 1;
     }
-    const int64_t e = lo;
-    const int seg = int(e / g.sg.C);
-    const int64_t c2 = e - int64_t(seg) * g.sg.C;
-    const int32_t bs0 = g.cbs[e];
-    const int64_t c1 = bs0 / 32 + int64_t(t - g.toff[e]);
-    const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
-    const int gf = f >> 3, ef = f & 7;
-    const int64_t sbase = g.sg.base(seg);
-    const uint32_t* O = g.order + sbase;
-    const uint8_t* Lc = g.lcp + sbase;
-    const uint64_t* Kj = g.keys + int64_t(j) * g.sg.M * D;
-    // bucket start of each column rank
-    const int64_t p2 = c2 * 32 + lane;
-    const bool v2 = p2 < g.sg.M;
-    int32_t sv = (v2 && int(Lc[p2]) < g.i) ? int32_t(p2) : -1;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t u = __shfl_up_sync(0xffffffffu, sv, o);
-      if (lane >= o) sv = max(sv, u);
+    return lo;
+  };
+  int64_t e = find(0, t_begin);
+  int64_t cur = -1;
+  // per column chunk state
+  int j = 0, f = 0, gf = 0, ef = 0, seg = 0;
+  int64_t c2 = 0;
+  int32_t bs0 = 0, bs2 = 0;
+  uint32_t wbl = 0;
+  const uint32_t* O = nullptr;
+  const uint64_t* Kj = nullptr;
+
+  auto load_planes = [&](uint32_t win, bool ok, int r) {
+    const uint64_t* kw = Kj + int64_t(win) * D;
+    for (int gg = 0; gg < G; ++gg) {
+      uint64_t pw[NPMAX];
+#pragma unroll
+      for (int q = 0; q < NPMAX; ++q) pw[q] = 0;
+      for (int ee = 0; ee < 8; ++ee) {
+        const int ff = gg * 8 + ee;
+        if (ff >= D || !ok) break;
+        const uint64_t key = kw[ff];
+#pragma unroll
+        for (int q = 0; q < NPMAX; ++q) pw[q] |= ((key >> (56 - 8 * q)) & 0xFFull) << (8 * ee);
+      }
+#pragma unroll
+      for (int q = 0; q < NPMAX; ++q)
+        if (q < NP) sp[(q * G + gg) * 64 + r] = pw[q];
     }
-    const int32_t bs2 = max(sv, bs0);
+  };
+
+  for (uint64_t t = t_begin; t < t_end; ++t) {
+    if (g.toff[e + 1] <= t) {
+      e = (g.toff[e + 2] <= t) ? find(e + 2, t) : e + 1;
+    }
+    if (e != cur) {
+      // new column chunk: its ranks, keys as byte planes and bucket starts
+      cur = e;
+      seg = int(e / g.sg.C);
+      c2 = e - int64_t(seg) * g.sg.C;
+      bs0 = g.cbs[e];
+      j = g.sg.j0 + seg / D;
+      f = seg - (seg / D) * D;
+      gf = f >> 3;
+      ef = f & 7;
+      const int64_t sbase = g.sg.base(seg);
+      O = g.order + sbase;
+      const uint8_t* Lc = g.lcp + sbase;
+      Kj = g.keys + int64_t(j) * g.sg.M * D;
+      const int64_t p2 = c2 * 32 + lane;
+      const bool v2 = p2 < g.sg.M;
+      int32_t sv = (v2 && int(Lc[p2]) < g.i) ? int32_t(p2) : -1;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t u = __shfl_up_sync(0xffffffffu, sv, o);
+        if (lane >= o) sv = max(sv, u);
+      }
+      bs2 = max(sv, bs0);
+      wbl = v2 ? O[p2] : 0u;
+      __syncwarp();
+      sidx[32 + lane] = wbl;
+      load_planes(wbl, v2, 32 + lane);
+    }
+    const int64_t c1 = bs0 / 32 + int64_t(t - g.toff[e]);
     const int64_t p1 = c1 * 32 + lane;
     const bool v1 = p1 < g.sg.M;
     const uint32_t wa = v1 ? O[p1] : 0u;
-    const uint32_t wbl = v2 ? O[p2] : 0u;
     __syncwarp();
     sidx[lane] = wa;
-    sidx[32 + lane] = wbl;
-    // byte planes of this lane's two windows
-    for (int half = 0; half < 2; ++half) {
-      const bool ok = half ? v2 : v1;
-      const uint64_t* kw = Kj + int64_t(half ? wbl : wa) * D;
-      const int r = half * 32 + lane;
-      for (int gg = 0; gg < G; ++gg) {
-        uint64_t pw[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) pw[q] = 0;
-        for (int ee = 0; ee < 8; ++ee) {
-          const int ff = gg * 8 + ee;
-          if (ff >= D || !ok) break;
-          const uint64_t key = kw[ff];
-#pragma unroll
-          for (int q = 0; q < 9; ++q)
-            if (q < NP) pw[q] |= ((key >> (56 - 8 * q)) & 0xFFull) << (8 * ee);
-        }
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-          if (q < NP) sp[(q * G + gg) * 64 + r] = pw[q];
-      }
-    }
+    load_planes(wa, v1, lane);
     __syncwarp();
+    // row planes of this lane's window in registers (one 64-bit word per
+    // hash value when D <= 8)
+    uint64_t rp[I];
+#pragma unroll
+    for (int q = 0; q < I; ++q) rp[q] = (G == 1) ? sp[q * 64 + lane] : 0ull;
+    const uint64_t valid0 = D >= 8 ? 0x8080808080808080ull
+                                   : (0x8080808080808080ull & ((1ull << (8 * D)) - 1));
+    const uint64_t lowmask = (gf == 0) ? ((1ull << (8 * ef)) - 1) & valid0 : 0ull;
     for (int cc = 0; cc < 32; ++cc) {
       const int64_t pc = c2 * 32 + cc;
       if (pc >= g.sg.M) break;                       // warp-uniform
       const int32_t bsc = __shfl_sync(0xffffffffu, bs2, cc);
       bool emit = p1 >= bsc && p1 < pc;
+      int W = 0;
+      if (emit) {
+        if (G == 1) {
+          uint64_t m = valid0;
+#pragma unroll
+          for (int q = 0; q < I; ++q) m &= zero_bytes(rp[q] ^ sp[q * 64 + 32 + cc]);
+          emit = (m & lowmask) == 0;
+          W = __popcll(m);
+          if (emit && W >= g.d && lvl_dup) {
+            const uint64_t m1 = m & zero_bytes(sp[I * 64 + lane] ^ sp[I * 64 + 32 + cc]);
+            if (__popcll(m1) >= g.d) emit = false;
+          }
+        } else {
+          bool low = false;
+          for (int gg = 0; gg < G && !low; ++gg) {
+            const int nvalid = min(8, D - gg * 8);
+            uint64_t m = nvalid == 8 ? 0x8080808080808080ull
+                                     : (0x8080808080808080ull & ((1ull << (8 * nvalid)) - 1));
+#pragma unroll
+            for (int q = 0; q < I; ++q)
+              m &= zero_bytes(sp[(q * G + gg) * 64 + lane] ^ sp[(q * G + gg) * 64 + 32 + cc]);
+            if (gg < gf) low = m != 0;
+            else if (gg == gf) low = (m & ((1ull << (8 * ef)) - 1)) != 0;
+            W += __popcll(m);
+          }
+          emit = !low;
+          if (emit && W >= g.d && lvl_dup) {
+            int W1 = 0;
+            for (int gg = 0; gg < G; ++gg) {
+              const int nvalid = min(8, D - gg * 8);
+              uint64_t m = nvalid == 8 ? 0x8080808080808080ull
+                                       : (0x8080808080808080ull & ((1ull << (8 * nvalid)) - 1));
+#pragma unroll
+              for (int q = 0; q <= I; ++q)
+                m &= zero_bytes(sp[(q * G + gg) * 64 + lane] ^ sp[(q * G + gg) * 64 + 32 + cc]);
+              W1 += __popcll(m);
+            }
+            if (W1 >= g.d) emit = false;
+          }
+        }
+        emit = emit && W >= g.d;
+      }
       uint32_t a = 0, b = 0;
       if (emit) {
         const uint32_t wb = sidx[32 + cc];
         a = min(wa, wb);
         b = max(wa, wb);
         emit = int64_t(b) - int64_t(a) > g.excl;
-      }
-      if (emit) {
-        int W = 0, W1 = 0;
-        bool low = false;
-        for (int gg = 0; gg < G && !low; ++gg) {
-          const int nvalid = min(8, D - gg * 8);
-          uint64_t m = nvalid == 8 ? 0x8080808080808080ull
-                                   : (0x8080808080808080ull & ((1ull << (8 * nvalid)) - 1));
-          for (int q = 0; q < g.i; ++q)
-            m &= zero_bytes(sp[(q * G + gg) * 64 + lane] ^ sp[(q * G + gg) * 64 + 32 + cc]);
-          if (gg < gf) low = m != 0;
-          else if (gg == gf) low = (m & ((1ull << (8 * ef)) - 1)) != 0;
-          W += __popcll(m);
-          if (lvl_dup && m)
-            W1 += __popcll(m & zero_bytes(sp[(g.i * G + gg) * 64 + lane] ^
-                                          sp[(g.i * G + gg) * 64 + 32 + cc]));
-        }
-        emit = !low && W >= g.d && !(lvl_dup && W1 >= g.d);
       }
       const uint64_t key = (uint64_t(a) << 32) | b;
       if (!PLAIN && emit) emit = !set_contains(g.hs, key);
@@ -349,6 +406,34 @@ __global__ void k_hs_clear(uint64_t* __restrict__ keys, uint64_t cap) {
 
 }  // namespace
 
+template <bool PLAIN, int I>
+static cudaError_t run_collide(const CollideArgs& g, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_collide<PLAIN, I>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  MOMENTI_LAUNCH("collide", s, k_collide<PLAIN, I><<<152 * 8, 128, smem, s>>>(g));
+  return cudaGetLastError();
+}
+
+template <bool PLAIN>
+static cudaError_t dispatch_plain(int i, const CollideArgs& g, size_t smem, cudaStream_t s) {
+  switch (i) {
+    case 1: return run_collide<PLAIN, 1>(g, smem, s);
+    case 2: return run_collide<PLAIN, 2>(g, smem, s);
+    case 3: return run_collide<PLAIN, 3>(g, smem, s);
+    case 4: return run_collide<PLAIN, 4>(g, smem, s);
+    case 5: return run_collide<PLAIN, 5>(g, smem, s);
+    case 6: return run_collide<PLAIN, 6>(g, smem, s);
+    case 7: return run_collide<PLAIN, 7>(g, smem, s);
+    case 8: return run_collide<PLAIN, 8>(g, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t dispatch_collide(int i, bool plain, const CollideArgs& g, size_t smem, cudaStream_t s) {
+  return plain ? dispatch_plain<true>(i, g, smem, s) : dispatch_plain<false>(i, g, smem, s);
+}
+
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {
   MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<152 * 8, 256, 0, s>>>(hs.keys, hs.cap));
   return cudaGetLastError();
@@ -375,16 +460,8 @@ cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const 
   const int G = (ix.D + 7) / 8;
   const int NP = (!mode_plain && i < ix.K) ? i + 1 : i;
   size_t smem = size_t(4) * (64 * G * NP + 32) * sizeof(uint64_t);
-  cudaError_t e;
-  if (mode_plain) {
-    e = cudaFuncSetAttribute(k_collide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("collide", s, k_collide<true><<<152 * 8, 128, smem, s>>>(g));
-  } else {
-    e = cudaFuncSetAttribute(k_collide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("collide", s, k_collide<false><<<152 * 8, 128, smem, s>>>(g));
-  }
+  cudaError_t e = dispatch_collide(i, mode_plain != 0, g, smem, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

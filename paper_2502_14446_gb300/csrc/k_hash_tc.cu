@@ -350,23 +350,27 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
           const int j = g.j0 + (nc * kBN + q * 32) / kRepStride + rr;
-          if (j >= g.j1 || !row_ok) continue;
+          const bool live = j < g.j1 && row_ok;      // warp-uniform in j, per lane in row
           uint64_t key = 0;
 #pragma unroll
           for (int k = 0; k < kRepStride; ++k) {
-            if (k >= g.K) continue;
-            const int nn = j * kRepStride + k;
+            const int nn = min(j, g.L - 1) * kRepStride + k;
             const float qv = (v[rr * 8 + k] + bo[nn]) * g.inv_r;
             float h = floorf(qv);
-            if (fabsf(qv - rintf(qv)) < kMargin) {
-              uint32_t pos = atomicAdd(g.flag_count, 1u);
-              if (pos < g.flag_cap)
+            const bool near = live && k < g.K && fabsf(qv - rintf(qv)) < kMargin;
+            const unsigned fm = __ballot_sync(0xffffffffu, near);
+            if (fm) {
+              uint32_t base = 0;
+              if (lane == __ffs(fm) - 1) base = atomicAdd(g.flag_count, uint32_t(__popc(fm)));
+              base = __shfl_sync(0xffffffffu, base, __ffs(fm) - 1);
+              const uint32_t pos = base + __popc(fm & ((1u << lane) - 1u));
+              if (near && pos < g.flag_cap)
                 g.flags[pos] = (uint64_t(f) << 56) | (uint64_t(nn) << 32) | uint64_t(a);
             }
             h = fminf(fmaxf(h, -128.f), 127.f);
-            key |= uint64_t(int(h) + 128) << (56 - 8 * k);
+            if (k < g.K) key |= uint64_t(int(h) + 128) << (56 - 8 * k);
           }
-          g.keys[(int64_t(j) * g.M + a) * g.D + f] = key;
+          if (live) g.keys[(int64_t(j) * g.M + a) * g.D + f] = key;
         }
       }
       tc_fence_before();
