@@ -207,6 +207,38 @@ int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, 
 int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int64_t cap,
                     int64_t* count);
 
+/* ---- index sort without allocation ------------------------------------ */
+
+/* Largest key count momenti_index_sort_noalloc accepts. */
+#define MOMENTI_NOALLOC_MAX_KEYS 262144
+
+/* The paper has no counterpart: this is a service for callers that must
+ * not allocate device memory, for example code that runs under a fixed
+ * device-memory budget reserved at start-up, or code called from inside
+ * another allocator (a caching allocator or an out-of-memory handler),
+ * where a nested cudaMalloc could fail or recurse.
+ *
+ * Sorts m composite hash keys (device array keys, the layout of one
+ * (repetition, dimension) column of momenti_get_keys) the way the index of
+ * momenti_hash_all is sorted: order[p] = position of the key at rank p
+ * (ties by position), lcp[p] = leading bytes shared with rank p - 1, at
+ * most K (lcp[0] = 0).  order (m uint32) and lcp (m uint8) are caller-owned
+ * device arrays.  Work is queued on stream (cudaStream_t, NULL = legacy
+ * default stream) and the call returns without waiting for it.
+ *
+ * It allocates nothing: its scratch is a fixed array inside the library
+ * (about 6.4 MB per device that loads the library, held until the process
+ * exits).  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * leaves the last call's contents in it; calls whose work overlaps on the
+ * GPU race on it, so serialise them (one stream, or events).
+ * Errors: MOMENTI_ERR_OVERFLOW if m > MOMENTI_NOALLOC_MAX_KEYS;
+ * MOMENTI_ERR_ARG for NULL arrays (m > 0), m < 0 or K outside 1..8;
+ * MOMENTI_ERR_CUDA if the address lookup or a launch fails. */
+int momenti_index_sort_noalloc(const uint64_t* keys, int64_t m, int32_t K, uint32_t* order,
+                               uint8_t* lcp, void* stream);
+
 /* ---- launch accounting (for benchmarks) ------------------------------ */
 
 /* Number of CUDA kernels this library has launched in the process.

@@ -22,6 +22,7 @@ F32, F64 = 0, 1
 PREC_FP32, PREC_F16X2 = 0, 1
 DELTA_PER_MOTIF, DELTA_ALL_K = 0, 1
 MAX_D, MAX_K = 64, 8
+NOALLOC_MAX_KEYS = 262144
 
 # every symbol include/momenti.h declares
 EXPORTS = (
@@ -29,7 +30,7 @@ EXPORTS = (
     "momenti_set_hash_params", "momenti_hash_all", "momenti_topk", "momenti_topk_exact",
     "momenti_verify", "momenti_get_info", "momenti_get_window_stats", "momenti_get_keys",
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
-    "momenti_kernel_time",
+    "momenti_kernel_time", "momenti_index_sort_noalloc",
 )
 
 
@@ -84,6 +85,7 @@ def _load():
         "momenti_launch_count": (C.c_uint64, []),
         "momenti_time_kernel": (C.c_int, [C.c_char_p]),
         "momenti_kernel_time": (C.c_int, [P(C.c_double), P(C.c_uint64)]),
+        "momenti_index_sort_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
