@@ -35,7 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # dominant kernels and their algorithmic work per launch
-DOMINANT = ("proj_hash_tc", "collide", "sort_scatter", "allpairs", "proj_hash_fp32", "verify_new")
+DOMINANT = ("proj_hash_tc", "collide", "subbucket", "sort_scatter", "allpairs", "proj_hash_fp32",
+            "verify_events")
 
 
 def parse():
@@ -133,17 +134,52 @@ def params_for(mom, wl, precision):
                               K=8, L=200, precision=precision)
 
 
-def algorithmic(kernel, info, st, wl):
-    """(bound, work per launch unit, unit label) of a kernel at this workload."""
+def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
+    """Roofline object of one kernel from its live CUDA-event time over the
+    timed steps: achieved = algorithmic work of the timed launches / their
+    device time.  Algorithmic work per unit (per step, from the step's own
+    counters):
+      proj_hash_tc    2 w flop per useful projection (M D L K of them)
+      proj_hash_fp32  the same, on FP32 CUDA cores
+      verify_events   8 D w bytes per verified pair (both windows, all dims)
+      allpairs        10 flop per pair and dim of the diagonal recurrence
+      sort_scatter    24 bytes per index entry per 8-bit pass (K passes)
+    """
+    if not k_n or k_ms <= 0:
+        return None
     M, D, L, K, w = info["M"], info["D"], info["L"], info["K"], wl.w
-    if kernel == "proj_hash_tc":
-        return "tensor", 2.0 * M * D * L * K * w, "TFLOP/s"     # one launch = all repetitions
-    if kernel == "proj_hash_fp32":
-        return "alu", 2.0 * M * D * L * K * w, "TFLOP/s"
-    if kernel == "sort_scatter":
-        # one launch = one 8-bit pass over a batch: read key+index, write key+index
-        return "hbm", None, "GB/s"
-    return None, None, None
+    secs = k_ms / 1e3
+    sm_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    if kernel in ("proj_hash_tc", "proj_hash_fp32"):
+        work = 2.0 * M * D * L * K * w * steps
+        bound, unit = ("tensor", "TFLOP/s") if kernel == "proj_hash_tc" else ("alu", "TFLOP/s")
+        achieved = work / secs / 1e12
+        peak = pk["tflops_sustained"] if bound == "tensor" else sm_peak
+        src = (pk["src"] + " sustained bf16 (fp16 same rate)") if bound == "tensor" else \
+            "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    elif kernel == "verify_events":
+        work = 8.0 * D * w * st["n_candidates"] * steps
+        bound, unit = "hbm", "GB/s"
+        achieved = work / secs / 1e9
+        peak, src = pk["hbm_gbs"], pk["src"] + " copy bandwidth"
+    elif kernel == "allpairs":
+        excl = w // 2
+        pairs = max(0, M - excl - 1) * max(0, M - excl) / 2.0
+        work = 10.0 * D * pairs * steps
+        bound, unit = "alu", "TFLOP/s"
+        achieved = work / secs / 1e12
+        peak, src = sm_peak, "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    elif kernel == "sort_scatter":
+        work = 24.0 * M * D * L * steps * K
+        bound, unit = "hbm", "GB/s"
+        achieved = work / secs / 1e9
+        peak, src = pk["hbm_gbs"], pk["src"] + " copy bandwidth"
+    else:
+        return {"kernel": kernel, "bound": None, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "launches": k_n, "ms_per_launch": k_ms / k_n}
+    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_src": src, "launches": k_n,
+            "ms_per_launch": k_ms / k_n, "work_per_step": work / steps}
 
 
 def run_momenti(args):
@@ -239,28 +275,7 @@ def run_momenti(args):
     out = None
     if rank == 0:
         pk = peaks()
-        roof = None
-        if k_n:
-            per_launch_s = (k_ms / k_n) / 1e3
-            bound, work, unit = algorithmic(kernel, info, st, wl)
-            if kernel == "proj_hash_tc":
-                achieved = work / per_launch_s / 1e12
-                peak = pk["tflops_sustained"]
-                roof = {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_src": pk["src"] + " sustained bf16 (fp16 same rate)",
-                        "launches": k_n, "ms_per_launch": k_ms / k_n}
-            elif kernel == "proj_hash_fp32":
-                achieved = work / per_launch_s / 1e12
-                peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-                roof = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_src": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                        "launches": k_n, "ms_per_launch": k_ms / k_n}
-            else:
-                roof = {"kernel": kernel, "bound": None, "achieved": None, "peak": None,
-                        "unit": None, "frac": None, "traffic": None, "launches": k_n,
-                        "ms_per_launch": k_ms / k_n}
+        roof = roofline(kernel, k_ms, k_n, info, st, wl, args.steps, pk)
         plain = None
         if not args.no_fp32 and prec != mom.PREC_FP32:
             h32 = mom.Momenti(params_for(mom, wl, mom.PREC_FP32))

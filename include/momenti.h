@@ -73,7 +73,13 @@ typedef struct momenti_params {
   uint64_t seed;          /* seed of the hash functions drawn on the device      */
   int32_t  precision;     /* MOMENTI_PREC_*                                      */
   int32_t  delta_mode;    /* MOMENTI_DELTA_*                                     */
+  uint32_t flags;         /* MOMENTI_FLAG_* (0 = defaults)                       */
+  uint32_t reserved;
 } momenti_params;
+
+/* flags: count collisions at prefix length 1 with the pair tiles instead of
+ * splitting buckets by a second dimension (same candidates; for tests). */
+#define MOMENTI_FLAG_TILES_ONLY 1u
 
 /* One motif: windows a < b (0-based), dist_d (Definition distdims),
  * dist_d^max (Eq. distdmax), the dims_d set as a bit mask (bit f = dim f),
@@ -107,6 +113,8 @@ typedef struct momenti_stats {
   int32_t  precision_used;   /* MOMENTI_PREC_* of the projections that ran            */
   int32_t  reserved;
   uint64_t n_rehashed;       /* tensor-core values re-hashed in FP32 (near a boundary) */
+  int64_t  n_lb_pruned;      /* candidates dropped by the segment-mean lower bound    */
+  double   t_host_ms;        /* host time replaying TOP and STOP in the traversal     */
 } momenti_stats;
 
 typedef struct momenti_handle momenti_handle;

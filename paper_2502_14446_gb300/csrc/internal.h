@@ -23,6 +23,10 @@ struct Index {
   bool has_lo = false;
   float* xs_hi = nullptr;     // [D][n]  series, float32 part
   float* xs_lo = nullptr;     // [D][n]  float64 input only: x - double(hi), as float
+  float* xT = nullptr;        // [n][Dp] point-major copy of xs_hi (D <= 8), dims padded with 0
+  float* xlT = nullptr;       // [n][Dp] point-major copy of xs_lo
+  int Dp = 0;                 // 4 or 8 when xT is present
+  float* smT = nullptr;       // [n-15][Dp] means of 16 consecutive points (D <= 8, w >= 32)
   double* mu = nullptr;       // [D][M]
   double* sig = nullptr;      // [D][M]
   float* mu_hi = nullptr;     // [D][M]  float(mu)
@@ -63,6 +67,8 @@ void prof_end(const char* name, cudaStream_t s);
 cudaError_t launch_split_series(const void* src, int dtype, int64_t n, int D, int64_t ld,
                                 float* hi, float* lo, cudaStream_t s);
 cudaError_t launch_window_stats(const Index& ix, cudaStream_t s);
+// xT / xlT from xs_hi / xs_lo, and smT (ix.Dp set)
+cudaError_t launch_point_major(const Index& ix, cudaStream_t s);
 // min/max of the projections of S evenly spaced windows per dim onto the K
 // vectors of repetition 0; out2 = {min, max} (device, 2 floats).
 cudaError_t launch_r_sample(const Index& ix, int S, float* out2, cudaStream_t s);
@@ -135,7 +141,8 @@ struct CollideScratch {
   Event* events = nullptr;
   uint64_t ev_cap = 0;
   // [0] events (or plain pairs), [1] close records, [2] set inserts,
-  // [3] verified pairs dropped at or above the threshold
+  // [3] events dropped by the lower bound, [4] verified pairs dropped at or
+  // above the threshold
   unsigned long long* counters = nullptr;
   int64_t seg_cap = 0;            // segments the arrays can hold
   int64_t chunk_cap = 0;          // chunks per segment
@@ -149,6 +156,22 @@ cudaError_t launch_collide(const Index& ix, int i, int j0, int j1, int d, const 
                            const CollideScratch& cs, int mode_plain, uint64_t* out_pairs,
                            uint64_t out_cap, cudaStream_t s);
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s);
+
+// Prefix length 1, d >= 2, D <= 8: the buckets of the chunk as jobs
+// (segment, first rank, size), then pairs found by splitting each bucket
+// by the first hash value of every higher dimension (a pair with W >= 2
+// collides in a second dim f2); each W >= d pair is emitted once, from its
+// two lowest colliding dims.  Same events as launch_collide.
+struct BucketJob {
+  uint32_t seg, start, n, pad;
+};
+constexpr int kSubBucketCap = 8192;      // members a CTA holds in shared memory (about 190 KB)
+// counts[0] = jobs, counts[1] = largest bucket
+cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob* jobs,
+                               uint64_t job_cap, unsigned long long* counts, cudaStream_t s);
+cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashSet& hs,
+                             const CollideScratch& cs, const BucketJob* jobs,
+                             const unsigned long long* counts, int max_bucket, cudaStream_t s);
 
 // ---- k_verify.cu --------------------------------------------------------
 // Verifies every event of the chunk: pairs with dist_d < tau are written to

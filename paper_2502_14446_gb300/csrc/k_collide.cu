@@ -398,6 +398,163 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
   }
 }
 
+// ---- prefix length 1: buckets split by a second dimension ---------------
+
+__global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs, int d,
+                              BucketJob* __restrict__ jobs, uint64_t job_cap,
+                              unsigned long long* __restrict__ counts) {
+  const int64_t total = int64_t(segs) * sg.M;
+  const int lane = threadIdx.x & 31;
+  for (int64_t q0 = blockIdx.x * int64_t(blockDim.x); q0 < total; q0 += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t q = q0 + threadIdx.x;
+    bool emit = false;
+    uint32_t n = 0, seg = 0, p = 0;
+    if (q < total) {
+      seg = uint32_t(q / sg.M);
+      p = uint32_t(q - int64_t(seg) * sg.M);
+      const int f = int(seg % sg.D);
+      const uint8_t* L = lcp + sg.base(int(seg));
+      if (f <= sg.D - d && int(L[p]) < 1 && int64_t(p) + 1 < sg.M && int(L[p + 1]) >= 1) {
+        int64_t e = p + 1;
+        while (e + 1 < sg.M && int(L[e + 1]) >= 1) ++e;
+        n = uint32_t(e - p + 1);
+        emit = true;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, emit);
+    if (m) {
+      unsigned long long base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(&counts[0], (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (emit) {
+        const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+        if (pos < job_cap) jobs[pos] = BucketJob{seg, p, n, 0u};
+        atomicMax(&counts[1], (unsigned long long)n);
+      }
+    }
+  }
+}
+
+struct SubArgs {
+  const uint32_t* order;
+  const uint64_t* keys;
+  Seg sg;
+  int K, d, excl;
+  HashSet hs;
+  Event* events;
+  uint64_t ev_cap;
+  unsigned long long* counters;
+  const BucketJob* jobs;
+  const unsigned long long* counts;
+  int cap;
+};
+
+__global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
+  // members of one bucket: first and second hash values of every dim as
+  // byte planes (byte e = dim e), window ids, sub-bucket keys, permutation
+  extern __shared__ uint64_t sub_smem[];
+  const int cap = g.cap;
+  uint64_t* p0 = sub_smem;
+  uint64_t* p1 = p0 + cap;
+  uint32_t* widx = reinterpret_cast<uint32_t*>(p1 + cap);
+  uint32_t* hist = widx + cap;
+  uint32_t* bend = hist + 256;
+  uint16_t* perm = reinterpret_cast<uint16_t*>(bend + 256);
+  uint8_t* skey = reinterpret_cast<uint8_t*>(perm + cap);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int D = g.sg.D;
+  const bool lvl_dup = g.K > 1;
+  const uint64_t valid0 = D >= 8 ? 0x8080808080808080ull
+                                 : (0x8080808080808080ull & ((1ull << (8 * D)) - 1));
+  uint64_t njobs = g.counts[0];
+  for (uint64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    const BucketJob job = g.jobs[jb];
+    const int n = int(job.n);
+    if (n > cap) continue;                         // never launched with such buckets
+    const int seg = int(job.seg);
+    const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
+    const uint32_t* O = g.order + g.sg.base(seg) + job.start;
+    const uint64_t* Kj = g.keys + int64_t(j) * g.sg.M * D;
+    __syncthreads();
+    for (int q = tid; q < n; q += blockDim.x) {
+      const uint32_t wv = O[q];
+      widx[q] = wv;
+      const uint64_t* kw = Kj + int64_t(wv) * D;
+      uint64_t a0 = 0, a1 = 0;
+      for (int e = 0; e < D; ++e) {
+        const uint64_t key = kw[e];
+        a0 |= (key >> 56) << (8 * e);
+        a1 |= ((key >> 48) & 0xFFull) << (8 * e);
+      }
+      p0[q] = a0;
+      p1[q] = a1;
+    }
+    __syncthreads();
+    // second-lowest colliding dim f2 leaves d - 2 dims above it
+    for (int f2 = f + 1; f2 <= D - g.d + 1; ++f2) {
+      for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for (int q = tid; q < n; q += blockDim.x) {
+        const uint8_t k = uint8_t(p0[q] >> (8 * f2));
+        skey[q] = k;
+        atomicAdd(&hist[k], 1u);
+      }
+      __syncthreads();
+      if (tid < 32) {                              // exclusive scan of 256 counts by one warp
+        uint32_t v[8], run = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) { v[r] = hist[tid * 8 + r]; run += v[r]; }
+        uint32_t incl = run;
+        for (int o = 1; o < 32; o <<= 1) {
+          uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (tid >= o) incl += u;
+        }
+        uint32_t base = incl - run;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) { hist[tid * 8 + r] = base; base += v[r]; }
+      }
+      __syncthreads();
+      for (int q = tid; q < n; q += blockDim.x) {
+        const uint32_t pos = atomicAdd(&hist[skey[q]], 1u);
+        perm[pos] = uint16_t(q);
+      }
+      __syncthreads();
+      for (int b = tid; b < 256; b += blockDim.x) bend[b] = hist[b];
+      __syncthreads();
+      // pairs inside a sub-bucket collide in f and f2 (first hash value)
+      const uint64_t below = ((1ull << (8 * f2)) - 1) & valid0;   // bytes of dims < f2
+      const uint64_t only_f = 0x80ull << (8 * f);
+      for (int r = tid; r < n; r += blockDim.x) {
+        const int u = perm[r];
+        const int end = int(bend[skey[u]]);
+        const uint64_t pu0 = p0[u], pu1 = p1[u];
+        const uint32_t wu = widx[u];
+        for (int r2 = r + 1; r2 < end; ++r2) {
+          const int v = perm[r2];
+          const uint64_t m = zero_bytes(pu0 ^ p0[v]) & valid0;
+          // f and f2 are the two lowest colliding dims
+          if ((m & below) != only_f) continue;
+          if (__popcll(m) < g.d) continue;
+          if (lvl_dup && __popcll(m & zero_bytes(pu1 ^ p1[v])) >= g.d) continue;
+          const uint32_t wv = widx[v];
+          const uint32_t a = min(wu, wv), b = max(wu, wv);
+          if (int64_t(b) - int64_t(a) <= g.excl) continue;
+          const uint64_t key = (uint64_t(a) << 32) | b;
+          if (set_contains(g.hs, key)) continue;
+          const unsigned act = __activemask();
+          const int leader = __ffs(act) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(&g.counters[0], (unsigned long long)__popc(act));
+          base = __shfl_sync(act, base, leader);
+          const unsigned long long pos = base + __popc(act & ((1u << lane) - 1u));
+          if (pos < g.ev_cap) g.events[pos] = Event{a, b, int32_t(j), 0u};
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void k_hs_clear(uint64_t* __restrict__ keys, uint64_t cap) {
   for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < cap;
        q += uint64_t(gridDim.x) * blockDim.x)
@@ -432,6 +589,38 @@ static cudaError_t dispatch_plain(int i, const CollideArgs& g, size_t smem, cuda
 
 static cudaError_t dispatch_collide(int i, bool plain, const CollideArgs& g, size_t smem, cudaStream_t s) {
   return plain ? dispatch_plain<true>(i, g, smem, s) : dispatch_plain<false>(i, g, smem, s);
+}
+
+cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob* jobs,
+                               uint64_t job_cap, unsigned long long* counts, cudaStream_t s) {
+  const int segs = (j1 - j0) * ix.D;
+  Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
+  const int64_t total = int64_t(segs) * ix.M;
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<unsigned(g), 256, 0, s>>>(ix.lcp, sg, segs, d, jobs, job_cap, counts));
+  return cudaGetLastError();
+}
+
+size_t subbucket_smem(int cap) {
+  return size_t(cap) * (8 + 8 + 4 + 2 + 1) + 2 * 256 * 4 + 16;
+}
+
+cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashSet& hs,
+                             const CollideScratch& cs, const BucketJob* jobs,
+                             const unsigned long long* counts, int max_bucket, cudaStream_t s) {
+  Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
+  const int cap = ((max_bucket + 255) / 256) * 256;
+  SubArgs g{ix.order, ix.keys, sg, ix.K, d, ix.excl, hs, cs.events, cs.ev_cap, cs.counters, jobs,
+            counts, cap};
+  const size_t smem = subbucket_smem(cap);
+  cudaError_t e = cudaFuncSetAttribute(k_subbucket, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = int((size_t(200) * 1024) / smem);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;
+  MOMENTI_LAUNCH("subbucket", s, k_subbucket<<<152 * per_sm, 256, smem, s>>>(g));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {

@@ -268,6 +268,39 @@ __global__ void k_layout_boff(const float* __restrict__ u_src, int D, int L, int
   }
 }
 
+__global__ void k_point_major(const float* __restrict__ hi, const float* __restrict__ lo,
+                              int64_t n, int D, int Dp, float* __restrict__ xT,
+                              float* __restrict__ xlT) {
+  const int64_t total = n * Dp;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t t = q / Dp;
+    const int f = int(q - t * Dp);
+    xT[q] = f < D ? hi[int64_t(f) * n + t] : 0.f;
+    if (lo) xlT[q] = f < D ? lo[int64_t(f) * n + t] : 0.f;
+  }
+}
+
+// Means of 16 consecutive points, point-major, from float64 running sums
+// restarted every 256 points.
+__global__ void k_mean16(const float* __restrict__ hi, const float* __restrict__ lo, int64_t n,
+                         int D, int Dp, float* __restrict__ smT) {
+  const int f = blockIdx.y;
+  const int64_t t0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 256;
+  const int64_t m = n - 15;
+  if (t0 >= m) return;
+  const int64_t t1 = min(m, t0 + 256);
+  const float* x = hi + int64_t(f) * n;
+  const float* y = lo ? lo + int64_t(f) * n : nullptr;
+  auto X = [&](int64_t t) { return double(x[t]) + (y ? double(y[t]) : 0.0); };
+  double s = 0.0;
+  for (int u = 0; u < 16; ++u) s += X(t0 + u);
+  for (int64_t t = t0; t < t1; ++t) {
+    if (t > t0) s += X(t + 15) - X(t - 1);
+    smT[t * Dp + f] = float(s * (1.0 / 16.0));
+  }
+}
+
 inline int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
   if (g > 152 * 32) g = 152 * 32;
@@ -296,6 +329,17 @@ cudaError_t launch_window_stats(const Index& ix, cudaStream_t s) {
   else
     MOMENTI_LAUNCH("window_stats", s, k_window_stats<false><<<grid, 128, 0, s>>>(ix.xs_hi, nullptr, ix.n, ix.M, ix.w, ix.mu, ix.sig,
                                                ix.mu_hi, ix.mu_lo, ix.inv_sig));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_point_major(const Index& ix, cudaStream_t s) {
+  if (!ix.xT) return cudaSuccess;
+  MOMENTI_LAUNCH("point_major", s, k_point_major<<<grid_for(ix.n * ix.Dp, 256), 256, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.n, ix.D, ix.Dp, ix.xT, ix.xlT));
+  if (ix.smT) {
+    const int64_t chunks = (ix.n - 15 + 255) / 256;
+    dim3 grid{unsigned((chunks + 127) / 128), unsigned(ix.D), 1u};
+    MOMENTI_LAUNCH("mean16", s, k_mean16<<<grid, 128, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.n, ix.D, ix.Dp, ix.smT));
+  }
   return cudaGetLastError();
 }
 

@@ -101,8 +101,182 @@ __device__ VerifyOut select_d(const T dist[2], int D, int d) {
   return VerifyOut{double(sum), double(mx), m0 | (m1 << 32)};
 }
 
-// One warp per candidate event: distances; a pair with dist_d < tau is
-// recorded (with its repetition) and offered to the set of close pairs.
+// Per-dimension distances of one pair in FP32 with all dims' partial sums
+// kept per lane (loads of every dim in flight together), then the D warp
+// reductions interleaved; lane f (and f - 32) ends with dimension f.
+template <int DM>
+__device__ __forceinline__ void pair_distances_fast(const Index& ix, uint32_t a, uint32_t b,
+                                                    float dist[2]) {
+  const int lane = threadIdx.x & 31;
+  float acc[DM];
+#pragma unroll
+  for (int f = 0; f < DM; ++f) acc[f] = 0.f;
+#pragma unroll
+  for (int f = 0; f < DM; ++f) {
+    if (f < ix.D) {
+      const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
+      const float m0a = ix.mu_hi[oa], m1a = ix.mu_lo[oa], isa = ix.inv_sig[oa];
+      const float m0b = ix.mu_hi[ob], m1b = ix.mu_lo[ob], isb = ix.inv_sig[ob];
+      const float* xa = ix.xs_hi + int64_t(f) * ix.n + a;
+      const float* xb = ix.xs_hi + int64_t(f) * ix.n + b;
+      const float* la = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n + a : nullptr;
+      const float* lb = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n + b : nullptr;
+      float s = 0.f;
+      for (int t = lane; t < ix.w; t += 32) {
+        float za = ((xa[t] - m0a) + ((la ? la[t] : 0.f) - m1a)) * isa;
+        float zb = ((xb[t] - m0b) + ((lb ? lb[t] : 0.f) - m1b)) * isb;
+        float dd = za - zb;
+        s = fmaf(dd, dd, s);
+      }
+      acc[f] = s;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int f = 0; f < DM; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
+  dist[0] = dist[1] = 0.f;
+#pragma unroll
+  for (int f = 0; f < DM; ++f)
+    if (f < ix.D && lane == (f & 31)) dist[f >> 5] = sqrtf(acc[f]);
+}
+
+// Point-major form (D <= 8): each lane reads all dims of a time point of
+// both windows with float4 loads.  Padding dims have 1/sigma = 0 and add 0.
+template <int DP, bool LO>
+__device__ __forceinline__ void pair_distances_pm(const Index& ix, uint32_t a, uint32_t b,
+                                                  float dist[2]) {
+  const int lane = threadIdx.x & 31;
+  float m0a[DP], m1a[DP], isa[DP], m0b[DP], m1b[DP], isb[DP], acc[DP];
+#pragma unroll
+  for (int f = 0; f < DP; ++f) {
+    acc[f] = 0.f;
+    m0a[f] = m1a[f] = isa[f] = m0b[f] = m1b[f] = isb[f] = 0.f;
+    if (f < ix.D) {
+      const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
+      m0a[f] = ix.mu_hi[oa]; m1a[f] = ix.mu_lo[oa]; isa[f] = ix.inv_sig[oa];
+      m0b[f] = ix.mu_hi[ob]; m1b[f] = ix.mu_lo[ob]; isb[f] = ix.inv_sig[ob];
+    }
+  }
+  const float4* pa = reinterpret_cast<const float4*>(ix.xT + int64_t(a) * DP);
+  const float4* pb = reinterpret_cast<const float4*>(ix.xT + int64_t(b) * DP);
+  const float4* la = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(a) * DP) : nullptr;
+  const float4* lb = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(b) * DP) : nullptr;
+  for (int t = lane; t < ix.w; t += 32) {
+    float xa[DP], xb[DP], ya[DP], yb[DP];
+#pragma unroll
+    for (int v = 0; v < DP / 4; ++v) {
+      const float4 qa = pa[int64_t(t) * (DP / 4) + v], qb = pb[int64_t(t) * (DP / 4) + v];
+      xa[4 * v] = qa.x; xa[4 * v + 1] = qa.y; xa[4 * v + 2] = qa.z; xa[4 * v + 3] = qa.w;
+      xb[4 * v] = qb.x; xb[4 * v + 1] = qb.y; xb[4 * v + 2] = qb.z; xb[4 * v + 3] = qb.w;
+      if (LO) {
+        const float4 ra = la[int64_t(t) * (DP / 4) + v], rb = lb[int64_t(t) * (DP / 4) + v];
+        ya[4 * v] = ra.x; ya[4 * v + 1] = ra.y; ya[4 * v + 2] = ra.z; ya[4 * v + 3] = ra.w;
+        yb[4 * v] = rb.x; yb[4 * v + 1] = rb.y; yb[4 * v + 2] = rb.z; yb[4 * v + 3] = rb.w;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      const float za = ((xa[f] - m0a[f]) + ((LO ? ya[f] : 0.f) - m1a[f])) * isa[f];
+      const float zb = ((xb[f] - m0b[f]) + ((LO ? yb[f] : 0.f) - m1b[f])) * isb[f];
+      const float dd = za - zb;
+      acc[f] = fmaf(dd, dd, acc[f]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int f = 0; f < DP; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
+  dist[0] = dist[1] = 0.f;
+#pragma unroll
+  for (int f = 0; f < DP; ++f)
+    if (f < ix.D && lane == f) dist[0] = sqrtf(acc[f]);
+}
+
+template <int DP>
+__device__ __forceinline__ void load_row(const float* __restrict__ base, int64_t t, float (&v)[DP]) {
+  const float4* p = reinterpret_cast<const float4*>(base + t * DP);
+#pragma unroll
+  for (int q = 0; q < DP / 4; ++q) {
+    const float4 u = p[q];
+    v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+  }
+}
+
+// dist_d of a pair from per-dim distances (registers), the d smallest.
+template <int DM>
+__device__ __forceinline__ float sum_d_smallest(const float (&v)[DM], int D, int d) {
+  float best[DM];
+#pragma unroll
+  for (int q = 0; q < DM; ++q) best[q] = INFINITY;
+#pragma unroll
+  for (int f = 0; f < DM; ++f) {
+    if (f < D) {
+      float x = v[f];
+      // insert x into the sorted prefix best[0..d)
+#pragma unroll
+      for (int q = DM - 1; q >= 0; --q) {
+        if (q < d) {
+          float prev = q > 0 ? best[q - 1] : -INFINITY;
+          if (x < best[q]) best[q] = x >= prev ? x : prev;
+        }
+      }
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < DM; ++q)
+    if (q < d) s += best[q];
+  return s;
+}
+
+// Lower bound of dist_d from segment means (piecewise aggregate
+// approximation): for 16-point segments of both windows,
+//   sum_t (z_a - z_b)^2 >= sum_k 16 (mean_k z_a - mean_k z_b)^2
+// (Cauchy-Schwarz on every segment; the points after the last full
+// segment are left out, which only lowers the bound), and the sum of the d
+// smallest per-dim bounds is below dist_d.  Reads w/16 rows per window.
+template <int DP>
+__device__ __forceinline__ float dist_d_lower_bound(const Index& ix, uint32_t a, uint32_t b, int d) {
+  const int lane = threadIdx.x & 31;
+  float m0a[DP], m1a[DP], isa[DP], m0b[DP], m1b[DP], isb[DP], acc[DP];
+#pragma unroll
+  for (int f = 0; f < DP; ++f) {
+    acc[f] = 0.f;
+    m0a[f] = m1a[f] = isa[f] = m0b[f] = m1b[f] = isb[f] = 0.f;
+    if (f < ix.D) {
+      const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
+      m0a[f] = ix.mu_hi[oa]; m1a[f] = ix.mu_lo[oa]; isa[f] = ix.inv_sig[oa];
+      m0b[f] = ix.mu_hi[ob]; m1b[f] = ix.mu_lo[ob]; isb[f] = ix.inv_sig[ob];
+    }
+  }
+  const int segs = ix.w / 16;
+  for (int k = lane; k < segs; k += 32) {
+    float ua[DP], ub[DP];
+    load_row<DP>(ix.smT, int64_t(a) + 16 * k, ua);
+    load_row<DP>(ix.smT, int64_t(b) + 16 * k, ub);
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      const float za = ((ua[f] - m0a[f]) - m1a[f]) * isa[f];
+      const float zb = ((ub[f] - m0b[f]) - m1b[f]) * isb[f];
+      const float dd = za - zb;
+      acc[f] = fmaf(dd, dd, acc[f]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int f = 0; f < DP; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
+  float lb[DP];
+#pragma unroll
+  for (int f = 0; f < DP; ++f) lb[f] = f < ix.D ? sqrtf(16.f * acc[f]) : INFINITY;
+  return sum_d_smallest<DP>(lb, ix.D, d);
+}
+
+// One warp per candidate event (each warp a contiguous range of events):
+// distances; a pair with dist_d < tau is recorded (with its repetition) and
+// offered to the set of close pairs.
+template <int DM, bool LO>
 __global__ void __launch_bounds__(256)
 k_verify_events(Index ix, int d, HashSet hs, const Event* __restrict__ ev,
                 unsigned long long* __restrict__ counters, uint64_t ev_cap, float tau,
@@ -111,14 +285,25 @@ k_verify_events(Index ix, int d, HashSet hs, const Event* __restrict__ ev,
   uint64_t cnt = counters[0];
   if (cnt > ev_cap) cnt = ev_cap;
   const uint64_t nw = uint64_t(gridDim.x) * (blockDim.x >> 5);
-  for (uint64_t q = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; q < cnt; q += nw) {
+  const uint64_t w = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t q0 = cnt * w / nw, q1 = cnt * (w + 1) / nw;
+  for (uint64_t q = q0; q < q1; ++q) {
     const Event e = ev[q];
+    if ((DM == 4 || DM == 8) && ix.smT) {
+      const float lb = dist_d_lower_bound<(DM == 4 ? 4 : 8)>(ix, e.a, e.b, d);
+      if (lb > tau * (1.f + 1e-3f) + 1e-3f) {          // provably not below tau
+        if (lane == 0) atomicAdd(&counters[3], 1ull);
+        continue;
+      }
+    }
     float dist[2];
-    pair_distances<float>(ix, e.a, e.b, dist);
+    if (DM == 4 || DM == 8) pair_distances_pm<(DM == 4 ? 4 : 8), LO>(ix, e.a, e.b, dist);
+    else if (DM > 0) pair_distances_fast<(DM > 0 ? DM : 1)>(ix, e.a, e.b, dist);
+    else pair_distances<float>(ix, e.a, e.b, dist);
     VerifyOut v = select_d<float>(dist, ix.D, d);
     if (lane != 0) continue;
     if (!(float(v.dist_d) < tau)) {
-      atomicAdd(&counters[3], 1ull);
+      atomicAdd(&counters[4], 1ull);
       continue;
     }
     const unsigned long long pos = atomicAdd(&counters[1], 1ull);
@@ -194,36 +379,224 @@ __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t)
   return xl ? xh[t] + xl[t] : xh[t];
 }
 
-// dist_d of a pair from per-dim distances (registers), the d smallest.
-template <int DM>
-__device__ __forceinline__ float sum_d_smallest(const float (&v)[DM], int D, int d) {
-  float best[DM];
-#pragma unroll
-  for (int q = 0; q < DM; ++q) best[q] = INFINITY;
-#pragma unroll
-  for (int f = 0; f < DM; ++f) {
-    if (f < D) {
-      float x = v[f];
-      // insert x into the sorted prefix best[0..d)
-#pragma unroll
-      for (int q = DM - 1; q >= 0; --q) {
-        if (q < d) {
-          float prev = q > 0 ? best[q - 1] : -INFINITY;
-          if (x < best[q]) best[q] = x >= prev ? x : prev;
-        }
-      }
-    }
-  }
-  float s = 0.f;
-#pragma unroll
-  for (int q = 0; q < DM; ++q)
-    if (q < d) s += best[q];
-  return s;
-}
-
 template <int DM, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
 k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
+           unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
+  const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
+  const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  if (delta >= ix.M || a0 >= ix.M - delta) return;
+  const int64_t a1 = min(a0 + kSeg, ix.M - delta);
+  const int D = ix.D, w = ix.w;
+  const float wf = float(w), inv_w = 1.f / float(w);
+  // per dim: sums of the two windows centred by ca / cb (sliding), and of
+  // their products
+  float qt[DM], s1a[DM], s2a[DM], s1b[DM], s2b[DM], ca[DM], cb[DM];
+#pragma unroll
+  for (int f = 0; f < DM; ++f) {
+    qt[f] = s1a[f] = s2a[f] = s1b[f] = s2b[f] = ca[f] = cb[f] = 0.f;
+    if (f < D) {
+      const float* xh = ix.xs_hi + int64_t(f) * ix.n;
+      const float* xl = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n : nullptr;
+      ca[f] = ix.mu_hi[int64_t(f) * ix.M + a0];
+      cb[f] = ix.mu_hi[int64_t(f) * ix.M + a0 + delta];
+      float q = 0.f, u1 = 0.f, u2 = 0.f, v1 = 0.f, v2 = 0.f;
+      for (int t = 0; t < w; ++t) {
+        const float xa = xv(xh, xl, a0 + t) - ca[f], xb = xv(xh, xl, a0 + delta + t) - cb[f];
+        q = fmaf(xa, xb, q);
+        u1 += xa;
+        u2 = fmaf(xa, xa, u2);
+        v1 += xb;
+        v2 = fmaf(xb, xb, v2);
+      }
+      qt[f] = q; s1a[f] = u1; s2a[f] = u2; s1b[f] = v1; s2b[f] = v2;
+    }
+  }
+  const float thr = tau * 1.01f + 1e-2f;
+  for (int64_t a = a0; a < a1; ++a) {
+    const int64_t b = a + delta;
+    float dist[DM];
+    int near = 0;
+    bool unsure = false;
+#pragma unroll
+    for (int f = 0; f < DM; ++f) {
+      dist[f] = INFINITY;
+      if (f < D) {
+        if (a > a0) {
+          const float* xh = ix.xs_hi + int64_t(f) * ix.n;
+          const float* xl = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n : nullptr;
+          const float oa = xv(xh, xl, a - 1) - ca[f], ob = xv(xh, xl, b - 1) - cb[f];
+          const float ia = xv(xh, xl, a + w - 1) - ca[f], ib = xv(xh, xl, b + w - 1) - cb[f];
+          qt[f] = fmaf(ia, ib, fmaf(-oa, ob, qt[f]));
+          s1a[f] += ia - oa;
+          s2a[f] = fmaf(ia, ia, fmaf(-oa, oa, s2a[f]));
+          s1b[f] += ib - ob;
+          s2b[f] = fmaf(ib, ib, fmaf(-ob, ob, s2b[f]));
+        }
+        const float ma = s1a[f] * inv_w, mb = s1b[f] * inv_w;
+        const float qa = s2a[f] * inv_w, qb = s2b[f] * inv_w;
+        const float va = qa - ma * ma, vb = qb - mb * mb;
+        const float cov = qt[f] * inv_w - ma * mb;
+        // a variance lost to cancellation (a near-flat window): keep the pair
+        // for the exact check
+        const bool fa = !(va > 1e-4f * qa), fb = !(vb > 1e-4f * qb);
+        float sq;
+        if (fa || fb) {
+          unsure = true;
+          sq = 0.f;
+        } else {
+          sq = 2.f * wf * (1.f - cov * rsqrtf(va * vb));
+        }
+        dist[f] = sqrtf(fmaxf(sq, 0.f));
+        near += dist[f] <= thr;
+      }
+    }
+    if (ROWMIN) {
+      float s = sum_d_smallest<DM>(dist, D, d);
+      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(s));
+      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(s));
+    } else if (near >= d || unsure) {
+      float s = unsure ? 0.f : sum_d_smallest<DM>(dist, D, d);
+      if (s <= thr) {
+        unsigned long long pos = atomicAdd(count, 1ull);
+        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
+      }
+    }
+  }
+}
+
+// Point-major series (D <= 8): the four time points a step touches are
+// read as whole rows of DP dims (float4 loads); the window sums of both
+// windows slide with the product sum, so no per-window statistic is read
+// per step.
+template <int DP, bool LO, bool ROWMIN>
+__global__ void __launch_bounds__(kDiagBlock, 4)
+k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
+              unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
+  const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
+  const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  if (delta >= ix.M || a0 >= ix.M - delta) return;
+  const int64_t a1 = min(a0 + kSeg, ix.M - delta);
+  const int D = ix.D, w = ix.w;
+  const float wf = float(w), inv_w = 1.f / float(w);
+  const float* X = ix.xT;
+  const float* XL = ix.xlT;
+  float qt[DP], s1a[DP], s2a[DP], s1b[DP], s2b[DP], ca[DP], cb[DP];
+#pragma unroll
+  for (int f = 0; f < DP; ++f) {
+    qt[f] = s1a[f] = s2a[f] = s1b[f] = s2b[f] = 0.f;
+    ca[f] = f < D ? ix.mu_hi[int64_t(f) * ix.M + a0] : 0.f;
+    cb[f] = f < D ? ix.mu_hi[int64_t(f) * ix.M + a0 + delta] : 0.f;
+  }
+  for (int t = 0; t < w; ++t) {
+    float xa[DP], xb[DP];
+    load_row<DP>(X, a0 + t, xa);
+    load_row<DP>(X, a0 + delta + t, xb);
+    if (LO) {
+      float ya[DP], yb[DP];
+      load_row<DP>(XL, a0 + t, ya);
+      load_row<DP>(XL, a0 + delta + t, yb);
+#pragma unroll
+      for (int f = 0; f < DP; ++f) { xa[f] += ya[f]; xb[f] += yb[f]; }
+    }
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      const float u = xa[f] - ca[f], v = xb[f] - cb[f];
+      qt[f] = fmaf(u, v, qt[f]);
+      s1a[f] += u;
+      s2a[f] = fmaf(u, u, s2a[f]);
+      s1b[f] += v;
+      s2b[f] = fmaf(v, v, s2b[f]);
+    }
+  }
+  const float thr = tau * 1.01f + 1e-2f;
+  const float c0 = 1.f - thr * thr / (2.f * wf);
+  const float c0sq = c0 * c0;
+  for (int64_t a = a0; a < a1; ++a) {
+    const int64_t b = a + delta;
+    if (a > a0) {
+      float oa[DP], ob[DP], ia[DP], ib[DP];
+      load_row<DP>(X, a - 1, oa);
+      load_row<DP>(X, b - 1, ob);
+      load_row<DP>(X, a + w - 1, ia);
+      load_row<DP>(X, b + w - 1, ib);
+      if (LO) {
+        float y[DP];
+        load_row<DP>(XL, a - 1, y);
+#pragma unroll
+        for (int f = 0; f < DP; ++f) oa[f] += y[f];
+        load_row<DP>(XL, b - 1, y);
+#pragma unroll
+        for (int f = 0; f < DP; ++f) ob[f] += y[f];
+        load_row<DP>(XL, a + w - 1, y);
+#pragma unroll
+        for (int f = 0; f < DP; ++f) ia[f] += y[f];
+        load_row<DP>(XL, b + w - 1, y);
+#pragma unroll
+        for (int f = 0; f < DP; ++f) ib[f] += y[f];
+      }
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        const float uo = oa[f] - ca[f], vo = ob[f] - cb[f];
+        const float ui = ia[f] - ca[f], vi = ib[f] - cb[f];
+        qt[f] = fmaf(ui, vi, fmaf(-uo, vo, qt[f]));
+        s1a[f] += ui - uo;
+        s2a[f] = fmaf(ui, ui, fmaf(-uo, uo, s2a[f]));
+        s1b[f] += vi - vo;
+        s2b[f] = fmaf(vi, vi, fmaf(-vo, vo, s2b[f]));
+      }
+    }
+    // dist_f <= thr  <=>  corr >= c0 = 1 - thr^2 / 2w  <=>  C >= c0 sqrt(VA VB)
+    // with C = w QT - S1a S1b, VA = w S2a - S1a^2 (sums of the centred windows)
+    int near = 0;
+    bool unsure = false;
+    unsigned nmask = 0;
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      if (f < D) {
+        const float VA = fmaf(wf, s2a[f], -s1a[f] * s1a[f]);
+        const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
+        const float Cv = fmaf(wf, qt[f], -s1a[f] * s1b[f]);
+        const bool flat = !(VA > 1e-4f * wf * s2a[f]) || !(VB > 1e-4f * wf * s2b[f]);
+        unsure |= flat;
+        const bool ok = c0 <= 0.f || (Cv > 0.f && Cv * Cv >= c0sq * VA * VB);
+        near += ok;
+        nmask |= unsigned(ok) << f;
+      }
+    }
+    float dist[DP];
+    if (ROWMIN || near >= d) {
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float VA = fmaf(wf, s2a[f], -s1a[f] * s1a[f]);
+          const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
+          const float Cv = fmaf(wf, qt[f], -s1a[f] * s1b[f]);
+          const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+          dist[f] = sqrtf(fmaxf(sq, 0.f));
+        }
+      }
+    }
+    (void)nmask;
+    if (ROWMIN) {
+      float sm = sum_d_smallest<DP>(dist, D, d);
+      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+    } else if (near >= d || unsure) {
+      const float sm = unsure ? 0.f : sum_d_smallest<DP>(dist, D, d);
+      if (sm <= thr) {
+        unsigned long long pos = atomicAdd(count, 1ull);
+        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
+      }
+    }
+  }
+}
+
+// Wide series (D > 16): per-window means and 1/sigma are read per step.
+template <int DM, bool ROWMIN>
+__global__ void __launch_bounds__(kDiagBlock)
+k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
            unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
   const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
@@ -298,16 +671,20 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, 
   const int64_t ndiag = ix.M - (ix.excl + 1);
   if (ndiag <= 0) return cudaSuccess;
   dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned((ndiag + kDiagBlock - 1) / kDiagBlock), 1u};
-  if (ix.D <= 4)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<4, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
-  else if (ix.D <= 8)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<8, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+  if (ix.xT && ix.Dp == 4 && ix.has_lo)
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+  else if (ix.xT && ix.Dp == 4)
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, false, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+  else if (ix.xT && ix.Dp == 8 && ix.has_lo)
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+  else if (ix.xT && ix.Dp == 8)
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, false, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
   else if (ix.D <= 16)
     MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
   else if (ix.D <= 32)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
   else
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
   return cudaGetLastError();
 }
 
@@ -316,7 +693,13 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, 
 cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
                                  const CollideScratch& cs, float tau, PairRec* rec,
                                  uint64_t rec_cap, cudaStream_t s) {
-  MOMENTI_LAUNCH("verify_events", s, k_verify_events<<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap));
+#define MOMENTI_VE(DM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, LO><<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
+  const bool lo = ix.has_lo;
+  if (ix.xT && ix.Dp == 4) { if (lo) MOMENTI_VE(4, true); else MOMENTI_VE(4, false); }
+  else if (ix.xT && ix.Dp == 8) { if (lo) MOMENTI_VE(8, true); else MOMENTI_VE(8, false); }
+  else if (ix.D <= 16) MOMENTI_VE(16, false);
+  else MOMENTI_VE(0, false);
+#undef MOMENTI_VE
   return cudaGetLastError();
 }
 

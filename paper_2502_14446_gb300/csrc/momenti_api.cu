@@ -86,9 +86,40 @@ double failure_bound(double dist_max, int i, int j, int K, int L, int d, double 
   return first * std::pow(1.0 - std::pow(p, i + 1), L - j);
 }
 
+// Open-addressing set of pair keys (host).
+struct KeySet {
+  std::vector<uint64_t> slot;
+  size_t used = 0;
+  static constexpr uint64_t kEmpty = ~0ull;
+  static uint64_t mix(uint64_t x) {
+    x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ull; x ^= x >> 27; x *= 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+  }
+  bool insert(uint64_t key) {   // true if new
+    if ((used + 1) * 2 > slot.size()) grow();
+    size_t m = slot.size() - 1, h = size_t(mix(key)) & m;
+    while (slot[h] != kEmpty) {
+      if (slot[h] == key) return false;
+      h = (h + 1) & m;
+    }
+    slot[h] = key;
+    ++used;
+    return true;
+  }
+  void grow() {
+    std::vector<uint64_t> old;
+    old.swap(slot);
+    slot.assign(std::max<size_t>(1 << 16, old.size() * 2), kEmpty);
+    used = 0;
+    for (uint64_t k : old)
+      if (k != kEmpty) insert(k);
+  }
+};
+
 struct Pool {
-  std::vector<PoolEntry> items;   // sorted by pair_less
-  std::unordered_set<uint64_t> seen;
+  std::vector<PoolEntry> items;   // items[0, sorted) sorted by pair_less, the rest appended
+  size_t sorted = 0;
+  KeySet seen;
   std::vector<PoolEntry> top;     // current greedy selection
   double tau_trunc = INFINITY;    // every pair with dist_d < tau_trunc is held
   size_t cap = size_t(1) << 22;
@@ -97,33 +128,52 @@ struct Pool {
 
   double kth() const { return int(top.size()) == k ? top.back().dd : INFINITY; }
   bool valid() const { return int(top.size()) == k && top.back().dd < tau_trunc; }
+  size_t size() const { return items.size(); }
 
-  // Adds a batch (merged into the sorted store); the greedy selection is
-  // recomputed only if a new pair is not after the current k-th.
+  void sort_all() {
+    if (sorted < items.size()) {
+      std::sort(items.begin() + sorted, items.end(), pair_less);
+      std::inplace_merge(items.begin(), items.begin() + sorted, items.end(), pair_less);
+      sorted = items.size();
+    }
+  }
+
+  // a new pair not after the k-th changes the selection only if no taken
+  // pair that precedes it is within eps of one of its windows
+  bool changes_top(const PoolEntry& c) const {
+    if (int(top.size()) < k) return true;
+    if (!pair_less(c, top.back())) return false;
+    if (int64_t(c.b) - int64_t(c.a) <= eps) return false;
+    for (const PoolEntry& t : top) {
+      if (!pair_less(t, c)) break;
+      const int64_t xs[2] = {c.a, c.b}, ys[2] = {t.a, t.b};
+      for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v)
+          if (std::llabs(xs[u] - ys[v]) <= eps) return false;
+    }
+    return true;
+  }
+
   void add(const PairRec* r, size_t m) {
-    const double kt = kth();
     bool dirty = false;
-    std::vector<PoolEntry> fresh;
     for (size_t q = 0; q < m; ++q) {
       if (double(r[q].dist_d) >= tau_trunc) continue;
       const uint64_t key = (uint64_t(r[q].a) << 32) | r[q].b;
-      if (!seen.insert(key).second) continue;
-      fresh.push_back(PoolEntry{double(r[q].dist_d), double(r[q].dist_max), r[q].a, r[q].b, r[q].dims});
-      if (double(r[q].dist_d) <= kt) dirty = true;
+      if (!seen.insert(key)) continue;
+      PoolEntry c{double(r[q].dist_d), double(r[q].dist_max), r[q].a, r[q].b, r[q].dims};
+      if (!dirty && changes_top(c)) dirty = true;
+      items.push_back(c);
     }
-    if (fresh.empty()) return;
-    std::sort(fresh.begin(), fresh.end(), pair_less);
-    const size_t old = items.size();
-    items.insert(items.end(), fresh.begin(), fresh.end());
-    std::inplace_merge(items.begin(), items.begin() + old, items.end(), pair_less);
     if (items.size() > cap) {
+      sort_all();
       const size_t keep = cap / 2;
       tau_trunc = std::min(tau_trunc, items[keep].dd);
       items.resize(keep);
+      sorted = keep;
       dirty = true;
     }
-    if (int(top.size()) < k) dirty = true;
     if (dirty) {
+      sort_all();
       auto acc = greedy(items, k, eps);
       top.clear();
       for (size_t q : acc) top.push_back(items[q]);
@@ -156,6 +206,9 @@ struct momenti_handle {
   uint64_t rec_cap = 0;
   uint64_t set_fill = 0;
   uint64_t ev_budget = uint64_t(1) << 30;
+  BucketJob* jobs = nullptr;                // prefix-length-1 bucket jobs
+  uint64_t job_cap = 0;
+  unsigned long long* job_counts = nullptr;
   unsigned long long* cnt_host = nullptr;
   int chunk_reps = 32;
   double t_hash_ms = 0, t_sort_ms = 0;
@@ -210,6 +263,9 @@ void free_all(momenti_handle* h) {
   h->draw_a = h->draw_u = nullptr;
   h->flags = nullptr;
   h->small = nullptr;
+  h->jobs = nullptr;
+  h->job_counts = nullptr;
+  h->job_cap = 0;
   h->ix = Index{};
   h->sort = SortScratch{};
   h->cs = CollideScratch{};
@@ -565,6 +621,16 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     const int N = L * kRepStride;
     CK(dalloc(h, &ix.xs_hi, size_t(D) * n));
     if (ix.has_lo) CK(dalloc(h, &ix.xs_lo, size_t(D) * n));
+    if (D <= 8) {
+      ix.Dp = D <= 4 ? 4 : 8;
+      CK(dalloc(h, &ix.xT, size_t(ix.Dp) * n));
+      if (ix.has_lo) CK(dalloc(h, &ix.xlT, size_t(ix.Dp) * n));
+      if (w >= 32) {
+        CK(dalloc(h, &ix.smT, size_t(ix.Dp) * n));
+        // padding dims stay zero
+        CK(cudaMemsetAsync(ix.smT, 0, size_t(ix.Dp) * n * 4, static_cast<cudaStream_t>(stream)));
+      }
+    }
     CK(dalloc(h, &ix.mu, size_t(D) * M));
     CK(dalloc(h, &ix.sig, size_t(D) * M));
     CK(dalloc(h, &ix.mu_hi, size_t(D) * M));
@@ -605,17 +671,22 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     CK(dalloc(h, &cs.cbs, size_t(E)));
     CK(dalloc(h, &cs.ntile, size_t(E + 1)));
     CK(dalloc(h, &cs.scan_tmp, size_t(E / 1024 + 2)));
-    CK(dalloc(h, &cs.counters, 4));
+    CK(dalloc(h, &cs.counters, 8));
     h->rec_cap = new_cap;
     CK(dalloc(h, &h->rec_dev, size_t(new_cap)));
     HashSet& hs = h->hs;
     hs.cap = hs_cap;
     CK(dalloc(h, &hs.keys, size_t(hs_cap)));
+    if (D <= 8 && p.d >= 2) {
+      h->job_cap = uint64_t(1) << 20;
+      CK(dalloc(h, &h->jobs, size_t(h->job_cap)));
+      CK(dalloc(h, &h->job_counts, 2));
+    }
     cs.ev_cap = uint64_t(1) << 22;
     h->ev_budget = std::max<uint64_t>(uint64_t(1) << 28, limit / 8);
     CK(dalloc(h, &cs.events, size_t(cs.ev_cap)));
     CK(cudaMallocHost(&h->rec_host, new_cap * sizeof(PairRec)));
-    CK(cudaMallocHost(&h->cnt_host, 4 * sizeof(unsigned long long)));
+    CK(cudaMallocHost(&h->cnt_host, 8 * sizeof(unsigned long long)));
     h->built_gen = h->hp_gen;
   }
   const int L = ix.L, Wp = ix.Wp, N = L * kRepStride;
@@ -632,6 +703,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     ld = n;
   }
   CK(launch_split_series(src, dtype, n, D, ld, ix.xs_hi, ix.xs_lo, s));
+  CK(launch_point_major(ix, s));
   if (staging) CK(cudaFreeAsync(staging, s));
   CK(launch_window_stats(ix, s));
 
@@ -730,15 +802,25 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
     int j1 = 0;
     for (int j0 = 0; j0 < L && !stop_i; j0 = j1) {
       j1 = std::min(L, j0 + h->chunk_reps);
-      // collision counting; halve the chunk while the event list overflows
+      // collision counting (prefix length 1: buckets split by a second
+      // dimension when every bucket fits a CTA); grow the event list, or
+      // halve the chunk beyond the event budget
       for (;;) {
-        CK(cudaMemsetAsync(h->cs.counters, 0, 4 * sizeof(unsigned long long), s));
-        CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
-        CK(cudaMemcpyAsync(cnt, h->cs.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        bool sub = false;
+        unsigned long long jc[2] = {0, 0};
+        if (i == 1 && d >= 2 && ix.D <= 8 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
+          CK(cudaMemsetAsync(h->job_counts, 0, 2 * sizeof(unsigned long long), s));
+          CK(launch_bucket_jobs(ix, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
+          CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          sub = jc[0] <= h->job_cap && jc[1] <= uint64_t(kSubBucketCap);
+        }
+        CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
+        if (sub) CK(launch_subbucket(ix, j0, j1, d, h->hs, h->cs, h->jobs, h->job_counts, int(jc[1]), s));
+        else CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
+        CK(cudaMemcpyAsync(cnt, h->cs.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (cnt[0] <= h->cs.ev_cap) break;
-        // grow the event list up to an eighth of the memory limit, beyond
-        // that split the chunk
         const uint64_t cap = next_pow2(cnt[0]);
         if (cap * sizeof(Event) > h->ev_budget && j1 - j0 > 1) {
           j1 = j0 + (j1 - j0) / 2;
@@ -755,7 +837,7 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
       if (cnt[0]) {
         for (;;) {
           CK(launch_verify_events(ix, d, h->hs, h->cs, tau, h->rec_dev, h->rec_cap, s));
-          CK(cudaMemcpyAsync(cnt, h->cs.counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+          CK(cudaMemcpyAsync(cnt, h->cs.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
           if (cnt[1] <= h->rec_cap) break;
           // grow the record buffers and verify the chunk's events again
@@ -768,7 +850,7 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
           h->rec_host = rh;
           h->rec_dev = rec;
           h->rec_cap = cap;
-          CK(cudaMemsetAsync(h->cs.counters + 1, 0, 3 * sizeof(unsigned long long), s));
+          CK(cudaMemsetAsync(h->cs.counters + 1, 0, 7 * sizeof(unsigned long long), s));
         }
         nrec = cnt[1];
         h->set_fill += cnt[2];
@@ -782,6 +864,8 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
         h->set_fill = 0;
       }
       ++st.n_chunks;
+      const auto th0 = std::chrono::steady_clock::now();
+      st.n_lb_pruned += int64_t(cnt[3]);
       for (auto& v : by_rep) v.clear();
       for (uint64_t q = 0; q < nrec; ++q) {
         int jj = h->rec_host[q].j - j0;
@@ -800,6 +884,7 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
           }
         }
       }
+      st.t_host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
       if (int(pool.top.size()) == k) {
         const float t2 = float(1.1 * pool.kth() + 1e-6);
         if (t2 < tau) tau = t2;
@@ -809,6 +894,7 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
   }
   st.t_traverse_ms = t_trav.stop();
   st.n_pool = int64_t(pool.items.size());
+  pool.sort_all();
   double max_err = 0;
   int rc;
   if (stop_i) {
@@ -940,7 +1026,7 @@ int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int
   uint64_t* dout = nullptr;
   const uint64_t dcap = uint64_t(std::max<int64_t>(cap, 1));
   CK(cudaMallocAsync(&dout, dcap * 8, s));
-  CK(cudaMemsetAsync(h->cs.counters, 0, 4 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
   CK(launch_collide(h->ix, i, j, j + 1, h->p.d, h->hs, h->cs, 1, dout, uint64_t(cap), s));
   unsigned long long c = 0;
   CK(cudaMemcpyAsync(&c, h->cs.counters, 8, cudaMemcpyDeviceToHost, s));

@@ -20,6 +20,7 @@ OK = 0
 ERR_ARG, ERR_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_STATE = -1, -2, -3, -4, -5, -6
 F32, F64 = 0, 1
 PREC_FP32, PREC_F16X2 = 0, 1
+FLAG_TILES_ONLY = 1
 DELTA_PER_MOTIF, DELTA_ALL_K = 0, 1
 MAX_D, MAX_K = 64, 8
 NOALLOC_MAX_KEYS = 262144
@@ -38,7 +39,7 @@ class momenti_params(C.Structure):
     _fields_ = [("w", C.c_int32), ("d", C.c_int32), ("k", C.c_int32), ("delta", C.c_double),
                 ("mem_limit", C.c_uint64), ("K", C.c_int32), ("L", C.c_int32), ("r", C.c_double),
                 ("excl", C.c_int32), ("seed", C.c_uint64), ("precision", C.c_int32),
-                ("delta_mode", C.c_int32)]
+                ("delta_mode", C.c_int32), ("flags", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class momenti_motif(C.Structure):
@@ -54,7 +55,7 @@ class momenti_stats(C.Structure):
                 ("t_traverse_ms", C.c_double), ("t_fallback_ms", C.c_double),
                 ("max_rel_err_fp32", C.c_double), ("device_bytes", C.c_uint64),
                 ("precision_used", C.c_int32), ("reserved", C.c_int32),
-                ("n_rehashed", C.c_uint64)]
+                ("n_rehashed", C.c_uint64), ("n_lb_pruned", C.c_int64), ("t_host_ms", C.c_double)]
 
 
 def _load():

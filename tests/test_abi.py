@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(mom):
 
 def test_struct_layouts(mom):
     assert C.sizeof(mom.momenti_motif) == 48
-    assert C.sizeof(mom.momenti_params) == 72
+    assert C.sizeof(mom.momenti_params) == 80
 
 
 def test_default_params_are_the_papers(mom):

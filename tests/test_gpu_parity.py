@@ -281,3 +281,27 @@ def test_topk_plain_small_matches_exact(mom):
     assert st["L"] == 200 and st["K"] == 8
     ex = h.topk_exact()
     assert_same_motifs(ex, gold["motifs"])
+
+
+@pytest.mark.parametrize("seed,D,d", [(5, 4, 2), (6, 8, 3), (7, 6, 2)])
+def test_subbucketed_and_tiled_collisions_agree(mom, seed, D, d):
+    # prefix length 1 splits buckets by a second dimension; the tile form
+    # checks every in-bucket pair: both must emit the same candidates
+    wl = synth.tiny(seed, 2500, D, 40, d, k=4, n_motifs=1)
+    L = 24
+    A, U = synth.hash_draws(wl.D, L, 8, wl.w, seed)
+    out = []
+    for flags in (0, mom.FLAG_TILES_ONLY):
+        h = mom.Momenti(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, K=8, L=L, r=0.0,
+                        precision=mom.PREC_FP32, flags=flags)
+        h.set_hash_params(A, U)
+        h.hash_all(wl.series)
+        motifs, st = h.topk()
+        out.append((motifs, st))
+    (m0, s0), (m1, s1) = out
+    assert s0["n_candidates"] == s1["n_candidates"] > 0
+    assert (s0["stop_i"], s0["stop_j"]) == (s1["stop_i"], s1["stop_j"])
+    assert [(m["a"], m["b"]) for m in m0] == [(m["a"], m["b"]) for m in m1]
+    ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+    if s0["fallback"]:
+        assert [(m["a"], m["b"]) for m in m0] == [(m[1], m[2]) for m in ref]
