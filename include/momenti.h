@@ -22,7 +22,11 @@
  *   - a handle is single-threaded: calls on one handle must not overlap;
  *   - all GPU work of a handle runs on the stream given to momenti_hash_all
  *     (the legacy default stream when NULL); calls return after that stream
- *     has finished the call's work, unless stated otherwise.
+ *     has finished the call's work, unless stated otherwise; that stream
+ *     must stay valid until the next momenti_hash_all or momenti_destroy
+ *     (device buffers are released on it);
+ *   - device memory comes from a stream-ordered pool of the library, one per
+ *     device, trimmed by momenti_destroy and at the end of a batch.
  */
 #ifndef MOMENTI_H
 #define MOMENTI_H
@@ -189,6 +193,36 @@ int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out);
  * [0, M); MOMENTI_ERR_STATE before momenti_hash_all. */
 int momenti_verify(momenti_handle* h, const int64_t* pairs, int64_t m, double* per_dim,
                    double* dist_d, uint64_t* dims_mask, int32_t fp64);
+
+/* ---- batching form ----------------------------------------------------- */
+
+/* Many independent searches at once: B series, each with its own
+ * parameters, length and dimension count (the batching form: series of
+ * uneven lengths and widths).  Series b is searched exactly as
+ *   momenti_create(&h, &params[b]);
+ *   momenti_hash_all(h, series[b], dtype[b], n[b], D[b], n[b], on_device, s);
+ *   momenti_topk(h, out + b * out_stride, &n_out[b], stats + b);
+ * would, and gives the same result (no arithmetic differs).  The work is
+ * spread over `threads` worker handles (8 when <= 0), each on its own
+ * non-blocking CUDA stream and host thread, taking the series longest first
+ * (by n * D), so the GPU interleaves the searches; device memory is held by
+ * at most `threads` series at a time.
+ *   params   : B parameter records, each checked as momenti_create checks one;
+ *              a zero mem_limit means 80% of the free memory / threads
+ *   series   : B pointers to D[b] x n[b] row-major arrays (row stride n[b]),
+ *              host memory, or device memory when on_device != 0 (already
+ *              written: the workers' streams do not wait for other streams)
+ *   out      : B * out_stride motifs; out_stride >= every params[b].k
+ *   n_out    : B counts; stats (B entries) and rc (B statuses) may be NULL
+ *   err      : optional buffer (err_len bytes) for the first failure's
+ *              message, "series <b>: <text>"
+ * Returns MOMENTI_OK, MOMENTI_ERR_ARG for bad batch arguments (nothing
+ * run), or the status of the lowest-numbered failing series; a failing
+ * series does not stop the others. */
+int momenti_topk_batch(int32_t B, const momenti_params* params, const void* const* series,
+                       const int32_t* dtype, const int64_t* n, const int32_t* D, int32_t on_device,
+                       int32_t threads, momenti_motif* out, int32_t out_stride, int32_t* n_out,
+                       momenti_stats* stats, int32_t* rc, char* err, int32_t err_len);
 
 /* ---- inspection of the index (for tests and tools) ------------------- */
 

@@ -27,6 +27,7 @@ struct Index {
   float* xlT = nullptr;       // [n][Dp] point-major copy of xs_lo
   int Dp = 0;                 // 4 or 8 when xT is present
   float* smT = nullptr;       // [n-15][Dp] means of 16 consecutive points (D <= 8, w >= 32)
+  float* stT = nullptr;       // [M][3][Dp] point-major mu_hi, mu_lo, inv_sig (D <= 8)
   double* mu = nullptr;       // [D][M]
   double* sig = nullptr;      // [D][M]
   float* mu_hi = nullptr;     // [D][M]  float(mu)
@@ -56,6 +57,10 @@ static_assert(sizeof(PairRec) == 32, "PairRec layout");
 // for the selected kernel, CUDA events on the launching stream).
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(const char* name, cudaStream_t s);
+// Opt a kernel in to `bytes` of dynamic shared memory on the current
+// device.  The limit only ever rises (under a lock), so a launch on one
+// thread never sees it lowered by another thread's smaller request.
+cudaError_t allow_smem(const void* func, size_t bytes);
 #define MOMENTI_LAUNCH(name, stream, ...)      \
   do {                                         \
     ::momenti::prof_begin(name, stream);       \
@@ -69,6 +74,8 @@ cudaError_t launch_split_series(const void* src, int dtype, int64_t n, int D, in
 cudaError_t launch_window_stats(const Index& ix, cudaStream_t s);
 // xT / xlT from xs_hi / xs_lo, and smT (ix.Dp set)
 cudaError_t launch_point_major(const Index& ix, cudaStream_t s);
+// stT from the window statistics (after launch_window_stats)
+cudaError_t launch_stats_point_major(const Index& ix, cudaStream_t s);
 // min/max of the projections of S evenly spaced windows per dim onto the K
 // vectors of repetition 0; out2 = {min, max} (device, 2 floats).
 cudaError_t launch_r_sample(const Index& ix, int S, float* out2, cudaStream_t s);

@@ -565,8 +565,7 @@ __global__ void k_hs_clear(uint64_t* __restrict__ keys, uint64_t cap) {
 
 template <bool PLAIN, int I>
 static cudaError_t run_collide(const CollideArgs& g, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_collide<PLAIN, I>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_collide<PLAIN, I>), smem);
   if (e != cudaSuccess) return e;
   MOMENTI_LAUNCH("collide", s, k_collide<PLAIN, I><<<152 * 8, 128, smem, s>>>(g));
   return cudaGetLastError();
@@ -614,7 +613,7 @@ cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashS
   SubArgs g{ix.order, ix.keys, sg, ix.K, d, ix.excl, hs, cs.events, cs.ev_cap, cs.counters, jobs,
             counts, cap};
   const size_t smem = subbucket_smem(cap);
-  cudaError_t e = cudaFuncSetAttribute(k_subbucket, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket), smem);
   if (e != cudaSuccess) return e;
   int per_sm = int((size_t(200) * 1024) / smem);
   if (per_sm < 1) per_sm = 1;

@@ -46,8 +46,9 @@ k_proj_hash_fp32(const float* __restrict__ xh, const float* __restrict__ xl,
   __shared__ float sxl[LO ? kBM + kTK : 1];
   __shared__ __align__(16) float sb[kTK][kBN];
 
-  const int f = blockIdx.z;
-  const int64_t a0 = int64_t(blockIdx.x) * kBM;
+  // dims fastest: the D CTAs of a window tile store into the same key rows
+  const int f = int(blockIdx.x % unsigned(D));
+  const int64_t a0 = int64_t(blockIdx.x / unsigned(D)) * kBM;
   const int jb = j0 + blockIdx.y * kBR;
   const int tid = threadIdx.x;
   const int tw = tid & 31, tr = tid >> 5;
@@ -121,7 +122,7 @@ k_proj_hash_fp32(const float* __restrict__ xh, const float* __restrict__ xl,
 
 cudaError_t launch_proj_hash_fp32(const Index& ix, int j0, int j1, cudaStream_t s) {
   if (j1 <= j0) return cudaSuccess;
-  dim3 grid(unsigned((ix.M + kBM - 1) / kBM), unsigned((j1 - j0 + kBR - 1) / kBR), unsigned(ix.D));
+  dim3 grid(unsigned(ix.D * ((ix.M + kBM - 1) / kBM)), unsigned((j1 - j0 + kBR - 1) / kBR), 1u);
   const int N = ix.L * kRepStride;
   if (ix.has_lo)
     MOMENTI_LAUNCH("proj_hash_fp32", s, k_proj_hash_fp32<true><<<grid, 256, 0, s>>>(ix.xs_hi, ix.xs_lo, ix.mu_hi, ix.mu_lo, ix.inv_sig,

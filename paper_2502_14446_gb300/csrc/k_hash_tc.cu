@@ -190,8 +190,10 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   float* sxl = sx + S.seg;
   float* sst = reinterpret_cast<float*>(base + (S.st - smem_u32(base)));   // [3][128]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f = blockIdx.y;
-  const int64_t a0 = int64_t(blockIdx.x) * kBM;
+  // the D dims of one window tile are neighbouring CTAs, so their 8-byte
+  // key stores into the same [j][a][0..D) rows meet in L2
+  const int f = int(blockIdx.x % unsigned(g.D));
+  const int64_t a0 = int64_t(blockIdx.x / unsigned(g.D)) * kBM;
   const int KC = g.Wp / kBK;
   const int NC = (g.j1 - g.j0) * kRepStride;
   const int nchunks = (NC + kBN - 1) / kBN;
@@ -429,15 +431,16 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  // initialised once, thread-safely (the batching form hashes from several threads)
+  static const EncodeFn fn = []() -> EncodeFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
-  }
+      return reinterpret_cast<EncodeFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -476,9 +479,9 @@ cudaError_t launch_proj_hash_tc(const Index& ix, int j0, int j1, uint64_t* flags
            ix.inv_r, ix.n, ix.M, ix.D, ix.w, ix.Wp, N, ix.K, ix.L, j0, j1, ix.keys, flags,
            flag_cap, flag_count, err};
   const size_t smem = tc_smem_bytes(ix.Wp, ix.has_lo);
-  cudaError_t e = cudaFuncSetAttribute(k_proj_hash_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_proj_hash_tc), smem);
   if (e != cudaSuccess) return e;
-  dim3 grid{unsigned((ix.M + kBM - 1) / kBM), unsigned(ix.D), 1u};
+  dim3 grid{unsigned(ix.D * ((ix.M + kBM - 1) / kBM)), 1u, 1u};
   MOMENTI_LAUNCH("proj_hash_tc", s, k_proj_hash_tc<<<grid, kThreads, smem, s>>>(map, g));
   return cudaGetLastError();
 }

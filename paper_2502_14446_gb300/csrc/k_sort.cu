@@ -49,7 +49,8 @@ struct Src {
 __global__ void __launch_bounds__(kThreads)
 k_hist(Src src, int shift, int tiles, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[256];
-  const int seg = blockIdx.y, tile = blockIdx.x;
+  // segments fastest: the first pass reads [j][a][0..D) rows of all dims together
+  const int seg = blockIdx.x, tile = blockIdx.y;
   for (int d = threadIdx.x; d < 256; d += kThreads) h[d] = 0;
   __syncthreads();
   const int64_t base = int64_t(tile) * kTile;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kThreads)
 k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
   __shared__ uint32_t wh[kWarps][256];
-  const int seg = blockIdx.y, tile = blockIdx.x;
+  const int seg = blockIdx.x, tile = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < kWarps * 256; q += kThreads) (&wh[0][0])[q] = 0;
   __syncthreads();
@@ -179,7 +180,7 @@ cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch&
   if (int64_t(segs) * ix.M > sc.cap_entries || sort_hist_entries(ix.M, segs) > sc.hist_entries)
     return cudaErrorInvalidValue;
   const int tiles = int((ix.M + kTile - 1) / kTile);
-  dim3 grid{unsigned(tiles), unsigned(segs), 1u};
+  dim3 grid{unsigned(segs), unsigned(tiles), 1u};
   uint64_t* kb[2] = {sc.k0, sc.k1};
   uint32_t* vb[2] = {sc.v0, sc.v1};
   for (int pass = 0; pass < ix.K; ++pass) {

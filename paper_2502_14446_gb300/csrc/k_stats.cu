@@ -301,6 +301,22 @@ __global__ void k_mean16(const float* __restrict__ hi, const float* __restrict__
   }
 }
 
+__global__ void k_stats_pm(const float* __restrict__ mh, const float* __restrict__ ml,
+                           const float* __restrict__ isg, int64_t M, int D, int Dp,
+                           float* __restrict__ stT) {
+  const int64_t total = M * Dp;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t a = q / Dp;
+    const int f = int(q - a * Dp);
+    const int64_t o = int64_t(f) * M + a;
+    float* dst = stT + a * 3 * Dp;
+    dst[f] = f < D ? mh[o] : 0.f;
+    dst[Dp + f] = f < D ? ml[o] : 0.f;
+    dst[2 * Dp + f] = f < D ? isg[o] : 0.f;
+  }
+}
+
 inline int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
   if (g > 152 * 32) g = 152 * 32;
@@ -340,6 +356,12 @@ cudaError_t launch_point_major(const Index& ix, cudaStream_t s) {
     dim3 grid{unsigned((chunks + 127) / 128), unsigned(ix.D), 1u};
     MOMENTI_LAUNCH("mean16", s, k_mean16<<<grid, 128, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.n, ix.D, ix.Dp, ix.smT));
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_point_major(const Index& ix, cudaStream_t s) {
+  if (!ix.stT) return cudaSuccess;
+  MOMENTI_LAUNCH("stats_pm", s, k_stats_pm<<<grid_for(ix.M * ix.Dp, 256), 256, 0, s>>>(ix.mu_hi, ix.mu_lo, ix.inv_sig, ix.M, ix.D, ix.Dp, ix.stT));
   return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 // verified exactly by the direct form above.
 #include "internal.h"
 
+#include <algorithm>
+
 namespace momenti {
 
 namespace {
@@ -141,58 +143,6 @@ __device__ __forceinline__ void pair_distances_fast(const Index& ix, uint32_t a,
     if (f < ix.D && lane == (f & 31)) dist[f >> 5] = sqrtf(acc[f]);
 }
 
-// Point-major form (D <= 8): each lane reads all dims of a time point of
-// both windows with float4 loads.  Padding dims have 1/sigma = 0 and add 0.
-template <int DP, bool LO>
-__device__ __forceinline__ void pair_distances_pm(const Index& ix, uint32_t a, uint32_t b,
-                                                  float dist[2]) {
-  const int lane = threadIdx.x & 31;
-  float m0a[DP], m1a[DP], isa[DP], m0b[DP], m1b[DP], isb[DP], acc[DP];
-#pragma unroll
-  for (int f = 0; f < DP; ++f) {
-    acc[f] = 0.f;
-    m0a[f] = m1a[f] = isa[f] = m0b[f] = m1b[f] = isb[f] = 0.f;
-    if (f < ix.D) {
-      const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
-      m0a[f] = ix.mu_hi[oa]; m1a[f] = ix.mu_lo[oa]; isa[f] = ix.inv_sig[oa];
-      m0b[f] = ix.mu_hi[ob]; m1b[f] = ix.mu_lo[ob]; isb[f] = ix.inv_sig[ob];
-    }
-  }
-  const float4* pa = reinterpret_cast<const float4*>(ix.xT + int64_t(a) * DP);
-  const float4* pb = reinterpret_cast<const float4*>(ix.xT + int64_t(b) * DP);
-  const float4* la = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(a) * DP) : nullptr;
-  const float4* lb = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(b) * DP) : nullptr;
-  for (int t = lane; t < ix.w; t += 32) {
-    float xa[DP], xb[DP], ya[DP], yb[DP];
-#pragma unroll
-    for (int v = 0; v < DP / 4; ++v) {
-      const float4 qa = pa[int64_t(t) * (DP / 4) + v], qb = pb[int64_t(t) * (DP / 4) + v];
-      xa[4 * v] = qa.x; xa[4 * v + 1] = qa.y; xa[4 * v + 2] = qa.z; xa[4 * v + 3] = qa.w;
-      xb[4 * v] = qb.x; xb[4 * v + 1] = qb.y; xb[4 * v + 2] = qb.z; xb[4 * v + 3] = qb.w;
-      if (LO) {
-        const float4 ra = la[int64_t(t) * (DP / 4) + v], rb = lb[int64_t(t) * (DP / 4) + v];
-        ya[4 * v] = ra.x; ya[4 * v + 1] = ra.y; ya[4 * v + 2] = ra.z; ya[4 * v + 3] = ra.w;
-        yb[4 * v] = rb.x; yb[4 * v + 1] = rb.y; yb[4 * v + 2] = rb.z; yb[4 * v + 3] = rb.w;
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < DP; ++f) {
-      const float za = ((xa[f] - m0a[f]) + ((LO ? ya[f] : 0.f) - m1a[f])) * isa[f];
-      const float zb = ((xb[f] - m0b[f]) + ((LO ? yb[f] : 0.f) - m1b[f])) * isb[f];
-      const float dd = za - zb;
-      acc[f] = fmaf(dd, dd, acc[f]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int f = 0; f < DP; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
-  dist[0] = dist[1] = 0.f;
-#pragma unroll
-  for (int f = 0; f < DP; ++f)
-    if (f < ix.D && lane == f) dist[0] = sqrtf(acc[f]);
-}
-
 template <int DP>
 __device__ __forceinline__ void load_row(const float* __restrict__ base, int64_t t, float (&v)[DP]) {
   const float4* p = reinterpret_cast<const float4*>(base + t * DP);
@@ -230,6 +180,62 @@ __device__ __forceinline__ float sum_d_smallest(const float (&v)[DM], int D, int
   return s;
 }
 
+// Window statistics of window a from the point-major copy: 3 rows of DP.
+template <int DP>
+__device__ __forceinline__ void load_stats(const Index& ix, uint32_t a, float (&mh)[DP],
+                                           float (&ml)[DP], float (&is)[DP]) {
+  const float* base = ix.stT + int64_t(a) * 3 * DP;
+  load_row<DP>(base, 0, mh);
+  load_row<DP>(base + DP, 0, ml);
+  load_row<DP>(base + 2 * DP, 0, is);
+}
+
+// Point-major form (D <= 8): each lane reads all dims of a time point of
+// both windows with float4 loads.  Padding dims have 1/sigma = 0 and add 0.
+template <int DP, bool LO>
+__device__ __forceinline__ void pair_distances_pm(const Index& ix, uint32_t a, uint32_t b,
+                                                  float dist[2]) {
+  const int lane = threadIdx.x & 31;
+  float m0a[DP], m1a[DP], isa[DP], m0b[DP], m1b[DP], isb[DP], acc[DP];
+  load_stats<DP>(ix, a, m0a, m1a, isa);
+  load_stats<DP>(ix, b, m0b, m1b, isb);
+#pragma unroll
+  for (int f = 0; f < DP; ++f) acc[f] = 0.f;
+  const float4* pa = reinterpret_cast<const float4*>(ix.xT + int64_t(a) * DP);
+  const float4* pb = reinterpret_cast<const float4*>(ix.xT + int64_t(b) * DP);
+  const float4* la = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(a) * DP) : nullptr;
+  const float4* lb = LO ? reinterpret_cast<const float4*>(ix.xlT + int64_t(b) * DP) : nullptr;
+  for (int t = lane; t < ix.w; t += 32) {
+    float xa[DP], xb[DP], ya[DP], yb[DP];
+#pragma unroll
+    for (int v = 0; v < DP / 4; ++v) {
+      const float4 qa = pa[int64_t(t) * (DP / 4) + v], qb = pb[int64_t(t) * (DP / 4) + v];
+      xa[4 * v] = qa.x; xa[4 * v + 1] = qa.y; xa[4 * v + 2] = qa.z; xa[4 * v + 3] = qa.w;
+      xb[4 * v] = qb.x; xb[4 * v + 1] = qb.y; xb[4 * v + 2] = qb.z; xb[4 * v + 3] = qb.w;
+      if (LO) {
+        const float4 ra = la[int64_t(t) * (DP / 4) + v], rb = lb[int64_t(t) * (DP / 4) + v];
+        ya[4 * v] = ra.x; ya[4 * v + 1] = ra.y; ya[4 * v + 2] = ra.z; ya[4 * v + 3] = ra.w;
+        yb[4 * v] = rb.x; yb[4 * v + 1] = rb.y; yb[4 * v + 2] = rb.z; yb[4 * v + 3] = rb.w;
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      const float za = ((xa[f] - m0a[f]) + ((LO ? ya[f] : 0.f) - m1a[f])) * isa[f];
+      const float zb = ((xb[f] - m0b[f]) + ((LO ? yb[f] : 0.f) - m1b[f])) * isb[f];
+      const float dd = za - zb;
+      acc[f] = fmaf(dd, dd, acc[f]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int f = 0; f < DP; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
+  dist[0] = dist[1] = 0.f;
+#pragma unroll
+  for (int f = 0; f < DP; ++f)
+    if (f < ix.D && lane == f) dist[0] = sqrtf(acc[f]);
+}
+
 // Lower bound of dist_d from segment means (piecewise aggregate
 // approximation): for 16-point segments of both windows,
 //   sum_t (z_a - z_b)^2 >= sum_k 16 (mean_k z_a - mean_k z_b)^2
@@ -240,16 +246,10 @@ template <int DP>
 __device__ __forceinline__ float dist_d_lower_bound(const Index& ix, uint32_t a, uint32_t b, int d) {
   const int lane = threadIdx.x & 31;
   float m0a[DP], m1a[DP], isa[DP], m0b[DP], m1b[DP], isb[DP], acc[DP];
+  load_stats<DP>(ix, a, m0a, m1a, isa);
+  load_stats<DP>(ix, b, m0b, m1b, isb);
 #pragma unroll
-  for (int f = 0; f < DP; ++f) {
-    acc[f] = 0.f;
-    m0a[f] = m1a[f] = isa[f] = m0b[f] = m1b[f] = isb[f] = 0.f;
-    if (f < ix.D) {
-      const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
-      m0a[f] = ix.mu_hi[oa]; m1a[f] = ix.mu_lo[oa]; isa[f] = ix.inv_sig[oa];
-      m0b[f] = ix.mu_hi[ob]; m1b[f] = ix.mu_lo[ob]; isb[f] = ix.inv_sig[ob];
-    }
-  }
+  for (int f = 0; f < DP; ++f) acc[f] = 0.f;
   const int segs = ix.w / 16;
   for (int k = lane; k < segs; k += 32) {
     float ua[DP], ub[DP];
@@ -382,8 +382,8 @@ __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t)
 template <int DM, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
 k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-           unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
-  const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
+           unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+  const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
   const int64_t a1 = min(a0 + kSeg, ix.M - delta);
@@ -472,8 +472,8 @@ k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
 template <int DP, bool LO, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock, 4)
 k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-              unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
-  const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
+              unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+  const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
   const int64_t a1 = min(a0 + kSeg, ix.M - delta);
@@ -593,12 +593,140 @@ k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t c
   }
 }
 
+// Point-major, block-shared rows: all diagonals of a block share the row
+// windows a in [a0, a0 + kSeg), so the row values (centred by the first
+// row window's mean) and their sliding sums are staged once in shared
+// memory; each thread keeps the column sums and the cross product.
+template <int DP, bool ROWMIN>
+__global__ void __launch_bounds__(kDiagBlock)
+k_allpairs_rows(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
+                unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+  extern __shared__ float ap_smem[];
+  const int w = ix.w, D = ix.D;
+  const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  const int64_t dlo = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock;
+  if (dlo >= ix.M || a0 >= ix.M - dlo) return;                  // block-uniform
+  const int64_t delta = dlo + threadIdx.x;
+  const bool live = delta < ix.M && a0 < ix.M - delta;
+  const int64_t a1 = live ? min(a0 + kSeg, ix.M - delta) : a0;
+  const int64_t nrow = min(int64_t(kSeg), ix.M - dlo - a0);     // row windows this block needs
+  const int span = int(nrow) - 1 + w;                           // points of those windows
+  float* rowx = ap_smem;                                        // [span][DP], centred
+  float* sa1 = rowx + (kSeg - 1 + w) * DP;                      // [kSeg][DP]
+  float* sa2 = sa1 + kSeg * DP;
+  float* cav = sa2 + kSeg * DP;                                 // [DP]
+  const float* X = ix.xT;
+  if (threadIdx.x < DP) cav[threadIdx.x] = threadIdx.x < D ? ix.mu_hi[int64_t(threadIdx.x) * ix.M + a0] : 0.f;
+  __syncthreads();
+  for (int q = threadIdx.x; q < span * DP; q += blockDim.x) {
+    const int t = q / DP, f = q - t * DP;
+    rowx[q] = f < D ? X[(a0 + t) * DP + f] - cav[f] : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x < DP) {                                       // one thread per dim slides the row sums
+    const int f = threadIdx.x;
+    float u1 = 0.f, u2 = 0.f;
+    for (int t = 0; t < w; ++t) {
+      const float v = rowx[t * DP + f];
+      u1 += v;
+      u2 = fmaf(v, v, u2);
+    }
+    sa1[f] = u1;
+    sa2[f] = u2;
+    for (int r = 1; r < nrow; ++r) {
+      const float o = rowx[(r - 1) * DP + f], in = rowx[(r - 1 + w) * DP + f];
+      u1 += in - o;
+      u2 = fmaf(in, in, fmaf(-o, o, u2));
+      sa1[r * DP + f] = u1;
+      sa2[r * DP + f] = u2;
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  const float wf = float(w);
+  float qt[DP], s1b[DP], s2b[DP], cb[DP];
+#pragma unroll
+  for (int f = 0; f < DP; ++f) {
+    qt[f] = s1b[f] = s2b[f] = 0.f;
+    cb[f] = f < D ? ix.mu_hi[int64_t(f) * ix.M + a0 + delta] : 0.f;
+  }
+  for (int t = 0; t < w; ++t) {
+    float xb[DP];
+    load_row<DP>(X, a0 + delta + t, xb);
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      const float u = rowx[t * DP + f], v = xb[f] - cb[f];
+      qt[f] = fmaf(u, v, qt[f]);
+      s1b[f] += v;
+      s2b[f] = fmaf(v, v, s2b[f]);
+    }
+  }
+  const float thr = tau * 1.01f + 1e-2f;
+  const float c0 = 1.f - thr * thr / (2.f * wf);
+  const float c0sq = c0 * c0;
+  for (int64_t a = a0; a < a1; ++a) {
+    const int r = int(a - a0);
+    const int64_t b = a + delta;
+    if (r > 0) {
+      float ob[DP], ib[DP];
+      load_row<DP>(X, b - 1, ob);
+      load_row<DP>(X, b + w - 1, ib);
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        const float uo = rowx[(r - 1) * DP + f], ui = rowx[(r - 1 + w) * DP + f];
+        const float vo = ob[f] - cb[f], vi = ib[f] - cb[f];
+        qt[f] = fmaf(ui, vi, fmaf(-uo, vo, qt[f]));
+        s1b[f] += vi - vo;
+        s2b[f] = fmaf(vi, vi, fmaf(-vo, vo, s2b[f]));
+      }
+    }
+    int near = 0;
+    bool unsure = false;
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      if (f < D) {
+        const float s1a = sa1[r * DP + f], s2a = sa2[r * DP + f];
+        const float VA = fmaf(wf, s2a, -s1a * s1a);
+        const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
+        const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
+        unsure |= !(VA > 1e-4f * wf * s2a) || !(VB > 1e-4f * wf * s2b[f]);
+        near += c0 <= 0.f || (Cv > 0.f && Cv * Cv >= c0sq * VA * VB);
+      }
+    }
+    if (!ROWMIN && near < d && !unsure) continue;
+    float dist[DP];
+#pragma unroll
+    for (int f = 0; f < DP; ++f) {
+      dist[f] = INFINITY;
+      if (f < D) {
+        const float s1a = sa1[r * DP + f], s2a = sa2[r * DP + f];
+        const float VA = fmaf(wf, s2a, -s1a * s1a);
+        const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
+        const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
+        const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+        dist[f] = sqrtf(fmaxf(sq, 0.f));
+      }
+    }
+    if (ROWMIN) {
+      const float sm = sum_d_smallest<DP>(dist, D, d);
+      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+    } else {
+      const float sm = unsure ? 0.f : sum_d_smallest<DP>(dist, D, d);
+      if (sm <= thr) {
+        unsigned long long pos = atomicAdd(count, 1ull);
+        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
+      }
+    }
+  }
+}
+
 // Wide series (D > 16): per-window means and 1/sigma are read per step.
 template <int DM, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
 k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-           unsigned long long* __restrict__ count, float* __restrict__ rowmin) {
-  const int64_t delta = int64_t(ix.excl) + 1 + int64_t(blockIdx.y) * kDiagBlock + threadIdx.x;
+           unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+  const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
   const int64_t a1 = min(a0 + kSeg, ix.M - delta);
@@ -665,26 +793,42 @@ k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
   }
 }
 
+// the row kernel stages kSeg-1+w points of every dimension in shared memory
+bool rows_fit(int w, int dp) {
+  return size_t((kSeg - 1 + w) * dp + 2 * kSeg * dp + dp) * sizeof(float) <= size_t(200) * 1024;
+}
+
 template <bool ROWMIN>
 cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, uint64_t cap,
                               unsigned long long* count, float* rowmin, cudaStream_t s) {
   const int64_t ndiag = ix.M - (ix.excl + 1);
   if (ndiag <= 0) return cudaSuccess;
-  dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned((ndiag + kDiagBlock - 1) / kDiagBlock), 1u};
+  const int64_t gy = (ndiag + kDiagBlock - 1) / kDiagBlock;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+  dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
   if (ix.xT && ix.Dp == 4 && ix.has_lo)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
-  else if (ix.xT && ix.Dp == 4)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, false, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+  else if (ix.xT && ix.Dp == 4 && rows_fit(ix.w, 4)) {
+    const size_t smem = size_t((kSeg - 1 + ix.w) * 4 + 2 * kSeg * 4 + 4) * sizeof(float);
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<4, ROWMIN>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<4, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+  }
   else if (ix.xT && ix.Dp == 8 && ix.has_lo)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
-  else if (ix.xT && ix.Dp == 8)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, false, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+  else if (ix.xT && ix.Dp == 8 && rows_fit(ix.w, 8)) {
+    const size_t smem = size_t((kSeg - 1 + ix.w) * 8 + 2 * kSeg * 8 + 8) * sizeof(float);
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<8, ROWMIN>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<8, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+  }
   else if (ix.D <= 16)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
   else if (ix.D <= 32)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
   else
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+  }
   return cudaGetLastError();
 }
 
@@ -696,7 +840,7 @@ cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
 #define MOMENTI_VE(DM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, LO><<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
   const bool lo = ix.has_lo;
   if (ix.xT && ix.Dp == 4) { if (lo) MOMENTI_VE(4, true); else MOMENTI_VE(4, false); }
-  else if (ix.xT && ix.Dp == 8) { if (lo) MOMENTI_VE(8, true); else MOMENTI_VE(8, false); }
+  else if (ix.xT && ix.Dp == 8 && rows_fit(ix.w, 8)) { if (lo) MOMENTI_VE(8, true); else MOMENTI_VE(8, false); }
   else if (ix.D <= 16) MOMENTI_VE(16, false);
   else MOMENTI_VE(0, false);
 #undef MOMENTI_VE

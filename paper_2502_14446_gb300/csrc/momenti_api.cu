@@ -20,10 +20,13 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -221,6 +224,9 @@ struct momenti_handle {
   uint64_t* flags = nullptr;                // near-boundary list of the tensor-core form
   uint32_t flag_cap = 0;
   uint32_t* small = nullptr;                // r min/max, flag count, error flag
+  cudaStream_t own_stream = nullptr;        // created for the batching form
+  momenti_params built_p{};                 // parameters the index was built with
+  size_t rec_host_cap = 0;                  // pinned record buffer (kept across rebuilds)
 };
 
 namespace {
@@ -237,11 +243,42 @@ int fail(momenti_handle* h, int code, const std::string& msg) {
       return fail(h, MOMENTI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Device memory comes from one stream-ordered pool per device: a free is
+// queued on the handle's stream (no device-wide synchronisation, so the
+// handles of the batching form never stall one another) and freed blocks
+// stay in the pool for the next allocation until momenti_destroy or the end
+// of a batch trims it.
+cudaMemPool_t lib_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps pr{};
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &pr) != cudaSuccess) return nullptr;
+    uint64_t keep = ~uint64_t(0);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
+void trim_pool() {
+  if (cudaMemPool_t pool = lib_pool()) cudaMemPoolTrimTo(pool, 0);
+}
+
 template <typename T>
 cudaError_t dalloc(momenti_handle* h, T** ptr, size_t count) {
   size_t bytes = std::max<size_t>(count * sizeof(T), 16);
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return cudaErrorInitializationError;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, h->stream);
   if (e != cudaSuccess) return e;
   h->bufs.push_back(DevBuf{p, bytes});
   h->device_bytes += bytes;
@@ -249,16 +286,21 @@ cudaError_t dalloc(momenti_handle* h, T** ptr, size_t count) {
   return cudaSuccess;
 }
 
-void free_all(momenti_handle* h) {
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  else cudaDeviceSynchronize();
-  for (auto& b : h->bufs) cudaFree(b.p);
+// Releases the device buffers (queued on the handle's stream); the pinned
+// host buffers survive unless `host` is set.
+void free_all(momenti_handle* h, bool host = false) {
+  for (auto& b : h->bufs) cudaFreeAsync(b.p, h->stream);
   h->bufs.clear();
   h->device_bytes = 0;
-  if (h->rec_host) cudaFreeHost(h->rec_host);
-  if (h->cnt_host) cudaFreeHost(h->cnt_host);
-  h->rec_host = nullptr;
-  h->cnt_host = nullptr;
+  if (host) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    if (h->rec_host) cudaFreeHost(h->rec_host);
+    if (h->cnt_host) cudaFreeHost(h->cnt_host);
+    h->rec_host = nullptr;
+    h->cnt_host = nullptr;
+    h->rec_host_cap = 0;
+  }
   h->rec_dev = nullptr;
   h->draw_a = h->draw_u = nullptr;
   h->flags = nullptr;
@@ -509,8 +551,10 @@ int momenti_create(momenti_handle** out, const momenti_params* p) {
 
 void momenti_destroy(momenti_handle* h) {
   if (!h) return;
-  free_all(h);
+  free_all(h, true);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
+  trim_pool();
 }
 
 const char* momenti_last_error(const momenti_handle* h) {
@@ -548,9 +592,13 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     return fail(h, MOMENTI_ERR_ARG, "hash_all: D differs from set_hash_params");
   // a series of the same shape reuses every buffer of the previous index
   const bool reuse = h->ready && h->ix.n == n && h->ix.D == D &&
-                     h->ix.has_lo == (dtype == MOMENTI_F64) && h->built_gen == h->hp_gen;
+                     h->ix.has_lo == (dtype == MOMENTI_F64) && h->built_gen == h->hp_gen &&
+                     std::memcmp(&h->built_p, &h->p, sizeof(momenti_params)) == 0;
   if (!reuse) free_all(h);
   h->ready = false;
+  // buffers last used on another stream: let that work finish first
+  if (h->stream != static_cast<cudaStream_t>(stream) && !h->bufs.empty())
+    cudaStreamSynchronize(h->stream);
   h->stream = static_cast<cudaStream_t>(stream);
   cudaStream_t s = h->stream;
   Index& ix = h->ix;
@@ -624,6 +672,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     if (D <= 8) {
       ix.Dp = D <= 4 ? 4 : 8;
       CK(dalloc(h, &ix.xT, size_t(ix.Dp) * n));
+      CK(dalloc(h, &ix.stT, size_t(3) * ix.Dp * M));
       if (ix.has_lo) CK(dalloc(h, &ix.xlT, size_t(ix.Dp) * n));
       if (w >= 32) {
         CK(dalloc(h, &ix.smT, size_t(ix.Dp) * n));
@@ -685,9 +734,19 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     cs.ev_cap = uint64_t(1) << 22;
     h->ev_budget = std::max<uint64_t>(uint64_t(1) << 28, limit / 8);
     CK(dalloc(h, &cs.events, size_t(cs.ev_cap)));
-    CK(cudaMallocHost(&h->rec_host, new_cap * sizeof(PairRec)));
-    CK(cudaMallocHost(&h->cnt_host, 8 * sizeof(unsigned long long)));
+    if (h->rec_host_cap < new_cap) {
+      if (h->rec_host) {
+        cudaStreamSynchronize(s);
+        cudaFreeHost(h->rec_host);
+        h->rec_host = nullptr;
+      }
+      h->rec_host_cap = 0;
+      CK(cudaMallocHost(&h->rec_host, new_cap * sizeof(PairRec)));
+      h->rec_host_cap = new_cap;
+    }
+    if (!h->cnt_host) CK(cudaMallocHost(&h->cnt_host, 8 * sizeof(unsigned long long)));
     h->built_gen = h->hp_gen;
+    h->built_p = h->p;
   }
   const int L = ix.L, Wp = ix.Wp, N = L * kRepStride;
   (void)Wp;
@@ -706,6 +765,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
   CK(launch_point_major(ix, s));
   if (staging) CK(cudaFreeAsync(staging, s));
   CK(launch_window_stats(ix, s));
+  CK(launch_stats_point_major(ix, s));
 
   // ---- hash functions ----
   int L_src = L;
@@ -844,10 +904,13 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
           const uint64_t cap = next_pow2(cnt[1]);
           PairRec* rec = nullptr;
           CK(dalloc(h, &rec, size_t(cap)));
-          PairRec* rh = nullptr;
-          CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
-          cudaFreeHost(h->rec_host);
-          h->rec_host = rh;
+          if (h->rec_host_cap < cap) {
+            PairRec* rh = nullptr;
+            CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
+            cudaFreeHost(h->rec_host);
+            h->rec_host = rh;
+            h->rec_host_cap = cap;
+          }
           h->rec_dev = rec;
           h->rec_cap = cap;
           CK(cudaMemsetAsync(h->cs.counters + 1, 0, 7 * sizeof(unsigned long long), s));
@@ -937,6 +1000,77 @@ int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
   if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk_exact before hash_all");
   double err = 0;
   return exact_path(h, 0.0, out, n_out, &err);
+}
+
+int momenti_topk_batch(int32_t B, const momenti_params* params, const void* const* series,
+                       const int32_t* dtype, const int64_t* n, const int32_t* D, int32_t on_device,
+                       int32_t threads, momenti_motif* out, int32_t out_stride, int32_t* n_out,
+                       momenti_stats* stats, int32_t* rc, char* err, int32_t err_len) {
+  if (err && err_len > 0) err[0] = 0;
+  if (B < 0 || out_stride < 0) return MOMENTI_ERR_ARG;
+  if (B == 0) return MOMENTI_OK;
+  if (!params || !series || !dtype || !n || !D || !out || !n_out) return MOMENTI_ERR_ARG;
+  for (int32_t b = 0; b < B; ++b)
+    if (params[b].k > out_stride) return MOMENTI_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MOMENTI_ERR_CUDA;
+  // longest first (n * D windows to hash), so the tail of the batch is short
+  std::vector<int32_t> order(static_cast<size_t>(B));
+  for (int32_t b = 0; b < B; ++b) order[size_t(b)] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return double(n[x]) * D[x] > double(n[y]) * D[y];
+  });
+  int T = threads > 0 ? threads : 8;
+  if (T > B) T = B;
+  // a zero memory limit shares 80% of the free memory among the workers
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MOMENTI_ERR_CUDA;
+  const uint64_t share = uint64_t(0.8 * double(free_b) / T);
+  std::vector<int> status(size_t(B), MOMENTI_OK);
+  std::vector<std::string> messages(static_cast<size_t>(B));
+  std::atomic<int32_t> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    momenti_handle* h = new momenti_handle();
+    bool stream_ok = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (;;) {
+      const int32_t q = next.fetch_add(1);
+      if (q >= B) break;
+      const int32_t b = order[size_t(q)];
+      int r = MOMENTI_ERR_CUDA;
+      n_out[b] = 0;
+      momenti_handle* probe = nullptr;
+      if (!stream_ok) {
+        h->err = "topk_batch: cannot create a stream";
+      } else if ((r = momenti_create(&probe, &params[b])) == MOMENTI_OK) {
+        momenti_destroy(probe);
+        h->p = params[b];
+        if (h->p.mem_limit == 0) h->p.mem_limit = share;
+        r = momenti_hash_all(h, series[b], dtype[b], n[b], D[b], n[b], on_device, h->own_stream);
+        if (r == MOMENTI_OK)
+          r = momenti_topk(h, out + int64_t(b) * out_stride, n_out + b, stats ? stats + b : nullptr);
+      } else {
+        h->err = "topk_batch: invalid parameters";
+      }
+      status[size_t(b)] = r;
+      if (r != MOMENTI_OK) messages[size_t(b)] = h->err;
+    }
+    momenti_destroy(h);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  int first = MOMENTI_OK;
+  for (int32_t b = 0; b < B; ++b) {
+    if (rc) rc[b] = status[size_t(b)];
+    if (first == MOMENTI_OK && status[size_t(b)] != MOMENTI_OK) {
+      first = status[size_t(b)];
+      if (err && err_len > 0)
+        std::snprintf(err, size_t(err_len), "series %d: %s", int(b), messages[size_t(b)].c_str());
+    }
+  }
+  return first;
 }
 
 int momenti_verify(momenti_handle* h, const int64_t* pairs, int64_t m, double* per_dim,

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -33,6 +34,20 @@ Ev take_ev() {
 thread_local Ev t_cur{nullptr, nullptr};
 thread_local bool t_timing = false;
 }  // namespace
+
+cudaError_t allow_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& g = granted[{dev, func}];
+  if (bytes <= g) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) g = bytes;
+  return e;
+}
 
 void prof_begin(const char* name, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -31,7 +31,7 @@ EXPORTS = (
     "momenti_set_hash_params", "momenti_hash_all", "momenti_topk", "momenti_topk_exact",
     "momenti_verify", "momenti_get_info", "momenti_get_window_stats", "momenti_get_keys",
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
-    "momenti_kernel_time", "momenti_index_sort_noalloc",
+    "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
 )
 
 
@@ -87,6 +87,10 @@ def _load():
         "momenti_time_kernel": (C.c_int, [C.c_char_p]),
         "momenti_kernel_time": (C.c_int, [P(C.c_double), P(C.c_uint64)]),
         "momenti_index_sort_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, vp, vp, vp]),
+        "momenti_topk_batch": (C.c_int, [C.c_int32, P(momenti_params), P(vp), P(C.c_int32),
+                                         P(C.c_int64), P(C.c_int32), C.c_int32, C.c_int32,
+                                         P(momenti_motif), C.c_int32, P(C.c_int32),
+                                         P(momenti_stats), P(C.c_int32), C.c_char_p, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -133,6 +137,54 @@ def kernel_time():
     if rc != OK:
         raise MomentiError(rc, "momenti_kernel_time")
     return ms.value, int(n.value)
+
+
+def topk_batch(params, series_list, threads: int = 8):
+    """momenti_topk_batch: search every series of ``series_list`` ((D, n)
+    host arrays, or CUDA tensors all on the device) with ``params[b]`` (a
+    list of momenti_params or of keyword dicts for default_params).
+    Returns ``[(motifs, stats)]`` as Momenti.topk gives them, in order.
+    Raises MomentiError (naming the first failing series) if any failed."""
+    B = len(series_list)
+    assert len(params) == B
+    P = (momenti_params * B)()
+    for b, p in enumerate(params):
+        P[b] = p if isinstance(p, momenti_params) else default_params(**p)
+    keep = []
+    on_dev = int(bool(B) and hasattr(series_list[0], "is_cuda") and series_list[0].is_cuda)
+    ptrs = (C.c_void_p * B)()
+    dt = (C.c_int32 * B)()
+    ns = (C.c_int64 * B)()
+    Ds = (C.c_int32 * B)()
+    for b, x in enumerate(series_list):
+        if on_dev:
+            import torch
+            assert x.is_cuda and x.dim() == 2 and x.is_contiguous()
+            ptrs[b] = x.data_ptr()
+            dt[b] = F64 if x.dtype == torch.float64 else F32
+        else:
+            x = np.ascontiguousarray(np.asarray(x))
+            if x.dtype not in (np.float32, np.float64):
+                x = x.astype(np.float64)
+            ptrs[b] = x.ctypes.data
+            dt[b] = F64 if x.dtype == np.float64 else F32
+        Ds[b], ns[b] = x.shape
+        keep.append(x)
+    kmax = max([P[b].k for b in range(B)] + [1])
+    out = (momenti_motif * (B * kmax))()
+    n_out = (C.c_int32 * B)()
+    st = (momenti_stats * B)()
+    rcs = (C.c_int32 * B)()
+    err = C.create_string_buffer(512)
+    rc = lib.momenti_topk_batch(B, P, ptrs, dt, ns, Ds, on_dev, threads, out, kmax, n_out, st,
+                                rcs, err, 512)
+    if rc != OK:
+        raise MomentiError(rc, f"momenti_topk_batch: {err.value.decode() or 'invalid arguments'}")
+    res = []
+    for b in range(B):
+        motifs = Momenti._motifs(out[b * kmax:(b + 1) * kmax], n_out[b])
+        res.append((motifs, {name: getattr(st[b], name) for name, _ in momenti_stats._fields_}))
+    return res
 
 
 class Momenti:

@@ -6,7 +6,10 @@ small JSON record: the workload name and seed, the exact top-k motifs of
 Definition (top-k multidimensional motifs, Section 3.1) as
 [dist_d, a, b, dims, dist_max], and the oracle's wall time.
 
-Usage: python tests/golden/make_golden.py plain_small plain_fp32
+Usage: python tests/golden/make_golden.py plain_small plain_fp32 batch_small
+
+batch_small is the batching form at reduced lengths (6 series, n
+log-uniform in [1500, 5000]); its file holds one record per series.
 """
 import json
 import os
@@ -43,6 +46,28 @@ def make(name: str, seed: int = 0):
     print(path, f"{dt:.1f}s")
 
 
+def make_batch_small(seed: int = 0):
+    wls = synth.batch_form(seed, count=6, n_lo=1500, n_hi=5000)
+    recs = []
+    t0 = time.time()
+    for wl in wls:
+        res = O.exact_topk(wl.series, wl.w, wl.d, wl.k, block=256)
+        recs.append({
+            "workload": wl.name, "D": wl.D, "n": wl.n, "w": wl.w, "d": wl.d, "k": wl.k,
+            "planted": [[a, b, list(dims)] for a, b, dims in wl.planted],
+            "motifs": [[m[0], m[1], m[2], list(m[3]), m[4]] for m in res],
+        })
+    dt = time.time() - t0
+    path = os.path.join(OUT, f"exact_batch_small_seed{seed}.json")
+    with open(path, "w") as fh:
+        json.dump({"workload": "batch_small", "seed": seed, "series": recs,
+                   "oracle_seconds": dt}, fh, indent=1)
+    print(path, f"{dt:.1f}s")
+
+
 if __name__ == "__main__":
     for nm in sys.argv[1:] or ["plain_small"]:
-        make(nm)
+        if nm == "batch_small":
+            make_batch_small()
+        else:
+            make(nm)
