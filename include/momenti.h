@@ -84,6 +84,13 @@ typedef struct momenti_params {
 /* flags: count collisions at prefix length 1 with the pair tiles instead of
  * splitting buckets by a second dimension (same candidates; for tests). */
 #define MOMENTI_FLAG_TILES_ONLY 1u
+/* flags: follow Algorithm 1's loop to its end before the exact path (no
+ * cost switch).  By default each level starts with a one-repetition probe
+ * whose work counts predict the rest of the level; when that prediction
+ * exceeds the predicted time of the exact all-pairs path, the traversal
+ * stops there and the exact path runs (its result is the exact top-k, the
+ * probability-1 branch of Lemma topk). */
+#define MOMENTI_FLAG_NO_COST_SWITCH 2u
 
 /* One motif: windows a < b (0-based), dist_d (Definition distdims),
  * dist_d^max (Eq. distdmax), the dims_d set as a bit mask (bit f = dim f),
@@ -119,6 +126,11 @@ typedef struct momenti_stats {
   uint64_t n_rehashed;       /* tensor-core values re-hashed in FP32 (near a boundary) */
   int64_t  n_lb_pruned;      /* candidates dropped by the segment-mean lower bound    */
   double   t_host_ms;        /* host time replaying TOP and STOP in the traversal     */
+  int32_t  switch_level;     /* level i at which the cost switch chose the exact path, 0 = none */
+  int32_t  reserved2;
+  int64_t  n_pair_checks;    /* bucket pairs compared by collision counting           */
+  double   predicted_rest_ms;  /* cost model at the switch: rest of that level        */
+  double   predicted_exact_ms; /*   and the exact path                                */
 } momenti_stats;
 
 typedef struct momenti_handle momenti_handle;

@@ -149,7 +149,7 @@ struct CollideScratch {
   uint64_t ev_cap = 0;
   // [0] events (or plain pairs), [1] close records, [2] set inserts,
   // [3] events dropped by the lower bound, [4] verified pairs dropped at or
-  // above the threshold
+  // above the threshold, [5] pairs compared by the sub-bucket form
   unsigned long long* counters = nullptr;
   int64_t seg_cap = 0;            // segments the arrays can hold
   int64_t chunk_cap = 0;          // chunks per segment
@@ -172,7 +172,9 @@ cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s);
 struct BucketJob {
   uint32_t seg, start, n, pad;
 };
-constexpr int kSubBucketCap = 8192;      // members a CTA holds in shared memory (about 190 KB)
+// members of one bucket a CTA holds in shared memory: 8192 for D <= 8
+// (about 190 KB), 4096 for D <= 16
+int subbucket_cap(int D);
 // counts[0] = jobs, counts[1] = largest bucket
 cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob* jobs,
                                uint64_t job_cap, unsigned long long* counts, cudaStream_t s);
@@ -192,8 +194,24 @@ cudaError_t launch_verify_pairs(const Index& ix, int d, const uint64_t* pairs, i
                                 cudaStream_t s);
 // Exact all-pairs: every non-trivial pair with approximate dist_d <= tau
 // appended to out (a << 32 | b) with count in *count (may exceed cap).
-cudaError_t launch_allpairs(const Index& ix, int d, float tau, uint64_t* out, uint64_t cap,
-                            unsigned long long* count, cudaStream_t s);
+// Output of an all-pairs sweep: pairs whose approximate dist_d (float32
+// Pearson form, within 1% + 0.01 of the exact value) lies in (lo, thr]
+// go to out / out_d while count < cap; count counts them all and hist
+// (kApBins bins over (lo, thr], may be NULL) their distribution.
+constexpr int kApBins = 4096;
+struct ApRec {
+  uint64_t* out = nullptr;
+  float* out_d = nullptr;
+  uint64_t cap = 0;
+  unsigned long long* count = nullptr;
+  uint32_t* hist = nullptr;
+  float lo = -1.f;
+  float hscale = 0.f;          // kApBins / (thr - lo)
+};
+cudaError_t launch_allpairs(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s);
+// Recorded pairs whose approximate distance lies in (lo, hi], compacted.
+cudaError_t launch_select_pairs(const uint64_t* pairs, const float* dd, uint64_t m, float lo,
+                                float hi, uint64_t* out, unsigned long long* count, cudaStream_t s);
 // Row minima of dist_d over non-trivial partners (approximate), for the
 // first threshold of the all-pairs path; rowmin [M].
 cudaError_t launch_allpairs_rowmin(const Index& ix, int d, float* rowmin, cudaStream_t s);

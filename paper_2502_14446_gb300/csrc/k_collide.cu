@@ -449,14 +449,17 @@ struct SubArgs {
   int cap;
 };
 
+// NW byte-plane words per hash level: dims 8g .. 8g+7 in word g (D <= 8 NW).
+template <int NW>
 __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
   // members of one bucket: first and second hash values of every dim as
-  // byte planes (byte e = dim e), window ids, sub-bucket keys, permutation
+  // byte planes (byte e of word c = dim 8c + e), window ids, sub-bucket
+  // keys, permutation
   extern __shared__ uint64_t sub_smem[];
   const int cap = g.cap;
-  uint64_t* p0 = sub_smem;
-  uint64_t* p1 = p0 + cap;
-  uint32_t* widx = reinterpret_cast<uint32_t*>(p1 + cap);
+  uint64_t* p0 = sub_smem;                 // [NW][cap]
+  uint64_t* p1 = p0 + NW * cap;            // [NW][cap]
+  uint32_t* widx = reinterpret_cast<uint32_t*>(p1 + NW * cap);
   uint32_t* hist = widx + cap;
   uint32_t* bend = hist + 256;
   uint16_t* perm = reinterpret_cast<uint16_t*>(bend + 256);
@@ -464,9 +467,15 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int D = g.sg.D;
   const bool lvl_dup = g.K > 1;
-  const uint64_t valid0 = D >= 8 ? 0x8080808080808080ull
-                                 : (0x8080808080808080ull & ((1ull << (8 * D)) - 1));
+  uint64_t valid[NW];
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    const int nd = D - 8 * c;
+    valid[c] = nd >= 8 ? 0x8080808080808080ull
+                       : (nd <= 0 ? 0ull : (0x8080808080808080ull & ((1ull << (8 * nd)) - 1)));
+  }
   uint64_t njobs = g.counts[0];
+  unsigned long long checks = 0;                   // pairs compared by this thread
   for (uint64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
     const BucketJob job = g.jobs[jb];
     const int n = int(job.n);
@@ -480,22 +489,26 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       const uint32_t wv = O[q];
       widx[q] = wv;
       const uint64_t* kw = Kj + int64_t(wv) * D;
-      uint64_t a0 = 0, a1 = 0;
-      for (int e = 0; e < D; ++e) {
-        const uint64_t key = kw[e];
-        a0 |= (key >> 56) << (8 * e);
-        a1 |= ((key >> 48) & 0xFFull) << (8 * e);
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        uint64_t a0 = 0, a1 = 0;
+        for (int e = 0; e < 8 && 8 * c + e < D; ++e) {
+          const uint64_t key = kw[8 * c + e];
+          a0 |= (key >> 56) << (8 * e);
+          a1 |= ((key >> 48) & 0xFFull) << (8 * e);
+        }
+        p0[c * cap + q] = a0;
+        p1[c * cap + q] = a1;
       }
-      p0[q] = a0;
-      p1[q] = a1;
     }
     __syncthreads();
     // second-lowest colliding dim f2 leaves d - 2 dims above it
     for (int f2 = f + 1; f2 <= D - g.d + 1; ++f2) {
       for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
       __syncthreads();
+      const int c2 = f2 >> 3, e2 = f2 & 7;
       for (int q = tid; q < n; q += blockDim.x) {
-        const uint8_t k = uint8_t(p0[q] >> (8 * f2));
+        const uint8_t k = uint8_t(p0[c2 * cap + q] >> (8 * e2));
         skey[q] = k;
         atomicAdd(&hist[k], 1u);
       }
@@ -521,21 +534,42 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       __syncthreads();
       for (int b = tid; b < 256; b += blockDim.x) bend[b] = hist[b];
       __syncthreads();
-      // pairs inside a sub-bucket collide in f and f2 (first hash value)
-      const uint64_t below = ((1ull << (8 * f2)) - 1) & valid0;   // bytes of dims < f2
-      const uint64_t only_f = 0x80ull << (8 * f);
+      // pairs inside a sub-bucket collide in f and f2 (first hash value);
+      // below[c]: bytes of dims < f2 in word c, only_f[c]: the byte of f
+      uint64_t below[NW], only_f[NW];
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        const uint64_t all = c < c2 ? ~0ull : (c == c2 ? ((1ull << (8 * e2)) - 1) : 0ull);
+        below[c] = all & valid[c];
+        only_f[c] = (f >> 3) == c ? (0x80ull << (8 * (f & 7))) : 0ull;
+      }
       for (int r = tid; r < n; r += blockDim.x) {
         const int u = perm[r];
         const int end = int(bend[skey[u]]);
-        const uint64_t pu0 = p0[u], pu1 = p1[u];
+        uint64_t pu0[NW], pu1[NW];
+#pragma unroll
+        for (int c = 0; c < NW; ++c) { pu0[c] = p0[c * cap + u]; pu1[c] = p1[c * cap + u]; }
         const uint32_t wu = widx[u];
+        checks += (unsigned long long)(end > r + 1 ? end - r - 1 : 0);
         for (int r2 = r + 1; r2 < end; ++r2) {
           const int v = perm[r2];
-          const uint64_t m = zero_bytes(pu0 ^ p0[v]) & valid0;
-          // f and f2 are the two lowest colliding dims
-          if ((m & below) != only_f) continue;
-          if (__popcll(m) < g.d) continue;
-          if (lvl_dup && __popcll(m & zero_bytes(pu1 ^ p1[v])) >= g.d) continue;
+          uint64_t m[NW];
+          bool lowest = true;
+          int w0 = 0;
+#pragma unroll
+          for (int c = 0; c < NW; ++c) {
+            m[c] = zero_bytes(pu0[c] ^ p0[c * cap + v]) & valid[c];
+            // f and f2 are the two lowest colliding dims
+            lowest = lowest && (m[c] & below[c]) == only_f[c];
+            w0 += __popcll(m[c]);
+          }
+          if (!lowest || w0 < g.d) continue;
+          if (lvl_dup) {
+            int w1 = 0;
+#pragma unroll
+            for (int c = 0; c < NW; ++c) w1 += __popcll(m[c] & zero_bytes(pu1[c] ^ p1[c * cap + v]));
+            if (w1 >= g.d) continue;
+          }
           const uint32_t wv = widx[v];
           const uint32_t a = min(wu, wv), b = max(wu, wv);
           if (int64_t(b) - int64_t(a) <= g.excl) continue;
@@ -553,6 +587,8 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       __syncthreads();
     }
   }
+  for (int o = 16; o > 0; o >>= 1) checks += __shfl_xor_sync(0xffffffffu, checks, o);
+  if (lane == 0 && checks) atomicAdd(&g.counters[5], checks);
 }
 
 __global__ void k_hs_clear(uint64_t* __restrict__ keys, uint64_t cap) {
@@ -601,24 +637,34 @@ cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob
   return cudaGetLastError();
 }
 
-size_t subbucket_smem(int cap) {
-  return size_t(cap) * (8 + 8 + 4 + 2 + 1) + 2 * 256 * 4 + 16;
+size_t subbucket_smem(int cap, int D) {
+  const int nw = (D + 7) / 8;
+  return size_t(cap) * (16 * nw + 4 + 2 + 1) + 2 * 256 * 4 + 16;
 }
+
+int subbucket_cap(int D) { return D <= 8 ? 8192 : 4096; }
 
 cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashSet& hs,
                              const CollideScratch& cs, const BucketJob* jobs,
                              const unsigned long long* counts, int max_bucket, cudaStream_t s) {
+  if (ix.D > 16 || max_bucket > subbucket_cap(ix.D)) return cudaErrorInvalidValue;
   Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
   const int cap = ((max_bucket + 255) / 256) * 256;
   SubArgs g{ix.order, ix.keys, sg, ix.K, d, ix.excl, hs, cs.events, cs.ev_cap, cs.counters, jobs,
             counts, cap};
-  const size_t smem = subbucket_smem(cap);
-  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket), smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = subbucket_smem(cap, ix.D);
   int per_sm = int((size_t(200) * 1024) / smem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
-  MOMENTI_LAUNCH("subbucket", s, k_subbucket<<<152 * per_sm, 256, smem, s>>>(g));
+  if (ix.D <= 8) {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket<1>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("subbucket", s, k_subbucket<1><<<152 * per_sm, 256, smem, s>>>(g));
+  } else {
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket<2>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("subbucket", s, k_subbucket<2><<<152 * per_sm, 256, smem, s>>>(g));
+  }
   return cudaGetLastError();
 }
 

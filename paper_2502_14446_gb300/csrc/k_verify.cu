@@ -276,7 +276,8 @@ __device__ __forceinline__ float dist_d_lower_bound(const Index& ix, uint32_t a,
 // One warp per candidate event (each warp a contiguous range of events):
 // distances; a pair with dist_d < tau is recorded (with its repetition) and
 // offered to the set of close pairs.
-template <int DM, bool LO>
+// DM: dims held per lane (0 = any D); PM: the point-major copies (DP = DM)
+template <int DM, bool PM, bool LO>
 __global__ void __launch_bounds__(256)
 k_verify_events(Index ix, int d, HashSet hs, const Event* __restrict__ ev,
                 unsigned long long* __restrict__ counters, uint64_t ev_cap, float tau,
@@ -289,15 +290,15 @@ k_verify_events(Index ix, int d, HashSet hs, const Event* __restrict__ ev,
   const uint64_t q0 = cnt * w / nw, q1 = cnt * (w + 1) / nw;
   for (uint64_t q = q0; q < q1; ++q) {
     const Event e = ev[q];
-    if ((DM == 4 || DM == 8) && ix.smT) {
-      const float lb = dist_d_lower_bound<(DM == 4 ? 4 : 8)>(ix, e.a, e.b, d);
+    if (PM && ix.smT) {
+      const float lb = dist_d_lower_bound<(PM ? DM : 4)>(ix, e.a, e.b, d);
       if (lb > tau * (1.f + 1e-3f) + 1e-3f) {          // provably not below tau
         if (lane == 0) atomicAdd(&counters[3], 1ull);
         continue;
       }
     }
     float dist[2];
-    if (DM == 4 || DM == 8) pair_distances_pm<(DM == 4 ? 4 : 8), LO>(ix, e.a, e.b, dist);
+    if (PM) pair_distances_pm<(PM ? DM : 4), LO>(ix, e.a, e.b, dist);
     else if (DM > 0) pair_distances_fast<(DM > 0 ? DM : 1)>(ix, e.a, e.b, dist);
     else pair_distances<float>(ix, e.a, e.b, dist);
     VerifyOut v = select_d<float>(dist, ix.D, d);
@@ -372,6 +373,22 @@ k_verify_pairs(Index ix, int d, const uint64_t* __restrict__ pairs, int64_t m, i
 
 // ---- all pairs ------------------------------------------------------------
 
+// A pair whose approximate dist_d lies in (rc.lo, thr]: appended (with its
+// approximate distance) while there is room, and counted in the histogram
+// of (rc.lo, thr] either way.
+__device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t b, float dd) {
+  const unsigned long long pos = atomicAdd(rc.count, 1ull);
+  if (pos < rc.cap) {
+    rc.out[pos] = (uint64_t(a) << 32) | uint64_t(b);
+    rc.out_d[pos] = dd;
+  }
+  if (rc.hist) {
+    const float x = (dd - rc.lo) * rc.hscale;
+    const int bin = x < float(kApBins - 1) ? int(fmaxf(x, 0.f)) : kApBins - 1;
+    atomicAdd(&rc.hist[bin], 1u);
+  }
+}
+
 constexpr int kSeg = 64;        // diagonal steps between direct restarts
 constexpr int kDiagBlock = 128; // diagonals per CTA
 
@@ -381,8 +398,7 @@ __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t)
 
 template <int DM, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
-k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-           unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+k_allpairs(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
@@ -412,7 +428,6 @@ k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
       qt[f] = q; s1a[f] = u1; s2a[f] = u2; s1b[f] = v1; s2b[f] = v2;
     }
   }
-  const float thr = tau * 1.01f + 1e-2f;
   for (int64_t a = a0; a < a1; ++a) {
     const int64_t b = a + delta;
     float dist[DM];
@@ -457,10 +472,7 @@ k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
       atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(s));
     } else if (near >= d || unsure) {
       float s = unsure ? 0.f : sum_d_smallest<DM>(dist, D, d);
-      if (s <= thr) {
-        unsigned long long pos = atomicAdd(count, 1ull);
-        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
-      }
+      if (s <= thr && s > rc.lo) record_pair(rc, a, b, s);
     }
   }
 }
@@ -471,8 +483,7 @@ k_allpairs(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
 // per step.
 template <int DP, bool LO, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock, 4)
-k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-              unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+k_allpairs_pm(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
@@ -509,7 +520,6 @@ k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t c
       s2b[f] = fmaf(v, v, s2b[f]);
     }
   }
-  const float thr = tau * 1.01f + 1e-2f;
   const float c0 = 1.f - thr * thr / (2.f * wf);
   const float c0sq = c0 * c0;
   for (int64_t a = a0; a < a1; ++a) {
@@ -585,10 +595,7 @@ k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t c
       atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
     } else if (near >= d || unsure) {
       const float sm = unsure ? 0.f : sum_d_smallest<DP>(dist, D, d);
-      if (sm <= thr) {
-        unsigned long long pos = atomicAdd(count, 1ull);
-        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
-      }
+      if (sm <= thr && sm > rc.lo) record_pair(rc, a, b, sm);
     }
   }
 }
@@ -599,8 +606,7 @@ k_allpairs_pm(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t c
 // memory; each thread keeps the column sums and the cross product.
 template <int DP, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
-k_allpairs_rows(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-                unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   extern __shared__ float ap_smem[];
   const int w = ix.w, D = ix.D;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
@@ -661,7 +667,6 @@ k_allpairs_rows(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
       s2b[f] = fmaf(v, v, s2b[f]);
     }
   }
-  const float thr = tau * 1.01f + 1e-2f;
   const float c0 = 1.f - thr * thr / (2.f * wf);
   const float c0sq = c0 * c0;
   for (int64_t a = a0; a < a1; ++a) {
@@ -713,10 +718,7 @@ k_allpairs_rows(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
       atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
     } else {
       const float sm = unsure ? 0.f : sum_d_smallest<DP>(dist, D, d);
-      if (sm <= thr) {
-        unsigned long long pos = atomicAdd(count, 1ull);
-        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
-      }
+      if (sm <= thr && sm > rc.lo) record_pair(rc, a, b, sm);
     }
   }
 }
@@ -724,8 +726,7 @@ k_allpairs_rows(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
 // Wide series (D > 16): per-window means and 1/sigma are read per step.
 template <int DM, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
-k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t cap,
-           unsigned long long* __restrict__ count, float* __restrict__ rowmin, int64_t ybase) {
+k_allpairs_wide(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
   if (delta >= ix.M || a0 >= ix.M - delta) return;
@@ -748,7 +749,6 @@ k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
       qt[f] = s;
     }
   }
-  const float thr = tau * 1.01f + 1e-2f;
   for (int64_t a = a0; a < a1; ++a) {
     const int64_t b = a + delta;
     if (a > a0) {
@@ -785,10 +785,7 @@ k_allpairs_wide(Index ix, int d, float tau, uint64_t* __restrict__ out, uint64_t
       atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(s));
     } else if (near >= d) {
       float s = sum_d_smallest<DM>(dist, D, d);
-      if (s <= thr) {
-        unsigned long long pos = atomicAdd(count, 1ull);
-        if (pos < cap) out[pos] = (uint64_t(a) << 32) | uint64_t(b);
-      }
+      if (s <= thr && s > rc.lo) record_pair(rc, a, b, s);
     }
   }
 }
@@ -799,35 +796,43 @@ bool rows_fit(int w, int dp) {
 }
 
 template <bool ROWMIN>
-cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, uint64_t cap,
-                              unsigned long long* count, float* rowmin, cudaStream_t s) {
+cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc, float* rowmin,
+                              cudaStream_t s) {
   const int64_t ndiag = ix.M - (ix.excl + 1);
   if (ndiag <= 0) return cudaSuccess;
   const int64_t gy = (ndiag + kDiagBlock - 1) / kDiagBlock;
   for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
   dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
   if (ix.xT && ix.Dp == 4 && ix.has_lo)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.xT && ix.Dp == 4 && rows_fit(ix.w, 4)) {
     const size_t smem = size_t((kSeg - 1 + ix.w) * 4 + 2 * kSeg * 4 + 4) * sizeof(float);
     cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<4, ROWMIN>), smem);
     if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<4, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<4, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
   }
   else if (ix.xT && ix.Dp == 8 && ix.has_lo)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.xT && ix.Dp == 8 && rows_fit(ix.w, 8)) {
     const size_t smem = size_t((kSeg - 1 + ix.w) * 8 + 2 * kSeg * 8 + 8) * sizeof(float);
     cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<8, ROWMIN>), smem);
     if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<8, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<8, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
+  }
+  else if (ix.xT && ix.Dp == 16 && ix.has_lo)
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<16, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
+  else if (ix.xT && ix.Dp == 16 && rows_fit(ix.w, 16)) {
+    const size_t smem = size_t((kSeg - 1 + ix.w) * 16 + 2 * kSeg * 16 + 16) * sizeof(float);
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<16, ROWMIN>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<16, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
   }
   else if (ix.D <= 16)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.D <= 32)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, tau, out, cap, count, rowmin, y0));
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   }
   return cudaGetLastError();
 }
@@ -837,12 +842,13 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float tau, uint64_t* out, 
 cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
                                  const CollideScratch& cs, float tau, PairRec* rec,
                                  uint64_t rec_cap, cudaStream_t s) {
-#define MOMENTI_VE(DM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, LO><<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
+#define MOMENTI_VE(DM, PM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, PM, LO><<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
   const bool lo = ix.has_lo;
-  if (ix.xT && ix.Dp == 4) { if (lo) MOMENTI_VE(4, true); else MOMENTI_VE(4, false); }
-  else if (ix.xT && ix.Dp == 8 && rows_fit(ix.w, 8)) { if (lo) MOMENTI_VE(8, true); else MOMENTI_VE(8, false); }
-  else if (ix.D <= 16) MOMENTI_VE(16, false);
-  else MOMENTI_VE(0, false);
+  if (ix.xT && ix.Dp == 4) { if (lo) MOMENTI_VE(4, true, true); else MOMENTI_VE(4, true, false); }
+  else if (ix.xT && ix.Dp == 8) { if (lo) MOMENTI_VE(8, true, true); else MOMENTI_VE(8, true, false); }
+  else if (ix.xT && ix.Dp == 16) { if (lo) MOMENTI_VE(16, true, true); else MOMENTI_VE(16, true, false); }
+  else if (ix.D <= 16) MOMENTI_VE(16, false, false);
+  else MOMENTI_VE(0, false, false);
 #undef MOMENTI_VE
   return cudaGetLastError();
 }
@@ -857,13 +863,38 @@ cudaError_t launch_verify_pairs(const Index& ix, int d, const uint64_t* pairs, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_allpairs(const Index& ix, int d, float tau, uint64_t* out, uint64_t cap,
-                            unsigned long long* count, cudaStream_t s) {
-  return allpairs_dispatch<false>(ix, d, tau, out, cap, count, nullptr, s);
+// Recorded pairs whose approximate distance lies in (lo, hi], compacted.
+__global__ void k_select_pairs(const uint64_t* __restrict__ pairs, const float* __restrict__ dd,
+                               uint64_t m, float lo, float hi, uint64_t* __restrict__ out,
+                               unsigned long long* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  for (uint64_t q0 = blockIdx.x * uint64_t(blockDim.x); q0 < m; q0 += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t q = q0 + threadIdx.x;
+    const bool keep = q < m && dd[q] > lo && dd[q] <= hi;
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask) continue;
+    unsigned long long base = 0;
+    if (lane == __ffs(mask) - 1) base = atomicAdd(count, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    if (keep) out[base + __popc(mask & ((1u << lane) - 1u))] = pairs[q];
+  }
+}
+
+cudaError_t launch_select_pairs(const uint64_t* pairs, const float* dd, uint64_t m, float lo,
+                                float hi, uint64_t* out, unsigned long long* count, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  uint64_t g = (m + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  MOMENTI_LAUNCH("select_pairs", s, k_select_pairs<<<unsigned(g), 256, 0, s>>>(pairs, dd, m, lo, hi, out, count));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_allpairs(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s) {
+  return allpairs_dispatch<false>(ix, d, thr, rc, nullptr, s);
 }
 
 cudaError_t launch_allpairs_rowmin(const Index& ix, int d, float* rowmin, cudaStream_t s) {
-  return allpairs_dispatch<true>(ix, d, 0.f, nullptr, 0, nullptr, rowmin, s);
+  return allpairs_dispatch<true>(ix, d, 0.f, ApRec{}, rowmin, s);
 }
 
 }  // namespace momenti

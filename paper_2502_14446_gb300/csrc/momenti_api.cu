@@ -25,6 +25,7 @@
 #include <thread>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -315,6 +316,29 @@ void free_all(momenti_handle* h, bool host = false) {
   h->ready = false;
 }
 
+// Work model of the traversal and of the exact path, in milliseconds on a
+// GB300 (fitted to measured kernel times; only the ratio of the two
+// predictions matters).  Per repetition of a level: pair tiles compared,
+// sub-bucket pairs compared, events (each gets the segment-mean lower
+// bound), full verifications, records handed to TOP on the host.
+double predict_rep_ms(const Index& ix, uint64_t tiles, uint64_t sub_checks, uint64_t events,
+                      uint64_t verified, uint64_t records) {
+  const double G = double((ix.D + 7) / 8);
+  const double verify_ns = 2.0 * double(ix.w) * double(ix.Dp ? ix.Dp : ix.D) / 2400.0 + 0.5;
+  return 1e-6 * (2.5 * G * double(tiles) + 0.4 * double(sub_checks) + 0.8 * double(events) +
+                 verify_ns * double(verified) + 100.0 * double(records));
+}
+
+double predict_exact_ms(const Index& ix, int passes) {
+  double ps_pair;                                  // all-pairs kernel, per pair
+  if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 8.0;
+  else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 25.0;
+  else if (ix.xT && !ix.has_lo && ix.Dp == 16) ps_pair = 75.0;
+  else ps_pair = 10.0 * double(ix.D);
+  const double pairs = 0.5 * double(ix.M) * double(ix.M);
+  return double(passes) * (ps_pair * 1e-9 * pairs + 0.2) + 2.0;
+}
+
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
@@ -445,72 +469,157 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     }
     tau = std::max(val * 1.2, 1e-3);
   }
-  uint64_t cap = uint64_t(1) << 22;
-  for (int attempt = 0; attempt < 64; ++attempt) {
-    uint64_t* dout = nullptr;
-    unsigned long long* dcnt = nullptr;
-    CK(cudaMallocAsync(&dout, cap * 8, h->stream));
-    CK(cudaMallocAsync(&dcnt, 8, h->stream));
+  if (const char* t0 = std::getenv("MOMENTI_TRACE"); t0 && t0[0] == '1')
+    std::fprintf(stderr, "momenti trace: exact tau=%.5g (%s)\n", tau, tau0 > 0 ? "from TOP" : "from row minima");
+  // Pairs are taken in slices of their approximate dist_d (float32 Pearson
+  // form, within 1% + 0.01 of the exact value): each all-pairs sweep records
+  // the pairs with approximate distance in (lo, hi] and a histogram of them;
+  // they are verified in ascending batches (float32, direct form) and added
+  // to the candidates, and greedy runs after every batch.  Once every pair
+  // with exact dist_d <= e is held (e = (edge - 0.01) / 1.01 for the upper
+  // edge of what has been taken) and greedy's k-th is below e, the prefix is
+  // exact.
+  std::vector<PoolEntry> got;
+  const char* tr = std::getenv("MOMENTI_TRACE");
+  const bool trace = tr && tr[0] == '1';
+  auto add_batch = [&](const uint64_t* dpairs, int64_t m) -> int {
+    if (m <= 0) return MOMENTI_OK;
+    double *dpd = nullptr, *ddd = nullptr;
+    uint64_t* dmask = nullptr;
+    CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
+    CK(cudaMallocAsync(&ddd, m * 8, h->stream));
+    CK(cudaMallocAsync(&dmask, m * 8, h->stream));
+    CK(launch_verify_pairs(ix, h->p.d, dpairs, m, 0, dpd, ddd, dmask, h->stream));
+    std::vector<uint64_t> pk(m), mk(m);
+    std::vector<double> per(m * ix.D), dd(m);
+    CK(cudaMemcpyAsync(pk.data(), dpairs, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(per.data(), dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(dd.data(), ddd, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(mk.data(), dmask, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(dpd, h->stream));
+    CK(cudaFreeAsync(ddd, h->stream));
+    CK(cudaFreeAsync(dmask, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const size_t old_n = got.size();
+    for (int64_t q = 0; q < m; ++q) {
+      double mx = 0;
+      for (int f = 0; f < ix.D; ++f)
+        if (mk[q] >> f & 1) mx = std::max(mx, per[q * ix.D + f]);
+      got.push_back(PoolEntry{dd[q], mx, uint32_t(pk[q] >> 32), uint32_t(pk[q]), mk[q]});
+    }
+    // got stays sorted: sort the batch, merge it in
+    std::sort(got.begin() + old_n, got.end(), pair_less);
+    std::inplace_merge(got.begin(), got.begin() + old_n, got.end(), pair_less);
+    return MOMENTI_OK;
+  };
+  // greedy over everything taken; true when its k-th lies below e
+  auto exact_below = [&](double e) -> bool {
+    auto acc = greedy(got, k, ix.excl);
+    return int(acc.size()) == k && got[acc.back()].dd * (1.0 + 1e-4) + 1e-6 <= e;
+  };
+  // no pair has an approximate distance above this
+  const float all_edge = float(2.0 * std::sqrt(double(ix.w)) * h->p.d * 1.01 + 0.02);
+  constexpr int64_t kBatch = int64_t(1) << 16;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const uint64_t cap_max = std::max<uint64_t>(uint64_t(1) << 22,
+                                              std::min<uint64_t>(uint64_t(1) << 30, free_b / 4 / 12));
+  uint64_t cap = std::min<uint64_t>(uint64_t(1) << 24, cap_max);
+  float lo = -1.f;
+  float hi = std::min(float(tau) * 1.01f + 1e-2f, all_edge);
+  uint64_t* dout = nullptr;
+  float* dval = nullptr;
+  unsigned long long* dcnt = nullptr;
+  uint32_t* dhist = nullptr;
+  uint64_t* dsel = nullptr;
+  auto release = [&]() {
+    if (dout) cudaFreeAsync(dout, h->stream);
+    if (dval) cudaFreeAsync(dval, h->stream);
+    if (dsel) cudaFreeAsync(dsel, h->stream);
+    dout = nullptr;
+    dval = nullptr;
+    dsel = nullptr;
+  };
+  CK(cudaMallocAsync(&dcnt, 8, h->stream));
+  CK(cudaMallocAsync(&dhist, kApBins * 4, h->stream));
+  std::vector<uint32_t> hist(kApBins);
+  int rc = MOMENTI_ERR_OVERFLOW;
+  for (int pass = 0; pass < 64; ++pass) {
+    if (!dout) {
+      CK(cudaMallocAsync(&dout, cap * 8, h->stream));
+      CK(cudaMallocAsync(&dval, cap * 4, h->stream));
+    }
     CK(cudaMemsetAsync(dcnt, 0, 8, h->stream));
-    CK(launch_allpairs(ix, h->p.d, float(tau), dout, cap, dcnt, h->stream));
+    CK(cudaMemsetAsync(dhist, 0, kApBins * 4, h->stream));
+    ApRec ar;
+    ar.out = dout;
+    ar.out_d = dval;
+    ar.cap = cap;
+    ar.count = dcnt;
+    ar.hist = dhist;
+    ar.lo = lo;
+    ar.hscale = float(kApBins) / (hi - lo);
+    CK(launch_allpairs(ix, h->p.d, hi, ar, h->stream));
     unsigned long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(hist.data(), dhist, kApBins * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (trace)
+      std::fprintf(stderr, "momenti trace: exact pass=%d lo=%.5g hi=%.5g pairs=%llu cap=%llu held=%zu\n",
+                   pass, double(lo), double(hi), cnt, (unsigned long long)cap, got.size());
+    const double width = double(hi - lo) / kApBins;
     if (cnt > cap) {
-      CK(cudaFreeAsync(dout, h->stream));
-      CK(cudaFreeAsync(dcnt, h->stream));
-      if (cnt > (uint64_t(1) << 28)) {
-        tau *= 0.5;
-        continue;
+      release();
+      if (cnt <= cap_max) {
+        cap = (uint64_t(cnt) + (uint64_t(1) << 20)) & ~((uint64_t(1) << 20) - 1);
+      } else {
+        // the largest upper edge whose pairs fit
+        uint64_t run = 0;
+        int bin = 0;
+        for (; bin < kApBins; ++bin) {
+          if (run + hist[bin] > cap_max) break;
+          run += hist[bin];
+        }
+        cap = cap_max;
+        if (bin == 0) return fail(h, MOMENTI_ERR_MEMORY, "exact path: one distance bin exceeds memory");
+        hi = float(double(lo) + width * bin);
       }
-      cap = next_pow2(cnt);
-      --attempt;
       continue;
     }
-    const int64_t m = int64_t(cnt);
-    std::vector<PoolEntry> cand;
-    if (m > 0) {
-      double *dpd = nullptr, *ddd = nullptr;
-      uint64_t* dmask = nullptr;
-      CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
-      CK(cudaMallocAsync(&ddd, m * 8, h->stream));
-      CK(cudaMallocAsync(&dmask, m * 8, h->stream));
-      CK(launch_verify_pairs(ix, h->p.d, dout, m, 0, dpd, ddd, dmask, h->stream));
-      std::vector<uint64_t> pk(m), mk(m);
-      std::vector<double> per(m * ix.D), dd(m);
-      CK(cudaMemcpyAsync(pk.data(), dout, m * 8, cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaMemcpyAsync(per.data(), dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaMemcpyAsync(dd.data(), ddd, m * 8, cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaMemcpyAsync(mk.data(), dmask, m * 8, cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaFreeAsync(dpd, h->stream));
-      CK(cudaFreeAsync(ddd, h->stream));
-      CK(cudaFreeAsync(dmask, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      cand.reserve(m);
-      for (int64_t q = 0; q < m; ++q) {
-        if (dd[q] > tau) continue;
-        double mx = 0;
-        for (int f = 0; f < ix.D; ++f)
-          if (mk[q] >> f & 1) mx = std::max(mx, per[q * ix.D + f]);
-        cand.push_back(PoolEntry{dd[q], mx, uint32_t(pk[q] >> 32), uint32_t(pk[q]), mk[q]});
+    // ascending batches of whole bins
+    CK(cudaMallocAsync(&dsel, std::max<uint64_t>(cnt, 1) * 8, h->stream));
+    bool done = false;
+    for (int b0 = 0; b0 < kApBins && !done;) {
+      int b1 = b0;
+      uint64_t run = 0;
+      while (b1 < kApBins && (b1 == b0 || run + hist[b1] <= uint64_t(kBatch))) run += hist[b1++];
+      const float slo = b0 == 0 ? lo : float(double(lo) + width * b0);
+      const float shi = b1 == kApBins ? hi : float(double(lo) + width * b1);
+      if (run > 0) {
+        CK(cudaMemsetAsync(dcnt, 0, 8, h->stream));
+        CK(launch_select_pairs(dout, dval, cnt, slo, shi, dsel, dcnt, h->stream));
+        unsigned long long ns = 0;
+        CK(cudaMemcpyAsync(&ns, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const int r = add_batch(dsel, int64_t(ns));
+        if (r != MOMENTI_OK) return r;
       }
+      done = exact_below((double(shi) - 1e-2) / 1.01);
+      b0 = b1;
     }
-    CK(cudaFreeAsync(dout, h->stream));
-    CK(cudaFreeAsync(dcnt, h->stream));
-    std::sort(cand.begin(), cand.end(), pair_less);
-    auto acc = greedy(cand, k, ix.excl);
-    // every pair with dist_d <= tau is held, so the greedy prefix is exact
-    // once k pairs are taken at or below tau; the float64 re-check keeps a
-    // margin for pairs near tau
-    if (int(acc.size()) == k && cand[acc.back()].dd * (1.0 + 1e-4) + 1e-6 <= tau)
-      return finalize(h, cand, out, n_out, 0.0, max_err);
-    if (int(acc.size()) < k && tau > 4.0 * std::sqrt(double(ix.w)) * h->p.d) {
-      // every pair is below tau: fewer than k non-trivial motifs exist
-      return finalize(h, cand, out, n_out, 0.0, max_err);
+    release();
+    if (done || hi >= all_edge) {
+      // done, or every pair is held: fewer than k non-trivial motifs exist
+      rc = finalize(h, got, out, n_out, 0.0, max_err);
+      break;
     }
-    tau *= 2.0;
+    lo = hi;
+    hi = std::min(2.f * hi + 1e-2f, all_edge);
   }
-  return fail(h, MOMENTI_ERR_OVERFLOW, "exact path: threshold search did not converge");
+  cudaFreeAsync(dcnt, h->stream);
+  cudaFreeAsync(dhist, h->stream);
+  if (rc == MOMENTI_ERR_OVERFLOW) return fail(h, rc, "exact path: threshold search did not converge");
+  return rc;
 }
 
 }  // namespace
@@ -614,6 +723,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     const uint64_t fixed = uint64_t(D) * n * (dtype == MOMENTI_F64 ? 8 : 4)  // series hi/lo
                            + uint64_t(D) * n * elem                          // transient staging
                            + uint64_t(D) * M * (8 + 8 + 4 + 4 + 4)           // stats
+                           + (D <= 16 ? uint64_t(16) * (3 * n + 3 * M) * 4 : 0)  // point-major copies
                            + (uint64_t(64) << 20);                           // small scratch
     const uint64_t per_rep = uint64_t(M) * D * (8 + 4 + 1)                   // keys, order, lcp
                              + uint64_t(D) * kRepStride * Wp * (2 + 4)       // a16, a32
@@ -669,8 +779,8 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     const int N = L * kRepStride;
     CK(dalloc(h, &ix.xs_hi, size_t(D) * n));
     if (ix.has_lo) CK(dalloc(h, &ix.xs_lo, size_t(D) * n));
-    if (D <= 8) {
-      ix.Dp = D <= 4 ? 4 : 8;
+    if (D <= 16) {
+      ix.Dp = D <= 4 ? 4 : (D <= 8 ? 8 : 16);
       CK(dalloc(h, &ix.xT, size_t(ix.Dp) * n));
       CK(dalloc(h, &ix.stT, size_t(3) * ix.Dp * M));
       if (ix.has_lo) CK(dalloc(h, &ix.xlT, size_t(ix.Dp) * n));
@@ -726,7 +836,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     HashSet& hs = h->hs;
     hs.cap = hs_cap;
     CK(dalloc(h, &hs.keys, size_t(hs_cap)));
-    if (D <= 8 && p.d >= 2) {
+    if (D <= 16 && p.d >= 2) {
       h->job_cap = uint64_t(1) << 20;
       CK(dalloc(h, &h->jobs, size_t(h->job_cap)));
       CK(dalloc(h, &h->job_counts, 2));
@@ -858,28 +968,46 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
   float tau = INFINITY;
   std::vector<std::vector<PairRec>> by_rep(h->chunk_reps);
   unsigned long long* cnt = h->cnt_host;
-  for (int i = K; i >= 1 && !stop_i; --i) {
+  // MOMENTI_TRACE=1 prints one line per chunk (level, repetitions, work counts, TOP state)
+  const char* tr = std::getenv("MOMENTI_TRACE");
+  const bool trace = tr && tr[0] == '1';
+  // cost switch: each level opens with a one-repetition probe
+  const bool cost_switch = !(p.flags & MOMENTI_FLAG_NO_COST_SWITCH) && L > 1;
+  int switch_level = 0;
+  for (int i = K; i >= 1 && !stop_i && !switch_level; --i) {
     int j1 = 0;
-    for (int j0 = 0; j0 < L && !stop_i; j0 = j1) {
-      j1 = std::min(L, j0 + h->chunk_reps);
+    for (int j0 = 0; j0 < L && !stop_i && !switch_level; j0 = j1) {
+      const bool probe = cost_switch && j0 == 0;
+      j1 = probe ? 1 : std::min(L, j0 + h->chunk_reps);
+      const auto tc0 = std::chrono::steady_clock::now();
+      bool used_sub = false;
+      unsigned long long tiles = 0;
       // collision counting (prefix length 1: buckets split by a second
       // dimension when every bucket fits a CTA); grow the event list, or
       // halve the chunk beyond the event budget
       for (;;) {
         bool sub = false;
         unsigned long long jc[2] = {0, 0};
-        if (i == 1 && d >= 2 && ix.D <= 8 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
+        if (i == 1 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
           CK(cudaMemsetAsync(h->job_counts, 0, 2 * sizeof(unsigned long long), s));
           CK(launch_bucket_jobs(ix, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
           CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
-          sub = jc[0] <= h->job_cap && jc[1] <= uint64_t(kSubBucketCap);
+          sub = jc[0] <= h->job_cap && jc[1] <= uint64_t(subbucket_cap(ix.D));
         }
         CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
-        if (sub) CK(launch_subbucket(ix, j0, j1, d, h->hs, h->cs, h->jobs, h->job_counts, int(jc[1]), s));
-        else CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
-        CK(cudaMemcpyAsync(cnt, h->cs.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        used_sub = sub;
+        if (sub) {
+          CK(launch_subbucket(ix, j0, j1, d, h->hs, h->cs, h->jobs, h->job_counts, int(jc[1]), s));
+        } else {
+          CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
+          const int64_t E = int64_t(j1 - j0) * ix.D * ((ix.M + 31) / 32);
+          CK(cudaMemcpyAsync(&cnt[5], h->cs.ntile + E, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaMemcpyAsync(cnt, h->cs.counters, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        if (sub) CK(cudaMemcpyAsync(&cnt[5], h->cs.counters + 5, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        tiles = cnt[5];
         if (cnt[0] <= h->cs.ev_cap) break;
         const uint64_t cap = next_pow2(cnt[0]);
         if (cap * sizeof(Event) > h->ev_budget && j1 - j0 > 1) {
@@ -893,6 +1021,9 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
       }
       st.n_candidates += int64_t(cnt[0]);
       st.n_verified += int64_t(cnt[0]);
+      const uint64_t checks = used_sub ? tiles : tiles * 1024;
+      st.n_pair_checks += int64_t(checks);
+      const uint64_t n_events = cnt[0];
       uint64_t nrec = 0;
       if (cnt[0]) {
         for (;;) {
@@ -947,14 +1078,34 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
           }
         }
       }
-      st.t_host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0).count();
+      const auto tc1 = std::chrono::steady_clock::now();
+      st.t_host_ms += std::chrono::duration<double, std::milli>(tc1 - th0).count();
+      if (trace)
+        std::fprintf(stderr,
+                     "momenti trace: i=%d j=[%d,%d) sub=%d events=%llu tiles=%llu lb_pruned=%llu "
+                     "records=%llu top=%d kth=%.5g ms=%.3f\n",
+                     i, j0, j1, int(used_sub), cnt[0], tiles, cnt[3], (unsigned long long)nrec,
+                     int(pool.top.size()), pool.top.empty() ? -1.0 : pool.kth(),
+                     std::chrono::duration<double, std::milli>(tc1 - tc0).count());
       if (int(pool.top.size()) == k) {
         const float t2 = float(1.1 * pool.kth() + 1e-6);
         if (t2 < tau) tau = t2;
         pool.tau_trunc = std::min(pool.tau_trunc, double(tau));
       }
+      if (probe && !stop_i) {
+        const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
+        const double rest = double(L - 1) *
+            predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events, verified, nrec);
+        const double exact = predict_exact_ms(ix, int(pool.top.size()) == k ? 1 : 2);
+        if (rest > exact) {
+          switch_level = i;
+          st.predicted_rest_ms = rest;
+          st.predicted_exact_ms = exact;
+        }
+      }
     }
   }
+  st.switch_level = switch_level;
   st.t_traverse_ms = t_trav.stop();
   st.n_pool = int64_t(pool.items.size());
   pool.sort_all();

@@ -21,6 +21,7 @@ ERR_ARG, ERR_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_STATE = -1, -2, -3
 F32, F64 = 0, 1
 PREC_FP32, PREC_F16X2 = 0, 1
 FLAG_TILES_ONLY = 1
+FLAG_NO_COST_SWITCH = 2
 DELTA_PER_MOTIF, DELTA_ALL_K = 0, 1
 MAX_D, MAX_K = 64, 8
 NOALLOC_MAX_KEYS = 262144
@@ -55,7 +56,10 @@ class momenti_stats(C.Structure):
                 ("t_traverse_ms", C.c_double), ("t_fallback_ms", C.c_double),
                 ("max_rel_err_fp32", C.c_double), ("device_bytes", C.c_uint64),
                 ("precision_used", C.c_int32), ("reserved", C.c_int32),
-                ("n_rehashed", C.c_uint64), ("n_lb_pruned", C.c_int64), ("t_host_ms", C.c_double)]
+                ("n_rehashed", C.c_uint64), ("n_lb_pruned", C.c_int64), ("t_host_ms", C.c_double),
+                ("switch_level", C.c_int32), ("reserved2", C.c_int32),
+                ("n_pair_checks", C.c_int64), ("predicted_rest_ms", C.c_double),
+                ("predicted_exact_ms", C.c_double)]
 
 
 def _load():

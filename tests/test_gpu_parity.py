@@ -257,7 +257,8 @@ def test_topk_follows_algorithm_1(mom, seed):
     L = 100
     A, U = synth.hash_draws(wl.D, L, 8, wl.w, seed)
     r = O.estimate_r(wl.series, wl.w, A)
-    h, _, _ = make(mom, wl, L=L, r=r, hash_seed=seed)
+    # Algorithm 1's loop to its end (no cost switch)
+    h, _, _ = make(mom, wl, L=L, r=r, hash_seed=seed, flags=mom.FLAG_NO_COST_SWITCH)
     keys_o, ok = agreeing_segments(h, wl, A, U, r, L)
     got, st = h.topk()
     res = O.momenti(wl.series, wl.w, wl.d, wl.k, wl.delta, A, U, r)
@@ -293,7 +294,7 @@ def test_subbucketed_and_tiled_collisions_agree(mom, seed, D, d):
     out = []
     for flags in (0, mom.FLAG_TILES_ONLY):
         h = mom.Momenti(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, K=8, L=L, r=0.0,
-                        precision=mom.PREC_FP32, flags=flags)
+                        precision=mom.PREC_FP32, flags=flags | mom.FLAG_NO_COST_SWITCH)
         h.set_hash_params(A, U)
         h.hash_all(wl.series)
         motifs, st = h.topk()
@@ -305,3 +306,25 @@ def test_subbucketed_and_tiled_collisions_agree(mom, seed, D, d):
     ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
     if s0["fallback"]:
         assert [(m["a"], m["b"]) for m in m0] == [(m[1], m[2]) for m in ref]
+
+
+@pytest.mark.parametrize("seed,n,D,w,d,k", [(8, 2500, 3, 50, 1, 3), (9, 2000, 6, 40, 2, 4),
+                                           (10, 1500, 12, 30, 4, 2)])
+def test_cost_switch_keeps_the_exact_result(mom, seed, n, D, w, d, k):
+    # the cost switch only moves the point where the exact path takes over;
+    # with or without it the result is the exact top-k of the oracle (these
+    # small, low-contrast cases never reach STOP)
+    wl = synth.tiny(seed, n, D, w, d, k=k, n_motifs=1)
+    ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+    for flags in (0, mom.FLAG_NO_COST_SWITCH):
+        h = mom.Momenti(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, precision=mom.PREC_FP32,
+                        flags=flags)
+        h.hash_all(wl.series)
+        got, st = h.topk()
+        if st["fallback"]:
+            assert_same_motifs(got, ref)
+        if flags:
+            assert st["switch_level"] == 0
+        elif st["switch_level"]:
+            assert st["fallback"] == 1 and st["predicted_rest_ms"] > st["predicted_exact_ms"]
+        h.close()
