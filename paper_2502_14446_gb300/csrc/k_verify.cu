@@ -377,7 +377,13 @@ k_verify_pairs(Index ix, int d, const uint64_t* __restrict__ pairs, int64_t m, i
 // approximate distance) while there is room, and counted in the histogram
 // of (rc.lo, thr] either way.
 __device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t b, float dd) {
-  const unsigned long long pos = atomicAdd(rc.count, 1ull);
+  // one counter atomic per group of converged lanes
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(rc.count, (unsigned long long)__popc(act));
+  base = __shfl_sync(act, base, leader);
+  const unsigned long long pos = base + __popc(act & ((1u << lane) - 1u));
   if (pos < rc.cap) {
     rc.out[pos] = (uint64_t(a) << 32) | uint64_t(b);
     rc.out_d[pos] = dd;
@@ -637,14 +643,18 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
       u1 += v;
       u2 = fmaf(v, v, u2);
     }
-    sa1[f] = u1;
-    sa2[f] = u2;
-    for (int r = 1; r < nrow; ++r) {
-      const float o = rowx[(r - 1) * DP + f], in = rowx[(r - 1 + w) * DP + f];
-      u1 += in - o;
-      u2 = fmaf(in, in, fmaf(-o, o, u2));
+    // per row window: the sum and w^2 var (-1 when cancellation leaves it
+    // unreliable: a near-flat window, always checked exactly)
+    const float wf = float(w);
+    for (int r = 0; r < nrow; ++r) {
+      if (r > 0) {
+        const float o = rowx[(r - 1) * DP + f], in = rowx[(r - 1 + w) * DP + f];
+        u1 += in - o;
+        u2 = fmaf(in, in, fmaf(-o, o, u2));
+      }
+      const float va = fmaf(wf, u2, -u1 * u1);
       sa1[r * DP + f] = u1;
-      sa2[r * DP + f] = u2;
+      sa2[r * DP + f] = va > 1e-4f * wf * u2 ? va : -1.f;
     }
   }
   __syncthreads();
@@ -667,8 +677,18 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
       s2b[f] = fmaf(v, v, s2b[f]);
     }
   }
-  const float c0 = 1.f - thr * thr / (2.f * wf);
-  const float c0sq = c0 * c0;
+  // Necessary conditions of dist_d <= thr on the sorted per-dim distances
+  // x(1) <= x(2) <= ...: x(1) <= thr / d, x(2) <= thr / (d - 1) and
+  // x(d) <= thr.  dist_f <= t  <=>  corr >= c = 1 - t^2 / 2w  <=>
+  // C >= c sqrt(VA VB), tested as C > 0 and C^2 >= c^2 VA VB (always true
+  // when c <= 0).
+  const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
+  const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
+  const float cd = 1.f - thr * thr / (2.f * wf);
+  const float k1 = c1 > 0.f ? c1 * c1 : -1.f, k2 = c2 > 0.f ? c2 * c2 : -1.f;
+  const float kd = cd > 0.f ? cd * cd : -1.f;
+  const int need2 = d >= 2 ? 2 : 1;
+  const float flat = 1e-4f * wf;
   for (int64_t a = a0; a < a1; ++a) {
     const int r = int(a - a0);
     const int64_t b = a + delta;
@@ -685,27 +705,29 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
         s2b[f] = fmaf(vi, vi, fmaf(-vo, vo, s2b[f]));
       }
     }
-    int near = 0;
+    int n1 = 0, n2 = 0, nd = 0;
     bool unsure = false;
 #pragma unroll
     for (int f = 0; f < DP; ++f) {
       if (f < D) {
-        const float s1a = sa1[r * DP + f], s2a = sa2[r * DP + f];
-        const float VA = fmaf(wf, s2a, -s1a * s1a);
+        const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
         const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
         const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
-        unsure |= !(VA > 1e-4f * wf * s2a) || !(VB > 1e-4f * wf * s2b[f]);
-        near += c0 <= 0.f || (Cv > 0.f && Cv * Cv >= c0sq * VA * VB);
+        const float P = VA * VB;
+        const float C2 = Cv > 0.f ? Cv * Cv : -1.f;
+        unsure |= VA < 0.f || !(VB > flat * s2b[f]);
+        n1 += k1 < 0.f || C2 >= k1 * P;
+        n2 += k2 < 0.f || C2 >= k2 * P;
+        nd += kd < 0.f || C2 >= kd * P;
       }
     }
-    if (!ROWMIN && near < d && !unsure) continue;
+    if (!ROWMIN && !unsure && (n1 < 1 || n2 < need2 || nd < d)) continue;
     float dist[DP];
 #pragma unroll
     for (int f = 0; f < DP; ++f) {
       dist[f] = INFINITY;
       if (f < D) {
-        const float s1a = sa1[r * DP + f], s2a = sa2[r * DP + f];
-        const float VA = fmaf(wf, s2a, -s1a * s1a);
+        const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
         const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
         const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
         const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;

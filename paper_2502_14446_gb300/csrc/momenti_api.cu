@@ -569,20 +569,21 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
                    pass, double(lo), double(hi), cnt, (unsigned long long)cap, got.size());
     const double width = double(hi - lo) / kApBins;
     if (cnt > cap) {
-      release();
-      if (cnt <= cap_max) {
-        cap = (uint64_t(cnt) + (uint64_t(1) << 20)) & ~((uint64_t(1) << 20) - 1);
-      } else {
-        // the largest upper edge whose pairs fit
-        uint64_t run = 0;
-        int bin = 0;
-        for (; bin < kApBins; ++bin) {
-          if (run + hist[bin] > cap_max) break;
-          run += hist[bin];
-        }
-        cap = cap_max;
-        if (bin == 0) return fail(h, MOMENTI_ERR_MEMORY, "exact path: one distance bin exceeds memory");
+      // lower the upper edge to the largest bin edge whose pairs fit; grow
+      // the buffer only when the first bin alone does not fit
+      uint64_t run = 0;
+      int bin = 0;
+      for (; bin < kApBins; ++bin) {
+        if (run + hist[bin] > cap) break;
+        run += hist[bin];
+      }
+      if (bin > 0) {
         hi = float(double(lo) + width * bin);
+      } else {
+        release();
+        if (uint64_t(hist[0]) > cap_max)
+          return fail(h, MOMENTI_ERR_MEMORY, "exact path: one distance bin exceeds memory");
+        cap = std::min<uint64_t>(cap_max, (uint64_t(cnt) + (uint64_t(1) << 20)) & ~((uint64_t(1) << 20) - 1));
       }
       continue;
     }
