@@ -395,7 +395,11 @@ __device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t 
   }
 }
 
-constexpr int kSeg = 64;        // diagonal steps between direct restarts
+// Diagonal steps between direct restarts: a restart costs w steps of a
+// direct dot product, so it is amortised over many sliding steps (the
+// float32 sliding sums drift by about sqrt(kSeg) roundings between
+// restarts, far inside the 1% + 0.01 filter margin).
+constexpr int kSeg = 512;
 constexpr int kDiagBlock = 128; // diagonals per CTA
 
 __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t) {
@@ -627,6 +631,13 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   float* sa1 = rowx + (kSeg - 1 + w) * DP;                      // [kSeg][DP]
   float* sa2 = sa1 + kSeg * DP;
   float* cav = sa2 + kSeg * DP;                                 // [DP]
+  // per-warp queue of candidate pairs: state (qt, s1b, s2b per dim),
+  // row and unsure flag, column window
+  constexpr int QS = 3 * DP + 2;
+  float* qall = cav + DP;                                       // [warps][32][QS]
+  uint32_t* qmeta = reinterpret_cast<uint32_t*>(qall + (kDiagBlock / 32) * 32 * QS);
+  uint32_t* qcol = qmeta + kDiagBlock;
+  __shared__ int rflag[kSeg];                                   // row window unreliable in some dim
   const float* X = ix.xT;
   if (threadIdx.x < DP) cav[threadIdx.x] = threadIdx.x < D ? ix.mu_hi[int64_t(threadIdx.x) * ix.M + a0] : 0.f;
   __syncthreads();
@@ -654,95 +665,171 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
       }
       const float va = fmaf(wf, u2, -u1 * u1);
       sa1[r * DP + f] = u1;
-      sa2[r * DP + f] = va > 1e-4f * wf * u2 ? va : -1.f;
+      // padding dims: NaN, so that no test on them passes
+      sa2[r * DP + f] = f >= D ? __int_as_float(0x7fc00000) : (va > 1e-4f * wf * u2 ? va : -1.f);
     }
   }
   __syncthreads();
-  if (!live) return;
-  const float wf = float(w);
-  float qt[DP], s1b[DP], s2b[DP], cb[DP];
-#pragma unroll
-  for (int f = 0; f < DP; ++f) {
-    qt[f] = s1b[f] = s2b[f] = 0.f;
-    cb[f] = f < D ? ix.mu_hi[int64_t(f) * ix.M + a0 + delta] : 0.f;
+  for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+    int u = 0;
+    for (int f = 0; f < D; ++f) u |= sa2[r * DP + f] < 0.f;
+    rflag[r] = u;
   }
-  for (int t = 0; t < w; ++t) {
+  __syncthreads();
+  // the per-step arithmetic runs on pairs of dims with the packed
+  // two-lane float32 instructions (same rounding as the scalar ones)
+  constexpr int DH = DP / 2;
+  const float wf = float(w);
+  const float2 wf2 = make_float2(wf, wf);
+  float2 qt[DH], s1b[DH], s2b[DH], ncb[DH];
+#pragma unroll
+  for (int p = 0; p < DH; ++p) {
+    qt[p] = s1b[p] = s2b[p] = make_float2(0.f, 0.f);
+    const int f0 = 2 * p, f1 = 2 * p + 1;
+    ncb[p] = make_float2(f0 < D ? -ix.mu_hi[int64_t(f0) * ix.M + a0 + delta] : 0.f,
+                         f1 < D ? -ix.mu_hi[int64_t(f1) * ix.M + a0 + delta] : 0.f);
+  }
+  const float2* row2 = reinterpret_cast<const float2*>(rowx);
+  const float2* sa1_2 = reinterpret_cast<const float2*>(sa1);
+  const float2* sa2_2 = reinterpret_cast<const float2*>(sa2);
+  for (int t = 0; t < (live ? w : 0); ++t) {
     float xb[DP];
     load_row<DP>(X, a0 + delta + t, xb);
 #pragma unroll
-    for (int f = 0; f < DP; ++f) {
-      const float u = rowx[t * DP + f], v = xb[f] - cb[f];
-      qt[f] = fmaf(u, v, qt[f]);
-      s1b[f] += v;
-      s2b[f] = fmaf(v, v, s2b[f]);
+    for (int p = 0; p < DH; ++p) {
+      const float2 u = row2[t * DH + p];
+      const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
+      qt[p] = __ffma2_rn(u, v, qt[p]);
+      s1b[p] = __fadd2_rn(s1b[p], v);
+      s2b[p] = __ffma2_rn(v, v, s2b[p]);
     }
   }
   // Necessary conditions of dist_d <= thr on the sorted per-dim distances
   // x(1) <= x(2) <= ...: x(1) <= thr / d, x(2) <= thr / (d - 1) and
   // x(d) <= thr.  dist_f <= t  <=>  corr >= c = 1 - t^2 / 2w  <=>
-  // C >= c sqrt(VA VB), tested as C > 0 and C^2 >= c^2 VA VB (always true
-  // when c <= 0).
+  // C >= c sqrt(VA VB)  <=>  C |C| >= c |c| VA VB (x -> x |x| is monotone).
   const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
   const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
   const float cd = 1.f - thr * thr / (2.f * wf);
-  const float k1 = c1 > 0.f ? c1 * c1 : -1.f, k2 = c2 > 0.f ? c2 * c2 : -1.f;
-  const float kd = cd > 0.f ? cd * cd : -1.f;
+  const float2 k1 = make_float2(c1 * fabsf(c1), c1 * fabsf(c1));
+  const float2 k2 = make_float2(c2 * fabsf(c2), c2 * fabsf(c2));
+  const float2 kd = make_float2(cd * fabsf(cd), cd * fabsf(cd));
   const int need2 = d >= 2 ? 2 : 1;
-  const float flat = 1e-4f * wf;
-  for (int64_t a = a0; a < a1; ++a) {
+  const float2 flat = make_float2(1e-4f * wf, 1e-4f * wf);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qst = qall + warp * 32 * QS;
+  uint32_t* qm = qmeta + warp * 32;
+  uint32_t* qc = qcol + warp * 32;
+  // distances of queued pairs, one per lane (lanes below count)
+  auto drain = [&](int count) {
+    __syncwarp();
+    if (lane < count) {
+      const float* st = qst + lane * QS;
+      const int r = int(qm[lane] >> 1);
+      const bool uns = (qm[lane] & 1u) != 0;
+      float dist[DP];
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float qf = st[f], s1 = st[DP + f], s2 = st[2 * DP + f];
+          const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
+          const float VB = fmaf(wf, s2, -s1 * s1);
+          const float Cv = fmaf(wf, qf, -s1a * s1);
+          const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+          dist[f] = sqrtf(fmaxf(sq, 0.f));
+        }
+      }
+      const float sm = uns ? 0.f : sum_d_smallest<DP>(dist, D, d);
+      if (sm <= thr && sm > rc.lo) record_pair(rc, a0 + r, int64_t(qc[lane]), sm);
+    }
+    __syncwarp();
+  };
+  int qn = 0;                       // queued pairs of this warp (warp-uniform)
+  // every lane runs the block's row count, so that the warp stays converged
+  for (int64_t a = a0; a < a0 + nrow; ++a) {
     const int r = int(a - a0);
     const int64_t b = a + delta;
-    if (r > 0) {
+    const bool act = a < a1;
+    if (act && r > 0) {
       float ob[DP], ib[DP];
       load_row<DP>(X, b - 1, ob);
       load_row<DP>(X, b + w - 1, ib);
 #pragma unroll
-      for (int f = 0; f < DP; ++f) {
-        const float uo = rowx[(r - 1) * DP + f], ui = rowx[(r - 1 + w) * DP + f];
-        const float vo = ob[f] - cb[f], vi = ib[f] - cb[f];
-        qt[f] = fmaf(ui, vi, fmaf(-uo, vo, qt[f]));
-        s1b[f] += vi - vo;
-        s2b[f] = fmaf(vi, vi, fmaf(-vo, vo, s2b[f]));
+      for (int p = 0; p < DH; ++p) {
+        const float2 uo = row2[(r - 1) * DH + p], ui = row2[(r - 1 + w) * DH + p];
+        const float2 vo = __fadd2_rn(make_float2(ob[2 * p], ob[2 * p + 1]), ncb[p]);
+        const float2 vi = __fadd2_rn(make_float2(ib[2 * p], ib[2 * p + 1]), ncb[p]);
+        qt[p] = __ffma2_rn(ui, vi, __ffma2_rn(make_float2(-uo.x, -uo.y), vo, qt[p]));
+        s1b[p] = __fadd2_rn(s1b[p], __fadd2_rn(vi, make_float2(-vo.x, -vo.y)));
+        s2b[p] = __ffma2_rn(vi, vi, __ffma2_rn(make_float2(-vo.x, -vo.y), vo, s2b[p]));
       }
     }
-    int n1 = 0, n2 = 0, nd = 0;
-    bool unsure = false;
+    uint32_t cnt = 0;              // tests passed: byte 0 x(1), byte 1 x(2), byte 2 x(d)
+    bool unsure = rflag[r] != 0;
 #pragma unroll
-    for (int f = 0; f < DP; ++f) {
-      if (f < D) {
-        const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
-        const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
-        const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
-        const float P = VA * VB;
-        const float C2 = Cv > 0.f ? Cv * Cv : -1.f;
-        unsure |= VA < 0.f || !(VB > flat * s2b[f]);
-        n1 += k1 < 0.f || C2 >= k1 * P;
-        n2 += k2 < 0.f || C2 >= k2 * P;
-        nd += kd < 0.f || C2 >= kd * P;
-      }
+    for (int p = 0; p < DH; ++p) {
+      const float2 s1a = sa1_2[r * DH + p], VA = sa2_2[r * DH + p];
+      const float2 VB = __ffma2_rn(wf2, s2b[p], __fmul2_rn(make_float2(-s1b[p].x, -s1b[p].y), s1b[p]));
+      const float2 Cv = __ffma2_rn(wf2, qt[p], __fmul2_rn(make_float2(-s1a.x, -s1a.y), s1b[p]));
+      const float2 P = __fmul2_rn(VA, VB);
+      const float2 S = __fmul2_rn(Cv, make_float2(fabsf(Cv.x), fabsf(Cv.y)));
+      const float2 T1 = __fmul2_rn(k1, P), T2 = __fmul2_rn(k2, P), Td = __fmul2_rn(kd, P);
+      const float2 FB = __fmul2_rn(flat, s2b[p]);
+      unsure |= (VB.x < FB.x) | (VB.y < FB.y);
+      cnt += (S.x >= T1.x) + (S.y >= T1.y) + ((S.x >= T2.x) + (S.y >= T2.y)) * 256u +
+             ((S.x >= Td.x) + (S.y >= Td.y)) * 65536u;
     }
-    if (!ROWMIN && !unsure && (n1 < 1 || n2 < need2 || nd < d)) continue;
+    if (!ROWMIN) {
+      const bool cand = act && (unsure || ((cnt & 255u) >= 1u && ((cnt >> 8) & 255u) >= uint32_t(need2) &&
+                                           (cnt >> 16) >= uint32_t(d)));
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (!m) continue;
+      const int n = __popc(m);
+      if (qn + n > 32) {
+        drain(qn);
+        qn = 0;
+      }
+      if (cand) {
+        const int pos = qn + __popc(m & ((1u << lane) - 1u));
+        float2* st = reinterpret_cast<float2*>(qst + pos * QS);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          st[p] = qt[p];
+          st[DH + p] = s1b[p];
+          st[2 * DH + p] = s2b[p];
+        }
+        qm[pos] = (uint32_t(r) << 1) | (unsure ? 1u : 0u);
+        qc[pos] = uint32_t(b);
+      }
+      qn += n;
+      if (qn == 32) {
+        drain(32);
+        qn = 0;
+      }
+      continue;
+    }
+    if (!act) continue;
     float dist[DP];
 #pragma unroll
     for (int f = 0; f < DP; ++f) {
       dist[f] = INFINITY;
       if (f < D) {
+        const float qf = (f & 1) ? qt[f >> 1].y : qt[f >> 1].x;
+        const float s1 = (f & 1) ? s1b[f >> 1].y : s1b[f >> 1].x;
+        const float s2 = (f & 1) ? s2b[f >> 1].y : s2b[f >> 1].x;
         const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
-        const float VB = fmaf(wf, s2b[f], -s1b[f] * s1b[f]);
-        const float Cv = fmaf(wf, qt[f], -s1a * s1b[f]);
+        const float VB = fmaf(wf, s2, -s1 * s1);
+        const float Cv = fmaf(wf, qf, -s1a * s1);
         const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
         dist[f] = sqrtf(fmaxf(sq, 0.f));
       }
     }
-    if (ROWMIN) {
-      const float sm = sum_d_smallest<DP>(dist, D, d);
-      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
-      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
-    } else {
-      const float sm = unsure ? 0.f : sum_d_smallest<DP>(dist, D, d);
-      if (sm <= thr && sm > rc.lo) record_pair(rc, a, b, sm);
-    }
+    const float sm = sum_d_smallest<DP>(dist, D, d);
+    atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+    atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
   }
+  if (!ROWMIN) drain(qn);
 }
 
 // Wide series (D > 16): per-window means and 1/sigma are read per step.
@@ -812,10 +899,14 @@ k_allpairs_wide(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   }
 }
 
-// the row kernel stages kSeg-1+w points of every dimension in shared memory
-bool rows_fit(int w, int dp) {
-  return size_t((kSeg - 1 + w) * dp + 2 * kSeg * dp + dp) * sizeof(float) <= size_t(200) * 1024;
+// the row kernel stages kSeg-1+w points of every dimension in shared
+// memory, the row sums, and a queue of 32 candidate pairs per warp
+size_t rows_smem(int w, int dp) {
+  return (size_t((kSeg - 1 + w) * dp + 2 * kSeg * dp + dp) +
+          size_t(kDiagBlock) * (3 * dp + 2) + 2 * size_t(kDiagBlock)) * sizeof(float);
 }
+
+bool rows_fit(int w, int dp) { return rows_smem(w, dp) <= size_t(200) * 1024; }
 
 template <bool ROWMIN>
 cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc, float* rowmin,
@@ -828,7 +919,7 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
   if (ix.xT && ix.Dp == 4 && ix.has_lo)
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<4, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.xT && ix.Dp == 4 && rows_fit(ix.w, 4)) {
-    const size_t smem = size_t((kSeg - 1 + ix.w) * 4 + 2 * kSeg * 4 + 4) * sizeof(float);
+    const size_t smem = rows_smem(ix.w, 4);
     cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<4, ROWMIN>), smem);
     if (e != cudaSuccess) return e;
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<4, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
@@ -836,7 +927,7 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
   else if (ix.xT && ix.Dp == 8 && ix.has_lo)
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<8, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.xT && ix.Dp == 8 && rows_fit(ix.w, 8)) {
-    const size_t smem = size_t((kSeg - 1 + ix.w) * 8 + 2 * kSeg * 8 + 8) * sizeof(float);
+    const size_t smem = rows_smem(ix.w, 8);
     cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<8, ROWMIN>), smem);
     if (e != cudaSuccess) return e;
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<8, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
@@ -844,7 +935,7 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
   else if (ix.xT && ix.Dp == 16 && ix.has_lo)
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_pm<16, true, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
   else if (ix.xT && ix.Dp == 16 && rows_fit(ix.w, 16)) {
-    const size_t smem = size_t((kSeg - 1 + ix.w) * 16 + 2 * kSeg * 16 + 16) * sizeof(float);
+    const size_t smem = rows_smem(ix.w, 16);
     cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<16, ROWMIN>), smem);
     if (e != cudaSuccess) return e;
     MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<16, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));

@@ -158,11 +158,13 @@ def agreeing_segments(h, wl, A, U, r, L):
     return keys_o, ok
 
 
-def test_index_matches_oracle(mom):
-    wl = synth.tiny(21, n=3000, D=3, w=64, d=2, k=2, n_motifs=1)
-    L = 6
+@pytest.mark.parametrize("n,D,L,r_scale", [(3000, 3, 6, 1.0), (6000, 2, 3, 40.0),
+                                           (12000, 2, 2, 400.0)])
+def test_index_matches_oracle(mom, n, D, L, r_scale):
+    # r_scale widens the buckets (long runs of equal hash values)
+    wl = synth.tiny(21, n=n, D=D, w=64, d=2, k=2, n_motifs=1)
     A, U = synth.hash_draws(wl.D, L, 8, wl.w, 21)
-    r = O.estimate_r(wl.series, wl.w, A)
+    r = O.estimate_r(wl.series, wl.w, A) * r_scale
     h, _, _ = make(mom, wl, L=L, r=r, hash_seed=21)
     keys_o, ok = agreeing_segments(h, wl, A, U, r, L)
     assert ok.mean() > 0.5
@@ -282,6 +284,23 @@ def test_topk_plain_small_matches_exact(mom):
     assert st["L"] == 200 and st["K"] == 8
     ex = h.topk_exact()
     assert_same_motifs(ex, gold["motifs"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "f16x2"])
+def test_topk_plain_fp32_full_size_matches_exact(mom, precision):
+    # the benchmark workload at full size (D=8, n=1e5, w=300, d=3, k=10):
+    # the exact top-k written by tests/golden/make_golden.py (4.5 h of the
+    # float64 oracle), with the library's default parameters
+    gold = json.load(open(os.path.join(GOLDEN, "exact_plain_fp32_seed0.json")))
+    wl = synth.plain_fp32(0)
+    prec = mom.PREC_FP32 if precision == "fp32" else mom.PREC_F16X2
+    h = mom.Momenti(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, mem_limit=wl.mem_limit,
+                    precision=prec)
+    h.hash_all(wl.series)
+    got, st = h.topk()
+    assert_same_motifs(got, gold["motifs"])
+    assert st["max_rel_err_fp32"] < 1e-4
+    h.close()
 
 
 @pytest.mark.parametrize("seed,D,d", [(5, 4, 2), (6, 8, 3), (7, 6, 2)])
