@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--kernel", default="auto", help="kernel for the roofline object")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--batch-series", type=int, default=64,
+                    help="series of the batching form timed beside the step (0: skip)")
     ap.add_argument("--n", type=int, default=100_000,
                     help="series length (smaller values only for profiler captures)")
     return ap.parse_args()
@@ -142,7 +144,9 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
       proj_hash_tc    2 w flop per useful projection (M D L K of them)
       proj_hash_fp32  the same, on FP32 CUDA cores
       verify_events   8 D w bytes per verified pair (both windows, all dims)
-      allpairs        10 flop per pair and dim of the diagonal recurrence
+      allpairs        18 flop per pair and dim: the diagonal recurrence of
+                      the centred dot product and both window sums (10) and
+                      the Pearson threshold test (8)
       sort_scatter    24 bytes per index entry per 8-bit pass (K passes)
     """
     if not k_n or k_ms <= 0:
@@ -165,7 +169,7 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
     elif kernel == "allpairs":
         excl = w // 2
         pairs = max(0, M - excl - 1) * max(0, M - excl) / 2.0
-        work = 10.0 * D * pairs * steps
+        work = 18.0 * D * pairs * steps
         bound, unit = "alu", "TFLOP/s"
         achieved = work / secs / 1e12
         peak, src = sm_peak, "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
@@ -296,6 +300,7 @@ def run_momenti(args):
                      "value": units_step / (statistics.mean(ts) / 1e3),
                      "t_hash_ms": st32["t_hash_ms"]}
             h32.close()
+        batch = batch_leg(mom, args.batch_series, dev) if args.batch_series > 0 else None
         base = None if args.no_baseline else cpu_baseline(wl)
         out = {
             "metric": "time-to-top-k motifs (s) and subsequences hashed/s, BF16/batched vs plain FP32",
@@ -319,6 +324,7 @@ def run_momenti(args):
                      "hashed_per_s_hash_all": units_step / (st["t_hash_ms"] / 1e3)},
             "motifs": [[m["a"], m["b"], round(m["dist_d"], 6), list(m["dims"])] for m in motifs],
             "plain_fp32": plain,
+            "batch_form": batch,
             "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
                     "time_to_topk_s": e2e_s, "h2d_bytes_per_step": h_bytes,
                     "d2h_bytes_per_step": d_bytes},
@@ -332,6 +338,35 @@ def run_momenti(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def batch_leg(mom, count: int, dev, threads: int = 8):
+    """The batching form on its first ``count`` series (lengths log-uniform in
+    [2,000, 200,000], D in 3..16, w in {50, 100, 200}, d = ceil(D/3), k=5,
+    delta=0.05, float32, series resident in HBM): momenti_topk_batch with
+    ``threads`` workers, against the same searches one at a time through
+    the same entry point (one worker).  Throughput in subsequence hashes
+    (windows x dims x repetitions) per second, whole batch."""
+    import torch
+    from paper_2502_14446_gb300 import synth
+    wls = synth.batch_form(0, count=count)
+    series = [torch.from_numpy(wl.series).to(dev) for wl in wls]
+    params = [dict(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta) for wl in wls]
+    torch.cuda.synchronize()
+    mom.topk_batch(params[:4], series[:4], threads=threads)          # warm-up
+    out = {"series": count, "threads": threads,
+           "workload": "batching form: n log-uniform [2e3, 2e5], D 3..16, w {50,100,200}, "
+                       "d=ceil(D/3), k=5, delta=0.05, float32, 2 planted motifs each"}
+    for name, T in (("batched", threads), ("one_at_a_time", 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = mom.topk_batch(params, series, threads=T)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        units = sum(st["n_windows"] * wl.D * st["L"] for (m, st), wl in zip(res, wls))
+        out[name] = {"seconds": dt, "value": units / dt, "unit": "subsequences/s",
+                     "fallbacks": sum(st["fallback"] for m, st in res)}
     return out
 
 

@@ -86,7 +86,8 @@ typedef struct momenti_params {
 #define MOMENTI_FLAG_TILES_ONLY 1u
 /* flags: follow Algorithm 1's loop to its end before the exact path (no
  * cost switch).  By default each level starts with a one-repetition probe
- * whose work counts predict the rest of the level; when that prediction
+ * whose work counts predict the rest of the traversal (the rest of the
+ * level, and each lower level at least as much); when that prediction
  * exceeds the predicted time of the exact all-pairs path, the traversal
  * stops there and the exact path runs (its result is the exact top-k, the
  * probability-1 branch of Lemma topk). */
@@ -129,7 +130,7 @@ typedef struct momenti_stats {
   int32_t  switch_level;     /* level i at which the cost switch chose the exact path, 0 = none */
   int32_t  reserved2;
   int64_t  n_pair_checks;    /* bucket pairs compared by collision counting           */
-  double   predicted_rest_ms;  /* cost model at the switch: rest of that level        */
+  double   predicted_rest_ms;  /* cost model at the switch: rest of the traversal     */
   double   predicted_exact_ms; /*   and the exact path                                */
 } momenti_stats;
 

@@ -7,7 +7,9 @@
 // segments of a batch of repetitions in the same launches.  Each pass is
 // three kernels: per-tile digit histograms, a per-segment scan of
 // (digit, tile) counts, and a stable scatter that ranks equal digits with
-// warp-level match masks.  The final kernel writes the sorted window order
+// warp-level match masks and writes each tile in digit order through
+// shared memory, so that equal digits leave as contiguous runs.  The final
+// kernel writes the sorted window order
 // and, per rank, the number of hash values shared with the previous rank
 // (the longest common prefix, 0..K), which is all the traversal needs.
 #include "internal.h"
@@ -34,6 +36,13 @@ struct Src {
   int64_t M;
   int D, j0;
   bool first;
+  __device__ __forceinline__ uint64_t load_key(int seg, int64_t p) const {
+    if (first) {
+      int j = j0 + seg / D, f = seg - (seg / D) * D;
+      return keys[(int64_t(j) * M + p) * D + f];
+    }
+    return kin[int64_t(seg) * M + p];
+  }
   __device__ __forceinline__ void load(int seg, int64_t p, uint64_t& k, uint32_t& v) const {
     if (first) {
       int j = j0 + seg / D, f = seg - (seg / D) * D;
@@ -54,14 +63,16 @@ k_hist(Src src, int shift, int tiles, uint32_t* __restrict__ hist) {
   for (int d = threadIdx.x; d < 256; d += kThreads) h[d] = 0;
   __syncthreads();
   const int64_t base = int64_t(tile) * kTile;
-  for (int q = threadIdx.x; q < kTile; q += kThreads) {
-    int64_t p = base + q;
-    if (p < src.M) {
-      uint64_t k;
-      uint32_t v;
-      src.load(seg, p, k, v);
-      atomicAdd(&h[(k >> shift) & 255u], 1u);
-    }
+  uint64_t k[kItems];
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t p = base + r * kThreads + threadIdx.x;
+    k[r] = p < src.M ? src.load_key(seg, p) : 0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t p = base + r * kThreads + threadIdx.x;
+    if (p < src.M) atomicAdd(&h[uint32_t(k[r] >> shift) & 255u], 1u);
   }
   __syncthreads();
   uint32_t* out = hist + int64_t(seg) * 256 * tiles;
@@ -74,7 +85,15 @@ __global__ void __launch_bounds__(256) k_scan(int tiles, uint32_t* __restrict__ 
   const int seg = blockIdx.x, d = threadIdx.x;
   uint32_t* hs = hist + int64_t(seg) * 256 * tiles + int64_t(d) * tiles;
   uint32_t s = 0;
-  for (int t = 0; t < tiles; ++t) s += hs[t];
+  int t0 = 0;
+  for (; t0 + 8 <= tiles; t0 += 8) {          // eight independent loads in flight
+    uint32_t c[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = hs[t0 + q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += c[q];
+  }
+  for (; t0 < tiles; ++t0) s += hs[t0];
   tot[d] = s;
   __syncthreads();
   // Hillis-Steele inclusive scan of the 256 digit totals
@@ -85,9 +104,20 @@ __global__ void __launch_bounds__(256) k_scan(int tiles, uint32_t* __restrict__ 
     __syncthreads();
   }
   uint32_t run = tot[d] - s;   // exclusive
-  for (int t = 0; t < tiles; ++t) {
-    uint32_t c = hs[t];
-    hs[t] = run;
+  int t1 = 0;
+  for (; t1 + 8 <= tiles; t1 += 8) {
+    uint32_t c[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = hs[t1 + q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      hs[t1 + q] = run;
+      run += c[q];
+    }
+  }
+  for (; t1 < tiles; ++t1) {
+    uint32_t c = hs[t1];
+    hs[t1] = run;
     run += c;
   }
 }
@@ -96,6 +126,9 @@ __global__ void __launch_bounds__(kThreads)
 k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
   __shared__ uint32_t wh[kWarps][256];
+  __shared__ uint32_t loff[256];             // tile-local start of each digit
+  __shared__ uint64_t sk[kTile];             // the tile in digit order
+  __shared__ uint32_t sv[kTile];
   const int seg = blockIdx.x, tile = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = threadIdx.x; q < kWarps * 256; q += kThreads) (&wh[0][0])[q] = 0;
@@ -104,16 +137,19 @@ k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
   const uint32_t lt = (1u << lane) - 1u;
   uint64_t key[kRounds];
   uint32_t val[kRounds], dig[kRounds], loc[kRounds];
+  // all loads of the warp's span first (independent, in flight together)
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    int64_t p = base + r * 32 + lane;
-    uint32_t dg = 256u + lane;           // out of range: a digit no valid item has
+    const int64_t p = base + r * 32 + lane;
     key[r] = 0;
     val[r] = 0;
-    if (p < src.M) {
-      src.load(seg, p, key[r], val[r]);
-      dg = uint32_t(key[r] >> shift) & 255u;
-    }
+    if (p < src.M) src.load(seg, p, key[r], val[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int64_t p = base + r * 32 + lane;
+    // out of range: a digit no valid item has
+    const uint32_t dg = p < src.M ? uint32_t(key[r] >> shift) & 255u : 256u + lane;
     dig[r] = dg;
     uint32_t peers = __match_any_sync(0xffffffffu, dg);
     uint32_t rank = __popc(peers & lt);
@@ -133,16 +169,42 @@ k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
       wh[w][d] = run;
       run += c;
     }
+    loff[d] = run;                           // digit total, scanned below
   }
   __syncthreads();
-  const uint32_t* hs = hist + int64_t(seg) * 256 * tiles;
+  if (threadIdx.x < 32) {                    // exclusive scan of the 256 totals
+    uint32_t v[8], run = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { v[q] = loff[lane * 8 + q]; run += v[q]; }
+    uint32_t incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    uint32_t b = incl - run;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { loff[lane * 8 + q] = b; b += v[q]; }
+  }
+  __syncthreads();
+  // the tile in digit order in shared memory (stable within each digit) ...
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
     if (dig[r] < 256u) {
-      uint32_t dst = hs[int64_t(dig[r]) * tiles + tile] + wh[warp][dig[r]] + loc[r];
-      kout[int64_t(seg) * src.M + dst] = key[r];
-      vout[int64_t(seg) * src.M + dst] = val[r];
+      const uint32_t q = loff[dig[r]] + wh[warp][dig[r]] + loc[r];
+      sk[q] = key[r];
+      sv[q] = val[r];
     }
+  }
+  __syncthreads();
+  // ... then written out in that order: runs of equal digits are contiguous
+  const uint32_t* hs = hist + int64_t(seg) * 256 * tiles;
+  const int64_t n_tile = min(int64_t(kTile), src.M - int64_t(tile) * kTile);
+  for (int q = threadIdx.x; q < n_tile; q += kThreads) {
+    const uint64_t k = sk[q];
+    const uint32_t d = uint32_t(k >> shift) & 255u;
+    const uint32_t dst = hs[int64_t(d) * tiles + tile] + (uint32_t(q) - loff[d]);
+    kout[int64_t(seg) * src.M + dst] = k;
+    vout[int64_t(seg) * src.M + dst] = sv[q];
   }
 }
 

@@ -400,7 +400,7 @@ __device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t 
 // float32 sliding sums drift by about sqrt(kSeg) roundings between
 // restarts, far inside the 1% + 0.01 filter margin).
 constexpr int kSeg = 512;
-constexpr int kDiagBlock = 128; // diagonals per CTA
+constexpr int kDiagBlock = 256; // diagonals per CTA
 
 __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t) {
   return xl ? xh[t] + xl[t] : xh[t];
@@ -492,7 +492,7 @@ k_allpairs(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int
 // windows slide with the product sum, so no per-window statistic is read
 // per step.
 template <int DP, bool LO, bool ROWMIN>
-__global__ void __launch_bounds__(kDiagBlock, 4)
+__global__ void __launch_bounds__(kDiagBlock, 2)
 k_allpairs_pm(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;

@@ -323,18 +323,20 @@ void free_all(momenti_handle* h, bool host = false) {
 // bound), full verifications, records handed to TOP on the host.
 double predict_rep_ms(const Index& ix, uint64_t tiles, uint64_t sub_checks, uint64_t events,
                       uint64_t verified, uint64_t records) {
-  const double G = double((ix.D + 7) / 8);
+  const int G = (ix.D + 7) / 8;                    // byte-plane words per hash value
+  const double tile_ns = G == 1 ? 3.0 : (G == 2 ? 4.1 : 5.3 * double(G));
   const double verify_ns = 2.0 * double(ix.w) * double(ix.Dp ? ix.Dp : ix.D) / 2400.0 + 0.5;
-  return 1e-6 * (2.5 * G * double(tiles) + 0.4 * double(sub_checks) + 0.8 * double(events) +
+  return 1e-6 * (tile_ns * double(tiles) + 0.4 * double(sub_checks) + 0.8 * double(events) +
                  verify_ns * double(verified) + 100.0 * double(records));
 }
 
 double predict_exact_ms(const Index& ix, int passes) {
   double ps_pair;                                  // all-pairs kernel, per pair
-  if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 8.0;
-  else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 25.0;
-  else if (ix.xT && !ix.has_lo && ix.Dp == 16) ps_pair = 75.0;
-  else ps_pair = 10.0 * double(ix.D);
+  if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 5.0;
+  else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 11.0;
+  else if (ix.xT && !ix.has_lo && ix.Dp == 16) ps_pair = 40.0;
+  else if (ix.D <= 32) ps_pair = 8.0 * double(ix.D);
+  else ps_pair = 31.0 * double(ix.D);
   const double pairs = 0.5 * double(ix.M) * double(ix.M);
   return double(passes) * (ps_pair * 1e-9 * pairs + 0.2) + 2.0;
 }
@@ -735,7 +737,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     const int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
     // sort scratch: a batch of repetitions whose ping-pong buffers stay near L2 size
     const uint64_t seg_bytes = uint64_t(M) * (8 + 8 + 4 + 4);
-    int sort_reps = int(std::max<uint64_t>(1, (uint64_t(96) << 20) / (seg_bytes * D)));
+    int sort_reps = int(std::max<uint64_t>(1, (uint64_t(320) << 20) / (seg_bytes * D)));
     // traversal scratch
     const int64_t C = (M + 31) / 32;
     int chunk = std::min(kChunkReps, L_user);
@@ -1094,9 +1096,12 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
         pool.tau_trunc = std::min(pool.tau_trunc, double(tau));
       }
       if (probe && !stop_i) {
+        // the rest of this level, and the lower levels (shorter prefixes
+        // collide more: each costs at least as much as this one)
         const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
-        const double rest = double(L - 1) *
-            predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events, verified, nrec);
+        const double rep = predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events,
+                                          verified, nrec);
+        const double rest = double(L - 1) * rep + double(i - 1) * double(L) * rep;
         const double exact = predict_exact_ms(ix, int(pool.top.size()) == k ? 1 : 2);
         if (rest > exact) {
           switch_level = i;

@@ -90,7 +90,12 @@ def _pick_offsets(rng: np.random.Generator, count: int, n: int, w: int, gap: int
         offs = sorted(int(x) for x in rng.integers(0, M, size=count))
         if all(offs[i + 1] - offs[i] >= gap for i in range(count - 1)):
             return offs
-    raise ValueError("cannot place planted motifs: series too short")
+    # crowded: draw in the range left after reserving the gaps, then spread
+    free = M - (count - 1) * gap
+    if free <= 0:
+        raise ValueError("cannot place planted motifs: series too short")
+    base = sorted(int(x) for x in rng.integers(0, free, size=count))
+    return [b + i * gap for i, b in enumerate(base)]
 
 
 def plant_motifs(rng: np.random.Generator, T: np.ndarray, w: int, n_motifs: int,

@@ -244,7 +244,9 @@ def assert_same_motifs(got, ref, rel=1e-9):
 
 
 @pytest.mark.parametrize("seed,n,D,w,d,k", [(0, 300, 3, 20, 2, 3), (1, 700, 2, 33, 1, 2),
-                                           (2, 1500, 4, 50, 2, 3), (3, 1031, 5, 64, 3, 2)])
+                                           (2, 1500, 4, 50, 2, 3), (3, 1031, 5, 64, 3, 2),
+                                           (11, 900, 12, 40, 4, 2), (12, 700, 20, 30, 5, 2),
+                                           (13, 500, 40, 24, 10, 2)])
 def test_topk_exact_matches_oracle(mom, seed, n, D, w, d, k):
     wl = synth.tiny(seed, n=n, D=D, w=w, d=d, k=k, n_motifs=1)
     h, _, _ = make(mom, wl, L=2)
