@@ -34,6 +34,30 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that
+# ncu measured for a kernel on this workload at full size, with the SHA-256
+# of the source file that kernel was built from: reported only while that
+# file is unchanged (the capture and its command are summarised in profiles/)
+NCU_TRAFFIC = {
+    "allpairs": ("paper_2502_14446_gb300/csrc/k_verify.cu",
+                 "5c61807f606fd36df00deac4180dff89cd720f6df31c588c3ff676daff5fbd10", 6986496),
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+    if kernel not in NCU_TRAFFIC:
+        return None
+    path, sha, nbytes = NCU_TRAFFIC[kernel]
+    try:
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 # dominant kernels and their algorithmic work per launch
 DOMINANT = ("proj_hash_tc", "collide", "subbucket", "sort_scatter", "allpairs", "proj_hash_fp32",
             "verify_events")
@@ -182,7 +206,7 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
         return {"kernel": kernel, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None, "launches": k_n, "ms_per_launch": k_ms / k_n}
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_src": src, "launches": k_n,
+            "frac": achieved / peak, "traffic": measured_traffic(kernel), "peak_src": src, "launches": k_n,
             "ms_per_launch": k_ms / k_n, "work_per_step": work / steps}
 
 

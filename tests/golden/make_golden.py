@@ -6,10 +6,13 @@ small JSON record: the workload name and seed, the exact top-k motifs of
 Definition (top-k multidimensional motifs, Section 3.1) as
 [dist_d, a, b, dims, dist_max], and the oracle's wall time.
 
-Usage: python tests/golden/make_golden.py plain_small plain_fp32 batch_small
+Usage: python tests/golden/make_golden.py plain_small plain_fp32 batch_small guarantee
 
 batch_small is the batching form at reduced lengths (6 series, n
 log-uniform in [1500, 5000]); its file holds one record per series.
+guarantee holds the exact top-2 of 100 small random-walk series (seeds
+100..199: n=1500, D=3, w=50, d=2, two planted motifs) for the failure-rate
+test of Lemma topk.
 """
 import json
 import os
@@ -65,9 +68,26 @@ def make_batch_small(seed: int = 0):
     print(path, f"{dt:.1f}s")
 
 
+def make_guarantee():
+    recs = []
+    t0 = time.time()
+    for seed in range(100, 200):
+        wl = synth.tiny(seed, 1500, 3, 50, 2, k=2, n_motifs=2)
+        res = O.exact_topk(wl.series, wl.w, wl.d, wl.k, block=256)
+        recs.append({"seed": seed, "motifs": [[m[0], m[1], m[2], list(m[3]), m[4]] for m in res]})
+    dt = time.time() - t0
+    path = os.path.join(OUT, "exact_guarantee_seeds100_199.json")
+    with open(path, "w") as fh:
+        json.dump({"workload": "tiny(seed, 1500, 3, 50, 2, k=2, n_motifs=2)", "series": recs,
+                   "oracle_seconds": dt}, fh, indent=0)
+    print(path, f"{dt:.1f}s")
+
+
 if __name__ == "__main__":
     for nm in sys.argv[1:] or ["plain_small"]:
         if nm == "batch_small":
             make_batch_small()
+        elif nm == "guarantee":
+            make_guarantee()
         else:
             make(nm)
