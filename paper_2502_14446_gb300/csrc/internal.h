@@ -172,14 +172,18 @@ cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s);
 struct BucketJob {
   uint32_t seg, start, n, pad;
 };
-// members of one bucket a CTA holds in shared memory: 8192 for D <= 8
-// (about 190 KB), 4096 for D <= 16
-int subbucket_cap(int D);
-// counts[0] = jobs, counts[1] = largest bucket
-cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob* jobs,
+// Largest bucket (members) a CTA holds in shared memory at prefix length i.
+int subbucket_cap(int D, int i);
+// Buckets of prefix length i (1..3): large ones to jobs[0 ..) (counts[0]),
+// those of at most 32 members to jobs[job_cap/2 ..) (counts[2]);
+// counts[1] = the largest bucket.  counts must be zeroed by the caller.
+cudaError_t launch_bucket_jobs(const Index& ix, int i, int j0, int j1, int d, BucketJob* jobs,
                                uint64_t job_cap, unsigned long long* counts, cudaStream_t s);
-cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashSet& hs,
-                             const CollideScratch& cs, const BucketJob* jobs,
+// Collision counting at prefix length i (1..3, d >= 2, D <= 16) from the
+// bucket jobs: a CTA per large bucket (sub-buckets by a second dim), a
+// warp per small one; the same events as launch_collide.
+cudaError_t launch_subbucket(const Index& ix, int i, int j0, int j1, int d, const HashSet& hs,
+                             const CollideScratch& cs, const BucketJob* jobs, uint64_t job_cap,
                              const unsigned long long* counts, int max_bucket, cudaStream_t s);
 
 // ---- k_verify.cu --------------------------------------------------------

@@ -20,6 +20,8 @@
 // balanced however skewed the bucket sizes are.
 #include "internal.h"
 
+#include <algorithm>
+
 namespace momenti {
 
 namespace {
@@ -400,11 +402,18 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
 
 // ---- prefix length 1: buckets split by a second dimension ---------------
 
-__global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs, int d,
+// Buckets of prefix length i (runs with lcp >= i) of the dims that can be
+// a pair's lowest colliding dim: buckets of at most kSmallJob members go to
+// the warp list (jobs + job_cap / 2, count counts[2]), larger ones to the
+// CTA list (jobs, count counts[0]); counts[1] = the largest bucket.
+constexpr int kSmallJob = 32;
+
+__global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i, int d,
                               BucketJob* __restrict__ jobs, uint64_t job_cap,
                               unsigned long long* __restrict__ counts) {
   const int64_t total = int64_t(segs) * sg.M;
   const int lane = threadIdx.x & 31;
+  const uint64_t half = job_cap / 2;
   for (int64_t q0 = blockIdx.x * int64_t(blockDim.x); q0 < total; q0 += int64_t(gridDim.x) * blockDim.x) {
     const int64_t q = q0 + threadIdx.x;
     bool emit = false;
@@ -414,22 +423,33 @@ __global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs,
       p = uint32_t(q - int64_t(seg) * sg.M);
       const int f = int(seg % sg.D);
       const uint8_t* L = lcp + sg.base(int(seg));
-      if (f <= sg.D - d && int(L[p]) < 1 && int64_t(p) + 1 < sg.M && int(L[p + 1]) >= 1) {
+      if (f <= sg.D - d && int(L[p]) < i && int64_t(p) + 1 < sg.M && int(L[p + 1]) >= i) {
         int64_t e = p + 1;
-        while (e + 1 < sg.M && int(L[e + 1]) >= 1) ++e;
+        while (e + 1 < sg.M && int(L[e + 1]) >= i) ++e;
         n = uint32_t(e - p + 1);
         emit = true;
       }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, emit);
-    if (m) {
+    const bool small = emit && n <= uint32_t(kSmallJob), large = emit && !small;
+    const unsigned ms = __ballot_sync(0xffffffffu, small), ml = __ballot_sync(0xffffffffu, large);
+    const unsigned lt = (1u << lane) - 1u;
+    if (ml) {
       unsigned long long base = 0;
-      if (lane == __ffs(m) - 1) base = atomicAdd(&counts[0], (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-      if (emit) {
-        const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
-        if (pos < job_cap) jobs[pos] = BucketJob{seg, p, n, 0u};
+      if (lane == __ffs(ml) - 1) base = atomicAdd(&counts[0], (unsigned long long)__popc(ml));
+      base = __shfl_sync(0xffffffffu, base, __ffs(ml) - 1);
+      if (large) {
+        const unsigned long long pos = base + __popc(ml & lt);
+        if (pos < half) jobs[pos] = BucketJob{seg, p, n, 0u};
         atomicMax(&counts[1], (unsigned long long)n);
+      }
+    }
+    if (ms) {
+      unsigned long long base = 0;
+      if (lane == __ffs(ms) - 1) base = atomicAdd(&counts[2], (unsigned long long)__popc(ms));
+      base = __shfl_sync(0xffffffffu, base, __ffs(ms) - 1);
+      if (small) {
+        const unsigned long long pos = base + __popc(ms & lt);
+        if (pos < half) jobs[half + pos] = BucketJob{seg, p, n, 0u};
       }
     }
   }
@@ -447,26 +467,36 @@ struct SubArgs {
   const BucketJob* jobs;
   const unsigned long long* counts;
   int cap;
+  uint64_t job_cap;
 };
 
-// NW byte-plane words per hash level: dims 8g .. 8g+7 in word g (D <= 8 NW).
-template <int NW>
+// Byte plane q of dims 8c .. 8c+7 of a window's keys (byte e = dim 8c + e).
+__device__ __forceinline__ uint64_t key_plane(const uint64_t* kw, int c, int q, int D) {
+  uint64_t a = 0;
+  for (int e = 0; e < 8 && 8 * c + e < D; ++e) a |= ((kw[8 * c + e] >> (56 - 8 * q)) & 0xFFull) << (8 * e);
+  return a;
+}
+
+// CTA per large bucket of prefix length I (the first I hash values equal
+// in its dim f).  NW byte-plane words per hash value (dims 8c .. 8c+7 in
+// word c), planes of hash values 0..I (value I only for the level
+// de-duplication).  A pair is handled from its two lowest colliding dims
+// (f, f2): members are split into sub-buckets by a hash of f2's first I
+// values, and only pairs inside a sub-bucket are compared.
+template <int NW, int I>
 __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
-  // members of one bucket: first and second hash values of every dim as
-  // byte planes (byte e of word c = dim 8c + e), window ids, sub-bucket
-  // keys, permutation
+  constexpr int NQ = I + 1;
   extern __shared__ uint64_t sub_smem[];
   const int cap = g.cap;
-  uint64_t* p0 = sub_smem;                 // [NW][cap]
-  uint64_t* p1 = p0 + NW * cap;            // [NW][cap]
-  uint32_t* widx = reinterpret_cast<uint32_t*>(p1 + NW * cap);
+  uint64_t* pl = sub_smem;                 // [NQ][NW][cap]
+  uint32_t* widx = reinterpret_cast<uint32_t*>(pl + NQ * NW * cap);
   uint32_t* hist = widx + cap;
   uint32_t* bend = hist + 256;
   uint16_t* perm = reinterpret_cast<uint16_t*>(bend + 256);
   uint8_t* skey = reinterpret_cast<uint8_t*>(perm + cap);
   const int tid = threadIdx.x, lane = tid & 31;
   const int D = g.sg.D;
-  const bool lvl_dup = g.K > 1;
+  const bool lvl_dup = g.K > I;
   uint64_t valid[NW];
 #pragma unroll
   for (int c = 0; c < NW; ++c) {
@@ -475,6 +505,7 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
                        : (nd <= 0 ? 0ull : (0x8080808080808080ull & ((1ull << (8 * nd)) - 1)));
   }
   uint64_t njobs = g.counts[0];
+  if (njobs > g.job_cap / 2) njobs = g.job_cap / 2;
   unsigned long long checks = 0;                   // pairs compared by this thread
   for (uint64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
     const BucketJob job = g.jobs[jb];
@@ -490,16 +521,9 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       widx[q] = wv;
       const uint64_t* kw = Kj + int64_t(wv) * D;
 #pragma unroll
-      for (int c = 0; c < NW; ++c) {
-        uint64_t a0 = 0, a1 = 0;
-        for (int e = 0; e < 8 && 8 * c + e < D; ++e) {
-          const uint64_t key = kw[8 * c + e];
-          a0 |= (key >> 56) << (8 * e);
-          a1 |= ((key >> 48) & 0xFFull) << (8 * e);
-        }
-        p0[c * cap + q] = a0;
-        p1[c * cap + q] = a1;
-      }
+      for (int h = 0; h < NQ; ++h)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) pl[(h * NW + c) * cap + q] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
     }
     __syncthreads();
     // second-lowest colliding dim f2 leaves d - 2 dims above it
@@ -508,8 +532,11 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       __syncthreads();
       const int c2 = f2 >> 3, e2 = f2 & 7;
       for (int q = tid; q < n; q += blockDim.x) {
-        const uint8_t k = uint8_t(p0[c2 * cap + q] >> (8 * e2));
-        skey[q] = k;
+        uint32_t k = 0;
+#pragma unroll
+        for (int h = 0; h < I; ++h) k ^= uint32_t(pl[(h * NW + c2) * cap + q] >> (8 * e2)) << h;
+        k &= 255u;
+        skey[q] = uint8_t(k);
         atomicAdd(&hist[k], 1u);
       }
       __syncthreads();
@@ -534,7 +561,7 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       __syncthreads();
       for (int b = tid; b < 256; b += blockDim.x) bend[b] = hist[b];
       __syncthreads();
-      // pairs inside a sub-bucket collide in f and f2 (first hash value);
+      // pairs inside a sub-bucket may collide in f and f2;
       // below[c]: bytes of dims < f2 in word c, only_f[c]: the byte of f
       uint64_t below[NW], only_f[NW];
 #pragma unroll
@@ -546,9 +573,11 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
       for (int r = tid; r < n; r += blockDim.x) {
         const int u = perm[r];
         const int end = int(bend[skey[u]]);
-        uint64_t pu0[NW], pu1[NW];
+        uint64_t pu[NQ][NW];
 #pragma unroll
-        for (int c = 0; c < NW; ++c) { pu0[c] = p0[c * cap + u]; pu1[c] = p1[c * cap + u]; }
+        for (int h = 0; h < NQ; ++h)
+#pragma unroll
+          for (int c = 0; c < NW; ++c) pu[h][c] = pl[(h * NW + c) * cap + u];
         const uint32_t wu = widx[u];
         checks += (unsigned long long)(end > r + 1 ? end - r - 1 : 0);
         for (int r2 = r + 1; r2 < end; ++r2) {
@@ -558,16 +587,20 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
           int w0 = 0;
 #pragma unroll
           for (int c = 0; c < NW; ++c) {
-            m[c] = zero_bytes(pu0[c] ^ p0[c * cap + v]) & valid[c];
+            uint64_t x = valid[c];
+#pragma unroll
+            for (int h = 0; h < I; ++h) x &= zero_bytes(pu[h][c] ^ pl[(h * NW + c) * cap + v]);
+            m[c] = x;
             // f and f2 are the two lowest colliding dims
-            lowest = lowest && (m[c] & below[c]) == only_f[c];
-            w0 += __popcll(m[c]);
+            lowest = lowest && (x & below[c]) == only_f[c];
+            w0 += __popcll(x);
           }
           if (!lowest || w0 < g.d) continue;
           if (lvl_dup) {
             int w1 = 0;
 #pragma unroll
-            for (int c = 0; c < NW; ++c) w1 += __popcll(m[c] & zero_bytes(pu1[c] ^ p1[c * cap + v]));
+            for (int c = 0; c < NW; ++c)
+              w1 += __popcll(m[c] & zero_bytes(pu[I][c] ^ pl[(I * NW + c) * cap + v]));
             if (w1 >= g.d) continue;
           }
           const uint32_t wv = widx[v];
@@ -585,6 +618,95 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
         }
       }
       __syncthreads();
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) checks += __shfl_xor_sync(0xffffffffu, checks, o);
+  if (lane == 0 && checks) atomicAdd(&g.counters[5], checks);
+}
+
+// Warp per small bucket (at most 32 members, one per lane): every pair is
+// compared directly and handled from its lowest colliding dim f.
+template <int NW, int I>
+__global__ void __launch_bounds__(256) k_subwarp(SubArgs g) {
+  constexpr int NQ = I + 1;
+  const int lane = threadIdx.x & 31;
+  const int D = g.sg.D;
+  const bool lvl_dup = g.K > I;
+  uint64_t valid[NW];
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    const int nd = D - 8 * c;
+    valid[c] = nd >= 8 ? 0x8080808080808080ull
+                       : (nd <= 0 ? 0ull : (0x8080808080808080ull & ((1ull << (8 * nd)) - 1)));
+  }
+  const uint64_t half = g.job_cap / 2;
+  uint64_t njobs = g.counts[2];
+  if (njobs > half) njobs = half;
+  const uint64_t nwarps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  unsigned long long checks = 0;
+  for (uint64_t jb = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; jb < njobs; jb += nwarps) {
+    const BucketJob job = g.jobs[half + jb];
+    const int n = int(job.n);
+    const int seg = int(job.seg);
+    const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
+    const uint32_t* O = g.order + g.sg.base(seg) + job.start;
+    const uint64_t* Kj = g.keys + int64_t(j) * g.sg.M * D;
+    uint32_t wu = 0;
+    uint64_t pu[NQ][NW];
+    if (lane < n) {
+      wu = O[lane];
+      const uint64_t* kw = Kj + int64_t(wu) * D;
+#pragma unroll
+      for (int h = 0; h < NQ; ++h)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) pu[h][c] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
+    } else {
+#pragma unroll
+      for (int h = 0; h < NQ; ++h)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) pu[h][c] = 0ull;
+    }
+    // dims below f must not collide: bytes of dims < f
+    uint64_t below[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      const int cf = f >> 3, ef = f & 7;
+      below[c] = (c < cf ? ~0ull : (c == cf ? ((1ull << (8 * ef)) - 1) : 0ull)) & valid[c];
+    }
+    for (int v = 0; v < n - 1; ++v) {
+      uint64_t pv[NQ][NW];
+#pragma unroll
+      for (int h = 0; h < NQ; ++h)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) pv[h][c] = __shfl_sync(0xffffffffu, pu[h][c], v);
+      const uint32_t wv = __shfl_sync(0xffffffffu, wu, v);
+      bool emit = lane > v && lane < n;
+      checks += emit ? 1u : 0u;
+      int w0 = 0, w1 = 0;
+      bool low = false;
+#pragma unroll
+      for (int c = 0; c < NW; ++c) {
+        uint64_t x = valid[c];
+#pragma unroll
+        for (int h = 0; h < I; ++h) x &= zero_bytes(pu[h][c] ^ pv[h][c]);
+        low = low || (x & below[c]) != 0;
+        w0 += __popcll(x);
+        if (lvl_dup) w1 += __popcll(x & zero_bytes(pu[I][c] ^ pv[I][c]));
+      }
+      emit = emit && !low && w0 >= g.d && !(lvl_dup && w1 >= g.d);
+      const uint32_t a = min(wu, wv), b = max(wu, wv);
+      emit = emit && int64_t(b) - int64_t(a) > g.excl;
+      const uint64_t key = (uint64_t(a) << 32) | b;
+      if (emit) emit = !set_contains(g.hs, key);
+      const unsigned m = __ballot_sync(0xffffffffu, emit);
+      if (!m) continue;
+      unsigned long long base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(&g.counters[0], (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (emit) {
+        const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+        if (pos < g.ev_cap) g.events[pos] = Event{a, b, int32_t(j), 0u};
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) checks += __shfl_xor_sync(0xffffffffu, checks, o);
@@ -626,46 +748,55 @@ static cudaError_t dispatch_collide(int i, bool plain, const CollideArgs& g, siz
   return plain ? dispatch_plain<true>(i, g, smem, s) : dispatch_plain<false>(i, g, smem, s);
 }
 
-cudaError_t launch_bucket_jobs(const Index& ix, int j0, int j1, int d, BucketJob* jobs,
+cudaError_t launch_bucket_jobs(const Index& ix, int i, int j0, int j1, int d, BucketJob* jobs,
                                uint64_t job_cap, unsigned long long* counts, cudaStream_t s) {
   const int segs = (j1 - j0) * ix.D;
   Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
   const int64_t total = int64_t(segs) * ix.M;
   int64_t g = (total + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<unsigned(g), 256, 0, s>>>(ix.lcp, sg, segs, d, jobs, job_cap, counts));
+  if (g > 152 * 32) g = 152 * 32;
+  MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<unsigned(g), 256, 0, s>>>(ix.lcp, sg, segs, i, d, jobs, job_cap, counts));
   return cudaGetLastError();
 }
 
-size_t subbucket_smem(int cap, int D) {
+size_t subbucket_smem(int cap, int D, int i) {
   const int nw = (D + 7) / 8;
-  return size_t(cap) * (16 * nw + 4 + 2 + 1) + 2 * 256 * 4 + 16;
+  return size_t(cap) * (8 * nw * (i + 1) + 4 + 2 + 1) + 2 * 256 * 4 + 16;
 }
 
-int subbucket_cap(int D) { return D <= 8 ? 8192 : 4096; }
+int subbucket_cap(int D, int i) {
+  for (int cap = 8192; cap >= 1024; cap /= 2)
+    if (subbucket_smem(cap, D, i) <= size_t(200) * 1024) return cap;
+  return 0;
+}
 
-cudaError_t launch_subbucket(const Index& ix, int j0, int j1, int d, const HashSet& hs,
-                             const CollideScratch& cs, const BucketJob* jobs,
-                             const unsigned long long* counts, int max_bucket, cudaStream_t s) {
-  if (ix.D > 16 || max_bucket > subbucket_cap(ix.D)) return cudaErrorInvalidValue;
-  Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
-  const int cap = ((max_bucket + 255) / 256) * 256;
-  SubArgs g{ix.order, ix.keys, sg, ix.K, d, ix.excl, hs, cs.events, cs.ev_cap, cs.counters, jobs,
-            counts, cap};
-  const size_t smem = subbucket_smem(cap, ix.D);
+template <int NW, int I>
+static cudaError_t run_subbucket(const SubArgs& g, size_t smem, cudaStream_t s) {
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket<NW, I>), smem);
+  if (e != cudaSuccess) return e;
   int per_sm = int((size_t(200) * 1024) / smem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
-  if (ix.D <= 8) {
-    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket<1>), smem);
-    if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("subbucket", s, k_subbucket<1><<<152 * per_sm, 256, smem, s>>>(g));
-  } else {
-    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_subbucket<2>), smem);
-    if (e != cudaSuccess) return e;
-    MOMENTI_LAUNCH("subbucket", s, k_subbucket<2><<<152 * per_sm, 256, smem, s>>>(g));
-  }
+  MOMENTI_LAUNCH("subbucket", s, k_subbucket<NW, I><<<152 * per_sm, 256, smem, s>>>(g));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I><<<152 * 8, 256, 0, s>>>(g));
   return cudaGetLastError();
+}
+
+cudaError_t launch_subbucket(const Index& ix, int i, int j0, int j1, int d, const HashSet& hs,
+                             const CollideScratch& cs, const BucketJob* jobs, uint64_t job_cap,
+                             const unsigned long long* counts, int max_bucket, cudaStream_t s) {
+  if (ix.D > 16 || i < 1 || i > 3 || max_bucket > subbucket_cap(ix.D, i)) return cudaErrorInvalidValue;
+  Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
+  const int cap = std::max(256, ((max_bucket + 255) / 256) * 256);
+  SubArgs g{ix.order, ix.keys, sg, ix.K, d, ix.excl, hs, cs.events, cs.ev_cap, cs.counters, jobs,
+            counts, cap, job_cap};
+  const size_t smem = subbucket_smem(cap, ix.D, i);
+  const bool two = ix.D > 8;
+  switch (i) {
+    case 1: return two ? run_subbucket<2, 1>(g, smem, s) : run_subbucket<1, 1>(g, smem, s);
+    case 2: return two ? run_subbucket<2, 2>(g, smem, s) : run_subbucket<1, 2>(g, smem, s);
+    default: return two ? run_subbucket<2, 3>(g, smem, s) : run_subbucket<1, 3>(g, smem, s);
+  }
 }
 
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {

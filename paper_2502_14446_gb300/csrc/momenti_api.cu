@@ -326,7 +326,7 @@ double predict_rep_ms(const Index& ix, uint64_t tiles, uint64_t sub_checks, uint
   const int G = (ix.D + 7) / 8;                    // byte-plane words per hash value
   const double tile_ns = G == 1 ? 3.0 : (G == 2 ? 4.1 : 5.3 * double(G));
   const double verify_ns = 2.0 * double(ix.w) * double(ix.Dp ? ix.Dp : ix.D) / 2400.0 + 0.5;
-  return 1e-6 * (tile_ns * double(tiles) + 0.4 * double(sub_checks) + 0.8 * double(events) +
+  return 1e-6 * (tile_ns * double(tiles) + 0.025 * double(sub_checks) + 0.8 * double(events) +
                  verify_ns * double(verified) + 100.0 * double(records));
 }
 
@@ -339,6 +339,13 @@ double predict_exact_ms(const Index& ix, int passes) {
   else ps_pair = 31.0 * double(ix.D);
   const double pairs = 0.5 * double(ix.M) * double(ix.M);
   return double(passes) * (ps_pair * 1e-9 * pairs + 0.2) + 2.0;
+}
+
+// Bucket jobs of one chunk of repetitions (large and small lists, half each)
+uint64_t job_cap_for(int64_t M, int D) {
+  uint64_t c = uint64_t(1) << 20;
+  while (c < uint64_t(kChunkReps) * uint64_t(D) * uint64_t(M) && c < (uint64_t(1) << 24)) c <<= 1;
+  return c;
 }
 
 uint64_t next_pow2(uint64_t x) {
@@ -727,6 +734,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
                            + uint64_t(D) * n * elem                          // transient staging
                            + uint64_t(D) * M * (8 + 8 + 4 + 4 + 4)           // stats
                            + (D <= 16 ? uint64_t(16) * (3 * n + 3 * M) * 4 : 0)  // point-major copies
+                           + (D <= 16 && p.d >= 2 ? job_cap_for(M, D) * sizeof(BucketJob) : 0)
                            + (uint64_t(64) << 20);                           // small scratch
     const uint64_t per_rep = uint64_t(M) * D * (8 + 4 + 1)                   // keys, order, lcp
                              + uint64_t(D) * kRepStride * Wp * (2 + 4)       // a16, a32
@@ -841,9 +849,9 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     hs.cap = hs_cap;
     CK(dalloc(h, &hs.keys, size_t(hs_cap)));
     if (D <= 16 && p.d >= 2) {
-      h->job_cap = uint64_t(1) << 20;
+      h->job_cap = job_cap_for(M, D);
       CK(dalloc(h, &h->jobs, size_t(h->job_cap)));
-      CK(dalloc(h, &h->job_counts, 2));
+      CK(dalloc(h, &h->job_counts, 4));
     }
     cs.ev_cap = uint64_t(1) << 22;
     h->ev_budget = std::max<uint64_t>(uint64_t(1) << 28, limit / 8);
@@ -991,18 +999,20 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
       // halve the chunk beyond the event budget
       for (;;) {
         bool sub = false;
-        unsigned long long jc[2] = {0, 0};
-        if (i == 1 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
-          CK(cudaMemsetAsync(h->job_counts, 0, 2 * sizeof(unsigned long long), s));
-          CK(launch_bucket_jobs(ix, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
+        unsigned long long jc[3] = {0, 0, 0};
+        if (i <= 3 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
+          CK(cudaMemsetAsync(h->job_counts, 0, 3 * sizeof(unsigned long long), s));
+          CK(launch_bucket_jobs(ix, i, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
           CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
-          sub = jc[0] <= h->job_cap && jc[1] <= uint64_t(subbucket_cap(ix.D));
+          sub = jc[0] <= h->job_cap / 2 && jc[2] <= h->job_cap / 2 &&
+                jc[1] <= uint64_t(subbucket_cap(ix.D, i));
         }
         CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
         used_sub = sub;
         if (sub) {
-          CK(launch_subbucket(ix, j0, j1, d, h->hs, h->cs, h->jobs, h->job_counts, int(jc[1]), s));
+          CK(launch_subbucket(ix, i, j0, j1, d, h->hs, h->cs, h->jobs, h->job_cap, h->job_counts,
+                              int(jc[1]), s));
         } else {
           CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
           const int64_t E = int64_t(j1 - j0) * ix.D * ((ix.M + 31) / 32);
