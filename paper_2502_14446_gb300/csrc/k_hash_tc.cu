@@ -12,8 +12,10 @@
 // product accumulates z_hi . a + z_lo . a in FP32, so it is exact to about
 // 2^-22 relative (the vectors a are half-representable by construction).
 //
-// Warp roles (10 warps): 0 TMA producer of the vectors, 1 MMA issuer and
-// TMEM owner, 2-5 converters, 6-9 epilogue.  A 3-stage ring of
+// Warp roles (26 warps): 0 TMA producer of the vectors, 1 MMA issuer and
+// TMEM owner, 2-9 converters (two threads per row, half a K-chunk each),
+// 10-25 epilogue (four warps per TMEM lane quarter, a quarter of the
+// columns each).  A 3-stage ring of
 // (Z_hi, Z_lo, vectors) chunks feeds the MMA; two 256-column TMEM
 // accumulators let the epilogue hash one 32-repetition block while the next
 // one is multiplied.  Every wait is bounded: on timeout the kernel raises
@@ -37,7 +39,9 @@ constexpr int kBK = 64;                  // fp16 per 128-byte swizzle row
 constexpr int kStages = 3;
 constexpr int kAStage = kBM * kBK * 2;   // 16 KB per operand half
 constexpr int kBStage = kBN * kBK * 2;   // 32 KB
-constexpr int kThreads = 320;
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr float kMargin = 1.0f / 2048.0f;
 constexpr long long kSpinCycles = 4000000000ll;   // about 2 s at 2 GHz
 
@@ -223,13 +227,13 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(full_a(s), 4);
+      mbar_init(full_a(s), kConvWarps);
       mbar_init(full_b(s), 1);
       mbar_init(empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 4);
+      mbar_init(tempty(b), kEpiWarps);
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -295,9 +299,11 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       umma_commit(mma_done);
       mbar_wait(mma_done, 0, g.err);
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + kConvWarps) {
     // ---- converters: z-normalised Hankel K-chunks, hi/lo halves ----
-    const int m = threadIdx.x - 64;                 // row 0..127
+    const int ct = threadIdx.x - 64;
+    const int m = ct >> 1;                          // row 0..127
+    const int c0 = (ct & 1) * (kBK / 16);           // first of this thread's 16-byte chunks
     const float mh = sst[m], ml = sst[kBM + m], is = sst[2 * kBM + m];
     for (int s = 0; s < steps; ++s) {
       const int st = s % kStages;
@@ -307,23 +313,21 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
       uint8_t* ahi = base + (S.a - smem_u32(base)) + st * 2 * kAStage;
       uint8_t* alo = ahi + kAStage;
 #pragma unroll
-      for (int c = 0; c < kBK / 8; ++c) {
+      for (int cc = 0; cc < kBK / 16; ++cc) {
+        const int c = c0 + cc;
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          float z2[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int t = kc * kBK + c * 8 + e * 2 + u;
-            float z = 0.f;
-            if (t < g.w) z = ((sx[m + t] - mh) + ((lo ? sxl[m + t] : 0.f) - ml)) * is;
-            z2[u] = z;
-          }
-          __half h0 = __float2half_rn(z2[0]), h1 = __float2half_rn(z2[1]);
-          __half l0 = __float2half_rn(z2[0] - __half2float(h0));
-          __half l1 = __float2half_rn(z2[1] - __half2float(h1));
-          hw[e] = uint32_t(__half_as_ushort(h0)) | (uint32_t(__half_as_ushort(h1)) << 16);
-          lw[e] = uint32_t(__half_as_ushort(l0)) | (uint32_t(__half_as_ushort(l1)) << 16);
+          const int t = kc * kBK + c * 8 + e * 2;
+          float2 z;
+          z.x = t < g.w ? ((sx[m + t] - mh) + ((lo ? sxl[m + t] : 0.f) - ml)) * is : 0.f;
+          z.y = t + 1 < g.w ? ((sx[m + t + 1] - mh) + ((lo ? sxl[m + t + 1] : 0.f) - ml)) * is : 0.f;
+          // packed conversions: hi = half(z), lo = half(z - hi)
+          const __half2 h = __float22half2_rn(z);
+          const float2 hb = __half22float2(h);
+          const __half2 l = __float22half2_rn(make_float2(z.x - hb.x, z.y - hb.y));
+          hw[e] = *reinterpret_cast<const uint32_t*>(&h);
+          lw[e] = *reinterpret_cast<const uint32_t*>(&l);
         }
         const int chunk = c ^ (m & 7);
         *reinterpret_cast<uint4*>(ahi + m * 128 + chunk * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -335,39 +339,41 @@ k_proj_hash_tc(const __grid_constant__ CUtensorMap tmap, TcArgs g) {
     }
   } else {
     // ---- epilogue: TMEM -> hash bytes -> keys ----
+    const int ew = warp - (2 + kConvWarps);        // 0 .. kEpiWarps-1
     const int quarter = warp & 3;                  // TMEM lanes 32*quarter ..
+    constexpr int kGroups = (kBN / 32) / (kEpiWarps / 4);   // column groups of 32 per warp
+    const int qbeg = (ew >> 2) * kGroups, qend = qbeg + kGroups;
     const int m = quarter * 32 + lane;
     const int64_t a = a0 + m;
     const bool row_ok = a < g.M;
-    const float* bo = g.boff + int64_t(f) * g.N;
+    const float* bo = g.boff + int64_t(f) * g.N + int64_t(g.j0) * kRepStride;
     for (int nc = 0; nc < nchunks; ++nc) {
       const int buf = nc & 1;
       bool ok = mbar_wait(tfull(buf), (nc >> 1) & 1, g.err);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
 #pragma unroll 1
-      for (int q = 0; q < kBN / 32; ++q) {
+      for (int q = qbeg; q < qend; ++q) {
+        // offsets of the 32 columns, scaled by 1/r, one per lane
+        const int col0 = nc * kBN + q * 32;
+        const float myb = col0 + lane < NC ? bo[col0 + lane] * g.inv_r : 0.f;
         float v[32];
         tmem_ld32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(buf * kBN + q * 32), v);
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
-          const int j = g.j0 + (nc * kBN + q * 32) / kRepStride + rr;
+          const int j = g.j0 + col0 / kRepStride + rr;
           const bool live = j < g.j1 && row_ok;      // warp-uniform in j, per lane in row
           uint64_t key = 0;
 #pragma unroll
           for (int k = 0; k < kRepStride; ++k) {
-            const int nn = min(j, g.L - 1) * kRepStride + k;
-            const float qv = (v[rr * 8 + k] + bo[nn]) * g.inv_r;
+            const float qv = fmaf(v[rr * 8 + k], g.inv_r, __shfl_sync(0xffffffffu, myb, rr * 8 + k));
             float h = floorf(qv);
-            const bool near = live && k < g.K && fabsf(qv - rintf(qv)) < kMargin;
-            const unsigned fm = __ballot_sync(0xffffffffu, near);
-            if (fm) {
-              uint32_t base = 0;
-              if (lane == __ffs(fm) - 1) base = atomicAdd(g.flag_count, uint32_t(__popc(fm)));
-              base = __shfl_sync(0xffffffffu, base, __ffs(fm) - 1);
-              const uint32_t pos = base + __popc(fm & ((1u << lane) - 1u));
-              if (near && pos < g.flag_cap)
-                g.flags[pos] = (uint64_t(f) << 56) | (uint64_t(nn) << 32) | uint64_t(a);
+            const float fr = qv - h;
+            // near a bucket boundary: recomputed by the canonical FP32 form
+            if (live && k < g.K && (fr < kMargin || fr > 1.f - kMargin)) {
+              const uint32_t pos = atomicAdd(g.flag_count, 1u);
+              const int nn = j * kRepStride + k;
+              if (pos < g.flag_cap) g.flags[pos] = (uint64_t(f) << 56) | (uint64_t(nn) << 32) | uint64_t(a);
             }
             h = fminf(fmaxf(h, -128.f), 127.f);
             if (k < g.K) key |= uint64_t(int(h) + 128) << (56 - 8 * k);
