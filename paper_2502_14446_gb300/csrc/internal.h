@@ -174,9 +174,10 @@ struct BucketJob {
 };
 // Largest bucket (members) a CTA holds in shared memory at prefix length i.
 int subbucket_cap(int D, int i);
-// Buckets of prefix length i (1..3): large ones to jobs[0 ..) (counts[0]),
-// those of at most 32 members to jobs[job_cap/2 ..) (counts[2]);
-// counts[1] = the largest bucket.  counts must be zeroed by the caller.
+// Buckets of prefix length i (1..3) in four lists of job_cap/4 entries by
+// size: > 32 members (counts[0]), 9..32 (counts[2]), 5..8 (counts[3]),
+// 2..4 (counts[4]); counts[1] = the largest bucket.  counts (5 entries)
+// must be zeroed by the caller.
 cudaError_t launch_bucket_jobs(const Index& ix, int i, int j0, int j1, int d, BucketJob* jobs,
                                uint64_t job_cap, unsigned long long* counts, cudaStream_t s);
 // Collision counting at prefix length i (1..3, d >= 2, D <= 16) from the

@@ -403,17 +403,18 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
 // ---- prefix length 1: buckets split by a second dimension ---------------
 
 // Buckets of prefix length i (runs with lcp >= i) of the dims that can be
-// a pair's lowest colliding dim: buckets of at most kSmallJob members go to
-// the warp list (jobs + job_cap / 2, count counts[2]), larger ones to the
-// CTA list (jobs, count counts[0]); counts[1] = the largest bucket.
-constexpr int kSmallJob = 32;
-
+// a pair's lowest colliding dim, in four lists of job_cap / 4 entries each,
+// by size: list 0 more than 32 members (a CTA each, count counts[0]),
+// list 1 9..32 (a warp each, counts[2]), list 2 5..8 (8 lanes each,
+// counts[3]), list 3 2..4 (4 lanes each, counts[4]); counts[1] = the
+// largest bucket.
 __global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i, int d,
                               BucketJob* __restrict__ jobs, uint64_t job_cap,
                               unsigned long long* __restrict__ counts) {
   const int64_t total = int64_t(segs) * sg.M;
   const int lane = threadIdx.x & 31;
-  const uint64_t half = job_cap / 2;
+  const uint64_t quarter = job_cap / 4;
+  const unsigned lt = (1u << lane) - 1u;
   for (int64_t q0 = blockIdx.x * int64_t(blockDim.x); q0 < total; q0 += int64_t(gridDim.x) * blockDim.x) {
     const int64_t q = q0 + threadIdx.x;
     bool emit = false;
@@ -430,26 +431,20 @@ __global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs,
         emit = true;
       }
     }
-    const bool small = emit && n <= uint32_t(kSmallJob), large = emit && !small;
-    const unsigned ms = __ballot_sync(0xffffffffu, small), ml = __ballot_sync(0xffffffffu, large);
-    const unsigned lt = (1u << lane) - 1u;
-    if (ml) {
+    const int cls = !emit ? -1 : (n > 32u ? 0 : (n > 8u ? 1 : (n > 4u ? 2 : 3)));
+    if (emit && cls == 0) atomicMax(&counts[1], (unsigned long long)n);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const bool mine = cls == c;
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (!m) continue;
+      unsigned long long* cnt = &counts[c == 0 ? 0 : c + 1];
       unsigned long long base = 0;
-      if (lane == __ffs(ml) - 1) base = atomicAdd(&counts[0], (unsigned long long)__popc(ml));
-      base = __shfl_sync(0xffffffffu, base, __ffs(ml) - 1);
-      if (large) {
-        const unsigned long long pos = base + __popc(ml & lt);
-        if (pos < half) jobs[pos] = BucketJob{seg, p, n, 0u};
-        atomicMax(&counts[1], (unsigned long long)n);
-      }
-    }
-    if (ms) {
-      unsigned long long base = 0;
-      if (lane == __ffs(ms) - 1) base = atomicAdd(&counts[2], (unsigned long long)__popc(ms));
-      base = __shfl_sync(0xffffffffu, base, __ffs(ms) - 1);
-      if (small) {
-        const unsigned long long pos = base + __popc(ms & lt);
-        if (pos < half) jobs[half + pos] = BucketJob{seg, p, n, 0u};
+      if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (mine) {
+        const unsigned long long pos = base + __popc(m & lt);
+        if (pos < quarter) jobs[c * quarter + pos] = BucketJob{seg, p, n, 0u};
       }
     }
   }
@@ -505,7 +500,7 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
                        : (nd <= 0 ? 0ull : (0x8080808080808080ull & ((1ull << (8 * nd)) - 1)));
   }
   uint64_t njobs = g.counts[0];
-  if (njobs > g.job_cap / 2) njobs = g.job_cap / 2;
+  if (njobs > g.job_cap / 4) njobs = g.job_cap / 4;
   unsigned long long checks = 0;                   // pairs compared by this thread
   for (uint64_t jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
     const BucketJob job = g.jobs[jb];
@@ -624,12 +619,14 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
   if (lane == 0 && checks) atomicAdd(&g.counters[5], checks);
 }
 
-// Warp per small bucket (at most 32 members, one per lane): every pair is
-// compared directly and handled from its lowest colliding dim f.
-template <int NW, int I>
-__global__ void __launch_bounds__(256) k_subwarp(SubArgs g) {
+// W lanes per small bucket (at most W members, one per lane; 32 / W
+// buckets per warp): every pair is compared directly and handled from its
+// lowest colliding dim f.  list = the job list (1..3) of buckets of this size.
+template <int NW, int I, int W>
+__global__ void __launch_bounds__(256) k_subwarp(SubArgs g, int list) {
   constexpr int NQ = I + 1;
-  const int lane = threadIdx.x & 31;
+  constexpr int J = 32 / W;                       // buckets per warp
+  const int lane = threadIdx.x & 31, sub = lane / W, sl = lane % W;
   const int D = g.sg.D;
   const bool lvl_dup = g.K > I;
   uint64_t valid[NW];
@@ -639,32 +636,36 @@ __global__ void __launch_bounds__(256) k_subwarp(SubArgs g) {
     valid[c] = nd >= 8 ? 0x8080808080808080ull
                        : (nd <= 0 ? 0ull : (0x8080808080808080ull & ((1ull << (8 * nd)) - 1)));
   }
-  const uint64_t half = g.job_cap / 2;
-  uint64_t njobs = g.counts[2];
-  if (njobs > half) njobs = half;
+  const uint64_t quarter = g.job_cap / 4;
+  uint64_t njobs = g.counts[list + 1];
+  if (njobs > quarter) njobs = quarter;
+  const BucketJob* jl = g.jobs + uint64_t(list) * quarter;
   const uint64_t nwarps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  const uint64_t wg = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   unsigned long long checks = 0;
-  for (uint64_t jb = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5; jb < njobs; jb += nwarps) {
-    const BucketJob job = g.jobs[half + jb];
-    const int n = int(job.n);
-    const int seg = int(job.seg);
-    const int j = g.sg.j0 + seg / D, f = seg - (seg / D) * D;
-    const uint32_t* O = g.order + g.sg.base(seg) + job.start;
-    const uint64_t* Kj = g.keys + int64_t(j) * g.sg.M * D;
+  for (uint64_t jb0 = wg * J; jb0 < njobs; jb0 += nwarps * J) {   // warp-uniform
+    const uint64_t jb = jb0 + sub;
+    int n = 0, j = 0, f = 0;
     uint32_t wu = 0;
     uint64_t pu[NQ][NW];
-    if (lane < n) {
-      wu = O[lane];
-      const uint64_t* kw = Kj + int64_t(wu) * D;
 #pragma unroll
-      for (int h = 0; h < NQ; ++h)
+    for (int h = 0; h < NQ; ++h)
 #pragma unroll
-        for (int c = 0; c < NW; ++c) pu[h][c] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
-    } else {
+      for (int c = 0; c < NW; ++c) pu[h][c] = 0ull;
+    if (jb < njobs) {
+      const BucketJob job = jl[jb];
+      n = int(job.n);
+      const int seg = int(job.seg);
+      j = g.sg.j0 + seg / D;
+      f = seg - (seg / D) * D;
+      if (sl < n) {
+        wu = g.order[g.sg.base(seg) + job.start + sl];
+        const uint64_t* kw = g.keys + (int64_t(j) * g.sg.M + wu) * D;
 #pragma unroll
-      for (int h = 0; h < NQ; ++h)
+        for (int h = 0; h < NQ; ++h)
 #pragma unroll
-        for (int c = 0; c < NW; ++c) pu[h][c] = 0ull;
+          for (int c = 0; c < NW; ++c) pu[h][c] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
+      }
     }
     // dims below f must not collide: bytes of dims < f
     uint64_t below[NW];
@@ -673,14 +674,17 @@ __global__ void __launch_bounds__(256) k_subwarp(SubArgs g) {
       const int cf = f >> 3, ef = f & 7;
       below[c] = (c < cf ? ~0ull : (c == cf ? ((1ull << (8 * ef)) - 1) : 0ull)) & valid[c];
     }
-    for (int v = 0; v < n - 1; ++v) {
+    int nmax = n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    for (int v = 0; v < nmax - 1; ++v) {
       uint64_t pv[NQ][NW];
 #pragma unroll
       for (int h = 0; h < NQ; ++h)
 #pragma unroll
-        for (int c = 0; c < NW; ++c) pv[h][c] = __shfl_sync(0xffffffffu, pu[h][c], v);
-      const uint32_t wv = __shfl_sync(0xffffffffu, wu, v);
-      bool emit = lane > v && lane < n;
+        for (int c = 0; c < NW; ++c) pv[h][c] = __shfl_sync(0xffffffffu, pu[h][c], v, W);
+      const uint32_t wv = __shfl_sync(0xffffffffu, wu, v, W);
+      bool emit = sl > v && sl < n;
       checks += emit ? 1u : 0u;
       int w0 = 0, w1 = 0;
       bool low = false;
@@ -778,7 +782,9 @@ static cudaError_t run_subbucket(const SubArgs& g, size_t smem, cudaStream_t s) 
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
   MOMENTI_LAUNCH("subbucket", s, k_subbucket<NW, I><<<152 * per_sm, 256, smem, s>>>(g));
-  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I><<<152 * 8, 256, 0, s>>>(g));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 32><<<152 * 8, 256, 0, s>>>(g, 1));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 8><<<152 * 8, 256, 0, s>>>(g, 2));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 4><<<152 * 8, 256, 0, s>>>(g, 3));
   return cudaGetLastError();
 }
 

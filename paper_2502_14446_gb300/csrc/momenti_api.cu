@@ -341,10 +341,10 @@ double predict_exact_ms(const Index& ix, int passes) {
   return double(passes) * (ps_pair * 1e-9 * pairs + 0.2) + 2.0;
 }
 
-// Bucket jobs of one chunk of repetitions (large and small lists, half each)
+// Bucket jobs of one chunk of repetitions (four lists by size, a quarter each)
 uint64_t job_cap_for(int64_t M, int D) {
   uint64_t c = uint64_t(1) << 20;
-  while (c < uint64_t(kChunkReps) * uint64_t(D) * uint64_t(M) && c < (uint64_t(1) << 24)) c <<= 1;
+  while (c < uint64_t(kChunkReps) * uint64_t(D) * uint64_t(M) && c < (uint64_t(1) << 25)) c <<= 1;
   return c;
 }
 
@@ -851,7 +851,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
     if (D <= 16 && p.d >= 2) {
       h->job_cap = job_cap_for(M, D);
       CK(dalloc(h, &h->jobs, size_t(h->job_cap)));
-      CK(dalloc(h, &h->job_counts, 4));
+      CK(dalloc(h, &h->job_counts, 8));
     }
     cs.ev_cap = uint64_t(1) << 22;
     h->ev_budget = std::max<uint64_t>(uint64_t(1) << 28, limit / 8);
@@ -999,13 +999,14 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
       // halve the chunk beyond the event budget
       for (;;) {
         bool sub = false;
-        unsigned long long jc[3] = {0, 0, 0};
+        unsigned long long jc[5] = {0, 0, 0, 0, 0};
         if (i <= 3 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
-          CK(cudaMemsetAsync(h->job_counts, 0, 3 * sizeof(unsigned long long), s));
+          CK(cudaMemsetAsync(h->job_counts, 0, 5 * sizeof(unsigned long long), s));
           CK(launch_bucket_jobs(ix, i, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
           CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
-          sub = jc[0] <= h->job_cap / 2 && jc[2] <= h->job_cap / 2 &&
+          const uint64_t qcap = h->job_cap / 4;
+          sub = jc[0] <= qcap && jc[2] <= qcap && jc[3] <= qcap && jc[4] <= qcap &&
                 jc[1] <= uint64_t(subbucket_cap(ix.D, i));
         }
         CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
