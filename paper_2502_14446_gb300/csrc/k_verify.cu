@@ -399,7 +399,8 @@ __device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t 
 // direct dot product, so it is amortised over many sliding steps (the
 // float32 sliding sums drift by about sqrt(kSeg) roundings between
 // restarts, far inside the 1% + 0.01 filter margin).
-constexpr int kSeg = 512;
+constexpr int kSeg = 2048;
+constexpr int kRowSub = 512;     // row windows staged in shared memory at a time
 constexpr int kDiagBlock = 256; // diagonals per CTA
 
 __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t) {
@@ -611,9 +612,12 @@ k_allpairs_pm(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, 
 }
 
 // Point-major, block-shared rows: all diagonals of a block share the row
-// windows a in [a0, a0 + kSeg), so the row values (centred by the first
-// row window's mean) and their sliding sums are staged once in shared
-// memory; each thread keeps the column sums and the cross product.
+// windows a in [a0, a0 + kSeg).  The rows are staged in shared memory
+// kRowSub at a time (centred by the first row window's mean of the stage,
+// with their sliding sums); each thread keeps the column sums and the
+// cross product of its diagonal and carries them across stages, re-centred
+// on the new row and column means, so a direct restart (w steps) is paid
+// once per kSeg steps.
 template <int DP, bool ROWMIN>
 __global__ void __launch_bounds__(kDiagBlock)
 k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
@@ -626,83 +630,35 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   const bool live = delta < ix.M && a0 < ix.M - delta;
   const int64_t a1 = live ? min(a0 + kSeg, ix.M - delta) : a0;
   const int64_t nrow = min(int64_t(kSeg), ix.M - dlo - a0);     // row windows this block needs
-  const int span = int(nrow) - 1 + w;                           // points of those windows
-  float* rowx = ap_smem;                                        // [span][DP], centred
-  float* sa1 = rowx + (kSeg - 1 + w) * DP;                      // [kSeg][DP]
-  float* sa2 = sa1 + kSeg * DP;
-  float* cav = sa2 + kSeg * DP;                                 // [DP]
+  // rowx[t] = point aS - 1 + t of the stage starting at row aS, centred
+  float* rowx = ap_smem;                                        // [kRowSub + w][DP]
+  float* sa1 = rowx + (kRowSub + w) * DP;                       // [kRowSub][DP] row sums
+  float* sa2 = sa1 + kRowSub * DP;                              // [kRowSub][DP] w^2 var (-1: unreliable)
+  float* cav = sa2 + kRowSub * DP;                              // [2][DP] row centring, by stage parity
+  float* sprev = cav + 2 * DP;                                  // [DP] sum of row window aS - 1
   // per-warp queue of candidate pairs: state (qt, s1b, s2b per dim),
   // row and unsure flag, column window
   constexpr int QS = 3 * DP + 2;
-  float* qall = cav + DP;                                       // [warps][32][QS]
+  float* qall = sprev + DP;                                     // [warps][32][QS]
   uint32_t* qmeta = reinterpret_cast<uint32_t*>(qall + (kDiagBlock / 32) * 32 * QS);
   uint32_t* qcol = qmeta + kDiagBlock;
-  __shared__ int rflag[kSeg];                                   // row window unreliable in some dim
+  __shared__ int rflag[kRowSub];                                // row window unreliable in some dim
   const float* X = ix.xT;
-  if (threadIdx.x < DP) cav[threadIdx.x] = threadIdx.x < D ? ix.mu_hi[int64_t(threadIdx.x) * ix.M + a0] : 0.f;
-  __syncthreads();
-  for (int q = threadIdx.x; q < span * DP; q += blockDim.x) {
-    const int t = q / DP, f = q - t * DP;
-    rowx[q] = f < D ? X[(a0 + t) * DP + f] - cav[f] : 0.f;
-  }
-  __syncthreads();
-  if (threadIdx.x < DP) {                                       // one thread per dim slides the row sums
-    const int f = threadIdx.x;
-    float u1 = 0.f, u2 = 0.f;
-    for (int t = 0; t < w; ++t) {
-      const float v = rowx[t * DP + f];
-      u1 += v;
-      u2 = fmaf(v, v, u2);
-    }
-    // per row window: the sum and w^2 var (-1 when cancellation leaves it
-    // unreliable: a near-flat window, always checked exactly)
-    const float wf = float(w);
-    for (int r = 0; r < nrow; ++r) {
-      if (r > 0) {
-        const float o = rowx[(r - 1) * DP + f], in = rowx[(r - 1 + w) * DP + f];
-        u1 += in - o;
-        u2 = fmaf(in, in, fmaf(-o, o, u2));
-      }
-      const float va = fmaf(wf, u2, -u1 * u1);
-      sa1[r * DP + f] = u1;
-      // padding dims: NaN, so that no test on them passes
-      sa2[r * DP + f] = f >= D ? __int_as_float(0x7fc00000) : (va > 1e-4f * wf * u2 ? va : -1.f);
-    }
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
-    int u = 0;
-    for (int f = 0; f < D; ++f) u |= sa2[r * DP + f] < 0.f;
-    rflag[r] = u;
-  }
-  __syncthreads();
-  // the per-step arithmetic runs on pairs of dims with the packed
-  // two-lane float32 instructions (same rounding as the scalar ones)
   constexpr int DH = DP / 2;
   const float wf = float(w);
   const float2 wf2 = make_float2(wf, wf);
+  const float2* row2 = reinterpret_cast<const float2*>(rowx);
+  const float2* sa1_2 = reinterpret_cast<const float2*>(sa1);
+  const float2* sa2_2 = reinterpret_cast<const float2*>(sa2);
+  // the per-step arithmetic runs on pairs of dims with the packed
+  // two-lane float32 instructions (same rounding as the scalar ones)
   float2 qt[DH], s1b[DH], s2b[DH], ncb[DH];
 #pragma unroll
   for (int p = 0; p < DH; ++p) {
     qt[p] = s1b[p] = s2b[p] = make_float2(0.f, 0.f);
     const int f0 = 2 * p, f1 = 2 * p + 1;
-    ncb[p] = make_float2(f0 < D ? -ix.mu_hi[int64_t(f0) * ix.M + a0 + delta] : 0.f,
-                         f1 < D ? -ix.mu_hi[int64_t(f1) * ix.M + a0 + delta] : 0.f);
-  }
-  const float2* row2 = reinterpret_cast<const float2*>(rowx);
-  const float2* sa1_2 = reinterpret_cast<const float2*>(sa1);
-  const float2* sa2_2 = reinterpret_cast<const float2*>(sa2);
-  for (int t = 0; t < (live ? w : 0); ++t) {
-    float xb[DP];
-    load_row<DP>(X, a0 + delta + t, xb);
-#pragma unroll
-    for (int p = 0; p < DH; ++p) {
-      const float2 u = row2[t * DH + p];
-      const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
-      qt[p] = __ffma2_rn(u, v, qt[p]);
-      s1b[p] = __fadd2_rn(s1b[p], v);
-      s2b[p] = __ffma2_rn(v, v, s2b[p]);
-    }
+    ncb[p] = make_float2(live && f0 < D ? -ix.mu_hi[int64_t(f0) * ix.M + a0 + delta] : 0.f,
+                         live && f1 < D ? -ix.mu_hi[int64_t(f1) * ix.M + a0 + delta] : 0.f);
   }
   // Necessary conditions of dist_d <= thr on the sorted per-dim distances
   // x(1) <= x(2) <= ...: x(1) <= thr / d, x(2) <= thr / (d - 1) and
@@ -720,6 +676,7 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   float* qst = qall + warp * 32 * QS;
   uint32_t* qm = qmeta + warp * 32;
   uint32_t* qc = qcol + warp * 32;
+  int64_t aS = a0;                  // first row of the current stage
   // distances of queued pairs, one per lane (lanes below count)
   auto drain = [&](int count) {
     __syncwarp();
@@ -741,95 +698,176 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
         }
       }
       const float sm = uns ? 0.f : sum_d_smallest<DP>(dist, D, d);
-      if (sm <= thr && sm > rc.lo) record_pair(rc, a0 + r, int64_t(qc[lane]), sm);
+      if (sm <= thr && sm > rc.lo) record_pair(rc, aS + r, int64_t(qc[lane]), sm);
     }
     __syncwarp();
   };
   int qn = 0;                       // queued pairs of this warp (warp-uniform)
-  // every lane runs the block's row count, so that the warp stays converged
-  for (int64_t a = a0; a < a0 + nrow; ++a) {
-    const int r = int(a - a0);
-    const int64_t b = a + delta;
-    const bool act = a < a1;
-    if (act && r > 0) {
-      float ob[DP], ib[DP];
-      load_row<DP>(X, b - 1, ob);
-      load_row<DP>(X, b + w - 1, ib);
-#pragma unroll
-      for (int p = 0; p < DH; ++p) {
-        const float2 uo = row2[(r - 1) * DH + p], ui = row2[(r - 1 + w) * DH + p];
-        const float2 vo = __fadd2_rn(make_float2(ob[2 * p], ob[2 * p + 1]), ncb[p]);
-        const float2 vi = __fadd2_rn(make_float2(ib[2 * p], ib[2 * p + 1]), ncb[p]);
-        qt[p] = __ffma2_rn(ui, vi, __ffma2_rn(make_float2(-uo.x, -uo.y), vo, qt[p]));
-        s1b[p] = __fadd2_rn(s1b[p], __fadd2_rn(vi, make_float2(-vo.x, -vo.y)));
-        s2b[p] = __ffma2_rn(vi, vi, __ffma2_rn(make_float2(-vo.x, -vo.y), vo, s2b[p]));
+  for (int stage = 0; aS < a0 + nrow; ++stage, aS += kRowSub) {
+    const int nsub = int(min(int64_t(kRowSub), a0 + nrow - aS));
+    float* cnew = cav + (stage & 1) * DP;
+    const float* cold = cav + ((stage & 1) ^ 1) * DP;
+    __syncthreads();                // the previous stage is fully consumed
+    if (threadIdx.x < DP) cnew[threadIdx.x] = threadIdx.x < D ? ix.mu_hi[int64_t(threadIdx.x) * ix.M + aS] : 0.f;
+    __syncthreads();
+    for (int q = threadIdx.x; q < (nsub + w) * DP; q += blockDim.x) {
+      const int t = q / DP, f = q - t * DP;
+      const int64_t pt = aS - 1 + t;
+      rowx[q] = (f < D && pt >= 0) ? X[pt * DP + f] - cnew[f] : 0.f;
+    }
+    __syncthreads();
+    if (threadIdx.x < DP) {                                     // one thread per dim slides the row sums
+      const int f = threadIdx.x;
+      float u1 = 0.f, u2 = 0.f;
+      for (int t = 1; t <= w; ++t) {
+        const float v = rowx[t * DP + f];
+        u1 += v;
+        u2 = fmaf(v, v, u2);
+      }
+      sprev[f] = u1 - rowx[w * DP + f] + rowx[f];               // window of row aS - 1
+      // per row window: the sum and w^2 var (-1 when cancellation leaves it
+      // unreliable: a near-flat window, always checked exactly)
+      for (int r = 0; r < nsub; ++r) {
+        if (r > 0) {
+          const float o = rowx[r * DP + f], in = rowx[(r + w) * DP + f];
+          u1 += in - o;
+          u2 = fmaf(in, in, fmaf(-o, o, u2));
+        }
+        const float va = fmaf(wf, u2, -u1 * u1);
+        sa1[r * DP + f] = u1;
+        // padding dims: NaN, so that no test on them passes
+        sa2[r * DP + f] = f >= D ? __int_as_float(0x7fc00000) : (va > 1e-4f * wf * u2 ? va : -1.f);
       }
     }
-    uint32_t cnt = 0;              // tests passed: byte 0 x(1), byte 1 x(2), byte 2 x(d)
-    bool unsure = rflag[r] != 0;
-#pragma unroll
-    for (int p = 0; p < DH; ++p) {
-      const float2 s1a = sa1_2[r * DH + p], VA = sa2_2[r * DH + p];
-      const float2 VB = __ffma2_rn(wf2, s2b[p], __fmul2_rn(make_float2(-s1b[p].x, -s1b[p].y), s1b[p]));
-      const float2 Cv = __ffma2_rn(wf2, qt[p], __fmul2_rn(make_float2(-s1a.x, -s1a.y), s1b[p]));
-      const float2 P = __fmul2_rn(VA, VB);
-      const float2 S = __fmul2_rn(Cv, make_float2(fabsf(Cv.x), fabsf(Cv.y)));
-      const float2 T1 = __fmul2_rn(k1, P), T2 = __fmul2_rn(k2, P), Td = __fmul2_rn(kd, P);
-      const float2 FB = __fmul2_rn(flat, s2b[p]);
-      unsure |= (VB.x < FB.x) | (VB.y < FB.y);
-      cnt += (S.x >= T1.x) + (S.y >= T1.y) + ((S.x >= T2.x) + (S.y >= T2.y)) * 256u +
-             ((S.x >= Td.x) + (S.y >= Td.y)) * 65536u;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nsub; r += blockDim.x) {
+      int u = 0;
+      for (int f = 0; f < D; ++f) u |= sa2[r * DP + f] < 0.f;
+      rflag[r] = u;
     }
-    if (!ROWMIN) {
-      const bool cand = act && (unsure || ((cnt & 255u) >= 1u && ((cnt >> 8) & 255u) >= uint32_t(need2) &&
-                                           (cnt >> 16) >= uint32_t(d)));
-      const unsigned m = __ballot_sync(0xffffffffu, cand);
-      if (!m) continue;
-      const int n = __popc(m);
-      if (qn + n > 32) {
-        drain(qn);
-        qn = 0;
-      }
-      if (cand) {
-        const int pos = qn + __popc(m & ((1u << lane) - 1u));
-        float2* st = reinterpret_cast<float2*>(qst + pos * QS);
+    __syncthreads();
+    if (stage == 0) {
+      // direct start: rows window a0 against column window a0 + delta
+      for (int t = 0; t < (live ? w : 0); ++t) {
+        float xb[DP];
+        load_row<DP>(X, a0 + delta + t, xb);
 #pragma unroll
         for (int p = 0; p < DH; ++p) {
-          st[p] = qt[p];
-          st[DH + p] = s1b[p];
-          st[2 * DH + p] = s2b[p];
+          const float2 u = row2[(t + 1) * DH + p];
+          const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(u, v, qt[p]);
+          s1b[p] = __fadd2_rn(s1b[p], v);
+          s2b[p] = __ffma2_rn(v, v, s2b[p]);
         }
-        qm[pos] = (uint32_t(r) << 1) | (unsure ? 1u : 0u);
-        qc[pos] = uint32_t(b);
       }
-      qn += n;
-      if (qn == 32) {
-        drain(32);
-        qn = 0;
-      }
-      continue;
-    }
-    if (!act) continue;
-    float dist[DP];
+    } else if (aS - 1 < a1) {
+      // the state holds row window aS - 1 and column window aS - 1 + delta:
+      // re-centre the rows on this stage's mean (qt += (c_old - c_new) s1b),
+      // then the columns on that column window's mean (v' = v - dc)
 #pragma unroll
-    for (int f = 0; f < DP; ++f) {
-      dist[f] = INFINITY;
-      if (f < D) {
-        const float qf = (f & 1) ? qt[f >> 1].y : qt[f >> 1].x;
-        const float s1 = (f & 1) ? s1b[f >> 1].y : s1b[f >> 1].x;
-        const float s2 = (f & 1) ? s2b[f >> 1].y : s2b[f >> 1].x;
-        const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
-        const float VB = fmaf(wf, s2, -s1 * s1);
-        const float Cv = fmaf(wf, qf, -s1a * s1);
-        const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
-        dist[f] = sqrtf(fmaxf(sq, 0.f));
+      for (int p = 0; p < DH; ++p) {
+        const int f0 = 2 * p, f1 = 2 * p + 1;
+        const float2 dr = make_float2(cold[f0] - cnew[f0], cold[f1] - cnew[f1]);
+        qt[p] = __ffma2_rn(dr, s1b[p], qt[p]);
+        const float2 cbn = make_float2(f0 < D ? ix.mu_hi[int64_t(f0) * ix.M + aS - 1 + delta] : 0.f,
+                                       f1 < D ? ix.mu_hi[int64_t(f1) * ix.M + aS - 1 + delta] : 0.f);
+        const float2 dc = make_float2(cbn.x + ncb[p].x, cbn.y + ncb[p].y);
+        const float2 sp = make_float2(sprev[f0], sprev[f1]);
+        qt[p] = __ffma2_rn(make_float2(-dc.x, -dc.y), sp, qt[p]);
+        s2b[p] = __ffma2_rn(make_float2(wf * dc.x, wf * dc.y), dc,
+                            __ffma2_rn(make_float2(-2.f * dc.x, -2.f * dc.y), s1b[p], s2b[p]));
+        s1b[p] = __ffma2_rn(make_float2(-wf, -wf), dc, s1b[p]);
+        ncb[p] = make_float2(-cbn.x, -cbn.y);
       }
     }
-    const float sm = sum_d_smallest<DP>(dist, D, d);
-    atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
-    atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+    // every lane runs the stage's row count, so that the warp stays converged
+    for (int r = 0; r < nsub; ++r) {
+      const int64_t a = aS + r;
+      const int64_t b = a + delta;
+      const bool act = a < a1;
+      if (act && (r > 0 || stage > 0)) {
+        float ob[DP], ib[DP];
+        load_row<DP>(X, b - 1, ob);
+        load_row<DP>(X, b + w - 1, ib);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          const float2 uo = row2[r * DH + p], ui = row2[(r + w) * DH + p];
+          const float2 vo = __fadd2_rn(make_float2(ob[2 * p], ob[2 * p + 1]), ncb[p]);
+          const float2 vi = __fadd2_rn(make_float2(ib[2 * p], ib[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(ui, vi, __ffma2_rn(make_float2(-uo.x, -uo.y), vo, qt[p]));
+          s1b[p] = __fadd2_rn(s1b[p], __fadd2_rn(vi, make_float2(-vo.x, -vo.y)));
+          s2b[p] = __ffma2_rn(vi, vi, __ffma2_rn(make_float2(-vo.x, -vo.y), vo, s2b[p]));
+        }
+      }
+      uint32_t cnt = 0;            // tests passed: byte 0 x(1), byte 1 x(2), byte 2 x(d)
+      bool unsure = rflag[r] != 0;
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const float2 s1a = sa1_2[r * DH + p], VA = sa2_2[r * DH + p];
+        const float2 VB = __ffma2_rn(wf2, s2b[p], __fmul2_rn(make_float2(-s1b[p].x, -s1b[p].y), s1b[p]));
+        const float2 Cv = __ffma2_rn(wf2, qt[p], __fmul2_rn(make_float2(-s1a.x, -s1a.y), s1b[p]));
+        const float2 P = __fmul2_rn(VA, VB);
+        const float2 S = __fmul2_rn(Cv, make_float2(fabsf(Cv.x), fabsf(Cv.y)));
+        const float2 T1 = __fmul2_rn(k1, P), T2 = __fmul2_rn(k2, P), Td = __fmul2_rn(kd, P);
+        const float2 FB = __fmul2_rn(flat, s2b[p]);
+        unsure |= (VB.x < FB.x) | (VB.y < FB.y);
+        cnt += (S.x >= T1.x) + (S.y >= T1.y) + ((S.x >= T2.x) + (S.y >= T2.y)) * 256u +
+               ((S.x >= Td.x) + (S.y >= Td.y)) * 65536u;
+      }
+      if (!ROWMIN) {
+        const bool cand = act && (unsure || ((cnt & 255u) >= 1u && ((cnt >> 8) & 255u) >= uint32_t(need2) &&
+                                             (cnt >> 16) >= uint32_t(d)));
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        if (!m) continue;
+        const int n = __popc(m);
+        if (qn + n > 32) {
+          drain(qn);
+          qn = 0;
+        }
+        if (cand) {
+          const int pos = qn + __popc(m & ((1u << lane) - 1u));
+          float2* st = reinterpret_cast<float2*>(qst + pos * QS);
+#pragma unroll
+          for (int p = 0; p < DH; ++p) {
+            st[p] = qt[p];
+            st[DH + p] = s1b[p];
+            st[2 * DH + p] = s2b[p];
+          }
+          qm[pos] = (uint32_t(r) << 1) | (unsure ? 1u : 0u);
+          qc[pos] = uint32_t(b);
+        }
+        qn += n;
+        if (qn == 32) {
+          drain(32);
+          qn = 0;
+        }
+        continue;
+      }
+      if (!act) continue;
+      float dist[DP];
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float qf = (f & 1) ? qt[f >> 1].y : qt[f >> 1].x;
+          const float s1 = (f & 1) ? s1b[f >> 1].y : s1b[f >> 1].x;
+          const float s2 = (f & 1) ? s2b[f >> 1].y : s2b[f >> 1].x;
+          const float s1a = sa1[r * DP + f], VA = sa2[r * DP + f];
+          const float VB = fmaf(wf, s2, -s1 * s1);
+          const float Cv = fmaf(wf, qf, -s1a * s1);
+          const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+          dist[f] = sqrtf(fmaxf(sq, 0.f));
+        }
+      }
+      const float sm = sum_d_smallest<DP>(dist, D, d);
+      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+    }
+    if (!ROWMIN) {                  // queued pairs refer to this stage's rows
+      drain(qn);
+      qn = 0;
+    }
   }
-  if (!ROWMIN) drain(qn);
 }
 
 // Wide series (D > 16): per-window means and 1/sigma are read per step.
@@ -899,10 +937,10 @@ k_allpairs_wide(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   }
 }
 
-// the row kernel stages kSeg-1+w points of every dimension in shared
+// the row kernel stages kRowSub+w points of every dimension in shared
 // memory, the row sums, and a queue of 32 candidate pairs per warp
 size_t rows_smem(int w, int dp) {
-  return (size_t((kSeg - 1 + w) * dp + 2 * kSeg * dp + dp) +
+  return (size_t((kRowSub + w) * dp + 2 * kRowSub * dp + 3 * dp) +
           size_t(kDiagBlock) * (3 * dp + 2) + 2 * size_t(kDiagBlock)) * sizeof(float);
 }
 
