@@ -400,7 +400,7 @@ __device__ __forceinline__ void record_pair(const ApRec& rc, int64_t a, int64_t 
 // float32 sliding sums drift by about sqrt(kSeg) roundings between
 // restarts, far inside the 1% + 0.01 filter margin).
 constexpr int kSeg = 2048;
-constexpr int kRowSub = 512;     // row windows staged in shared memory at a time
+constexpr int kRowSub = 256;     // row windows staged in shared memory at a time
 constexpr int kDiagBlock = 256; // diagonals per CTA
 
 __device__ __forceinline__ float xv(const float* xh, const float* xl, int64_t t) {
@@ -613,13 +613,14 @@ k_allpairs_pm(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, 
 
 // Point-major, block-shared rows: all diagonals of a block share the row
 // windows a in [a0, a0 + kSeg).  The rows are staged in shared memory
-// kRowSub at a time (centred by the first row window's mean of the stage,
+// kRowSub at a time (small stages leave room for three CTAs per SM;
+// centred by the first row window's mean of the stage,
 // with their sliding sums); each thread keeps the column sums and the
 // cross product of its diagonal and carries them across stages, re-centred
 // on the new row and column means, so a direct restart (w steps) is paid
 // once per kSeg steps.
 template <int DP, bool ROWMIN>
-__global__ void __launch_bounds__(kDiagBlock)
+__global__ void __launch_bounds__(kDiagBlock, DP <= 8 ? 3 : 2)
 k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
   extern __shared__ float ap_smem[];
   const int w = ix.w, D = ix.D;
