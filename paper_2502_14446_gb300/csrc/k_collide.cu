@@ -411,42 +411,70 @@ __global__ void __launch_bounds__(128) k_collide(CollideArgs g) {
 __global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs, int i, int d,
                               BucketJob* __restrict__ jobs, uint64_t job_cap,
                               unsigned long long* __restrict__ counts) {
-  const int64_t total = int64_t(segs) * sg.M;
-  const int lane = threadIdx.x & 31;
+  // grid: x over the positions of a segment, y over the segments
+  __shared__ uint32_t wcnt[32][4];
+  __shared__ unsigned long long bbase[4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const uint64_t quarter = job_cap / 4;
   const unsigned lt = (1u << lane) - 1u;
-  for (int64_t q0 = blockIdx.x * int64_t(blockDim.x); q0 < total; q0 += int64_t(gridDim.x) * blockDim.x) {
+  const uint32_t seg = blockIdx.y;
+  const int f = int(seg % uint32_t(sg.D));
+  if (f > sg.D - d) return;                        // block-uniform: f cannot be a lowest dim
+  const uint8_t* L = lcp + sg.base(int(seg));
+  for (int64_t q0 = blockIdx.x * int64_t(blockDim.x); q0 < sg.M; q0 += int64_t(gridDim.x) * blockDim.x) {
     const int64_t q = q0 + threadIdx.x;
     bool emit = false;
-    uint32_t n = 0, seg = 0, p = 0;
-    if (q < total) {
-      seg = uint32_t(q / sg.M);
-      p = uint32_t(q - int64_t(seg) * sg.M);
-      const int f = int(seg % sg.D);
-      const uint8_t* L = lcp + sg.base(int(seg));
-      if (f <= sg.D - d && int(L[p]) < i && int64_t(p) + 1 < sg.M && int(L[p + 1]) >= i) {
+    uint32_t n = 0, p = 0;
+    if (q < sg.M) {
+      p = uint32_t(q);
+      if (int(L[p]) < i && int64_t(p) + 1 < sg.M && int(L[p + 1]) >= i) {
+        // walk to the end of the run, eight prefix lengths at a time where
+        // aligned: every byte of a word is >= i iff byte + 128 - i has its
+        // top bit set (bytes are 0..8, so no carry crosses a byte)
+        const uint64_t add = 0x0101010101010101ull * uint64_t(128 - i);
         int64_t e = p + 1;
-        while (e + 1 < sg.M && int(L[e + 1]) >= i) ++e;
+        while (e + 1 < sg.M) {
+          const int64_t q = e + 1;
+          if ((reinterpret_cast<uintptr_t>(L + q) & 7) == 0 && q + 8 <= sg.M) {
+            const uint64_t w8 = *reinterpret_cast<const uint64_t*>(L + q);
+            if (((w8 + add) & 0x8080808080808080ull) == 0x8080808080808080ull) {
+              e += 8;
+              continue;
+            }
+          }
+          if (int(L[q]) < i) break;
+          ++e;
+        }
         n = uint32_t(e - p + 1);
         emit = true;
       }
     }
     const int cls = !emit ? -1 : (n > 32u ? 0 : (n > 8u ? 1 : (n > 4u ? 2 : 3)));
     if (emit && cls == 0) atomicMax(&counts[1], (unsigned long long)n);
+    // room in the four lists: one global atomic per list and block
+    unsigned m[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const bool mine = cls == c;
-      const unsigned m = __ballot_sync(0xffffffffu, mine);
-      if (!m) continue;
-      unsigned long long* cnt = &counts[c == 0 ? 0 : c + 1];
-      unsigned long long base = 0;
-      if (lane == __ffs(m) - 1) base = atomicAdd(cnt, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-      if (mine) {
-        const unsigned long long pos = base + __popc(m & lt);
-        if (pos < quarter) jobs[c * quarter + pos] = BucketJob{seg, p, n, 0u};
-      }
+      m[c] = __ballot_sync(0xffffffffu, cls == c);
+      if (lane == 0) wcnt[warp][c] = __popc(m[c]);
     }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      const int c = threadIdx.x;
+      uint32_t run = 0;
+      for (int ww = 0; ww < nwarp; ++ww) {
+        const uint32_t x = wcnt[ww][c];
+        wcnt[ww][c] = run;
+        run += x;
+      }
+      bbase[c] = run ? atomicAdd(&counts[c == 0 ? 0 : c + 1], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    if (cls >= 0) {
+      const unsigned long long pos = bbase[cls] + wcnt[warp][cls] + __popc(m[cls] & lt);
+      if (pos < quarter) jobs[cls * quarter + pos] = BucketJob{seg, p, n, 0u};
+    }
+    __syncthreads();                               // wcnt / bbase reused by the next round
   }
 }
 
@@ -756,10 +784,11 @@ cudaError_t launch_bucket_jobs(const Index& ix, int i, int j0, int j1, int d, Bu
                                uint64_t job_cap, unsigned long long* counts, cudaStream_t s) {
   const int segs = (j1 - j0) * ix.D;
   Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
-  const int64_t total = int64_t(segs) * ix.M;
-  int64_t g = (total + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<unsigned(g), 256, 0, s>>>(ix.lcp, sg, segs, i, d, jobs, job_cap, counts));
+  int64_t gx = (ix.M + 255) / 256;
+  const int64_t per_seg = std::max<int64_t>(1, (152 * 16 + segs - 1) / segs);
+  if (gx > per_seg) gx = per_seg;
+  dim3 grid{unsigned(gx), unsigned(segs), 1u};
+  MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<grid, 256, 0, s>>>(ix.lcp, sg, segs, i, d, jobs, job_cap, counts));
   return cudaGetLastError();
 }
 
