@@ -437,7 +437,11 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": "plain_fp32 prefix sample (see cpu_baseline.sample)"},
+           "config": {"workload": f"plain_fp32: D=8 n={wl.n} w=300 d=3 k=10 delta=0.05 "
+                                   "float32, 8 GB limit, K=8 L=200, r auto",
+                      "sample": "each step times the oracle on a bounded prefix (cpu_baseline.sample) "
+                                "and reports its throughput",
+                      "parallelism": f"replicas x{world}"},
            "cpu_baseline": {"value": value, "unit": "subsequences/s", "cores": os.cpu_count(),
                             "kind": "oracle", "sample": base["sample"]},
            "e2e": {"value": value, "unit": "subsequences/s", "h2d_bytes_per_step": 0,

@@ -493,11 +493,23 @@ struct SubArgs {
   uint64_t job_cap;
 };
 
-// Byte plane q of dims 8c .. 8c+7 of a window's keys (byte e = dim 8c + e).
-__device__ __forceinline__ uint64_t key_plane(const uint64_t* kw, int c, int q, int D) {
-  uint64_t a = 0;
-  for (int e = 0; e < 8 && 8 * c + e < D; ++e) a |= ((kw[8 * c + e] >> (56 - 8 * q)) & 0xFFull) << (8 * e);
-  return a;
+// Byte planes 0..NQ-1 of a window's D keys (plane h, word c: byte e =
+// hash value h of dim 8c + e), each key loaded once.
+template <int NQ, int NW>
+__device__ __forceinline__ void key_planes(const uint64_t* kw, int D, int K, uint64_t (&pl)[NQ][NW]) {
+#pragma unroll
+  for (int c = 0; c < NW; ++c) {
+    uint64_t key[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) key[e] = 8 * c + e < D ? kw[8 * c + e] : 0ull;
+#pragma unroll
+    for (int h = 0; h < NQ; ++h) {
+      uint64_t a = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a |= ((key[e] >> (56 - 8 * h)) & 0xFFull) << (8 * e);
+      pl[h][c] = h < K ? a : 0ull;
+    }
+  }
 }
 
 // CTA per large bucket of prefix length I (the first I hash values equal
@@ -542,11 +554,12 @@ __global__ void __launch_bounds__(256) k_subbucket(SubArgs g) {
     for (int q = tid; q < n; q += blockDim.x) {
       const uint32_t wv = O[q];
       widx[q] = wv;
-      const uint64_t* kw = Kj + int64_t(wv) * D;
+      uint64_t kp[NQ][NW];
+      key_planes<NQ, NW>(Kj + int64_t(wv) * D, D, g.K, kp);
 #pragma unroll
       for (int h = 0; h < NQ; ++h)
 #pragma unroll
-        for (int c = 0; c < NW; ++c) pl[(h * NW + c) * cap + q] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
+        for (int c = 0; c < NW; ++c) pl[(h * NW + c) * cap + q] = kp[h][c];
     }
     __syncthreads();
     // second-lowest colliding dim f2 leaves d - 2 dims above it
@@ -688,11 +701,7 @@ __global__ void __launch_bounds__(256) k_subwarp(SubArgs g, int list) {
       f = seg - (seg / D) * D;
       if (sl < n) {
         wu = g.order[g.sg.base(seg) + job.start + sl];
-        const uint64_t* kw = g.keys + (int64_t(j) * g.sg.M + wu) * D;
-#pragma unroll
-        for (int h = 0; h < NQ; ++h)
-#pragma unroll
-          for (int c = 0; c < NW; ++c) pu[h][c] = (h < g.K) ? key_plane(kw, c, h, D) : 0ull;
+        key_planes<NQ, NW>(g.keys + (int64_t(j) * g.sg.M + wu) * D, D, g.K, pu);
       }
     }
     // dims below f must not collide: bytes of dims < f
