@@ -273,6 +273,15 @@ void trim_pool() {
   if (cudaMemPool_t pool = lib_pool()) cudaMemPoolTrimTo(pool, 0);
 }
 
+// Transient stream-ordered allocation from the library pool (memory the
+// pool keeps is reused by the next call instead of being mapped again).
+template <typename T>
+cudaError_t pool_malloc(T** ptr, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return cudaErrorInitializationError;
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(ptr), std::max<size_t>(bytes, 16), pool, s);
+}
+
 template <typename T>
 cudaError_t dalloc(momenti_handle* h, T** ptr, size_t count) {
   size_t bytes = std::max<size_t>(count * sizeof(T), 16);
@@ -398,10 +407,10 @@ int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out,
     uint64_t* dp = nullptr;
     double *dpd = nullptr, *ddd = nullptr;
     uint64_t* dmask = nullptr;
-    CK(cudaMallocAsync(&dp, m * 8, h->stream));
-    CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
-    CK(cudaMallocAsync(&ddd, m * 8, h->stream));
-    CK(cudaMallocAsync(&dmask, m * 8, h->stream));
+    CK(pool_malloc(&dp, m * 8, h->stream));
+    CK(pool_malloc(&dpd, m * ix.D * 8, h->stream));
+    CK(pool_malloc(&ddd, m * 8, h->stream));
+    CK(pool_malloc(&dmask, m * 8, h->stream));
     CK(cudaMemcpyAsync(dp, pk.data(), m * 8, cudaMemcpyHostToDevice, h->stream));
     CK(launch_verify_pairs(ix, h->p.d, dp, m, 1, dpd, ddd, dmask, h->stream));
     std::vector<double> per(m * ix.D), dd(m);
@@ -449,7 +458,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
   double tau = tau0;
   if (!(tau > 0)) {
     float* rowmin = nullptr;
-    CK(cudaMallocAsync(&rowmin, ix.M * 4, h->stream));
+    CK(pool_malloc(&rowmin, ix.M * 4, h->stream));
     CK(cudaMemsetAsync(rowmin, 0x7f, ix.M * 4, h->stream));
     CK(launch_allpairs_rowmin(ix, h->p.d, rowmin, h->stream));
     std::vector<float> rm(ix.M);
@@ -495,9 +504,9 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     if (m <= 0) return MOMENTI_OK;
     double *dpd = nullptr, *ddd = nullptr;
     uint64_t* dmask = nullptr;
-    CK(cudaMallocAsync(&dpd, m * ix.D * 8, h->stream));
-    CK(cudaMallocAsync(&ddd, m * 8, h->stream));
-    CK(cudaMallocAsync(&dmask, m * 8, h->stream));
+    CK(pool_malloc(&dpd, m * ix.D * 8, h->stream));
+    CK(pool_malloc(&ddd, m * 8, h->stream));
+    CK(pool_malloc(&dmask, m * 8, h->stream));
     CK(launch_verify_pairs(ix, h->p.d, dpairs, m, 0, dpd, ddd, dmask, h->stream));
     std::vector<uint64_t> pk(m), mk(m);
     std::vector<double> per(m * ix.D), dd(m);
@@ -549,14 +558,14 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     dval = nullptr;
     dsel = nullptr;
   };
-  CK(cudaMallocAsync(&dcnt, 8, h->stream));
-  CK(cudaMallocAsync(&dhist, kApBins * 4, h->stream));
+  CK(pool_malloc(&dcnt, 8, h->stream));
+  CK(pool_malloc(&dhist, kApBins * 4, h->stream));
   std::vector<uint32_t> hist(kApBins);
   int rc = MOMENTI_ERR_OVERFLOW;
   for (int pass = 0; pass < 64; ++pass) {
     if (!dout) {
-      CK(cudaMallocAsync(&dout, cap * 8, h->stream));
-      CK(cudaMallocAsync(&dval, cap * 4, h->stream));
+      CK(pool_malloc(&dout, cap * 8, h->stream));
+      CK(pool_malloc(&dval, cap * 4, h->stream));
     }
     CK(cudaMemsetAsync(dcnt, 0, 8, h->stream));
     CK(cudaMemsetAsync(dhist, 0, kApBins * 4, h->stream));
@@ -597,7 +606,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
       continue;
     }
     // ascending batches of whole bins
-    CK(cudaMallocAsync(&dsel, std::max<uint64_t>(cnt, 1) * 8, h->stream));
+    CK(pool_malloc(&dsel, std::max<uint64_t>(cnt, 1) * 8, h->stream));
     bool done = false;
     for (int b0 = 0; b0 < kApBins && !done;) {
       int b1 = b0;
@@ -878,7 +887,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
   const void* src = series;
   void* staging = nullptr;
   if (!on_device) {
-    CK(cudaMallocAsync(&staging, size_t(D) * n * elem, s));
+    CK(pool_malloc(&staging, size_t(D) * n * elem, s));
     CK(cudaMemcpy2DAsync(staging, n * elem, series, ld * elem, n * elem, D, cudaMemcpyHostToDevice, s));
     src = staging;
     ld = n;
@@ -1259,10 +1268,10 @@ int momenti_verify(momenti_handle* h, const int64_t* pairs, int64_t m, double* p
   uint64_t* dp = nullptr;
   double *dpd = nullptr, *ddd = nullptr;
   uint64_t* dmask = nullptr;
-  CK(cudaMallocAsync(&dp, m * 8, s));
-  CK(cudaMallocAsync(&dpd, m * ix.D * 8, s));
-  CK(cudaMallocAsync(&ddd, m * 8, s));
-  CK(cudaMallocAsync(&dmask, m * 8, s));
+  CK(pool_malloc(&dp, m * 8, s));
+  CK(pool_malloc(&dpd, m * ix.D * 8, s));
+  CK(pool_malloc(&ddd, m * 8, s));
+  CK(pool_malloc(&dmask, m * 8, s));
   CK(cudaMemcpyAsync(dp, pk.data(), m * 8, cudaMemcpyHostToDevice, s));
   CK(launch_verify_pairs(ix, h->p.d, dp, m, fp64, dpd, ddd, dmask, s));
   if (per_dim) CK(cudaMemcpyAsync(per_dim, dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, s));
@@ -1328,7 +1337,7 @@ int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int
   cudaStream_t s = h->stream;
   uint64_t* dout = nullptr;
   const uint64_t dcap = uint64_t(std::max<int64_t>(cap, 1));
-  CK(cudaMallocAsync(&dout, dcap * 8, s));
+  CK(pool_malloc(&dout, dcap * 8, s));
   CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
   CK(launch_collide(h->ix, i, j, j + 1, h->p.d, h->hs, h->cs, 1, dout, uint64_t(cap), s));
   unsigned long long c = 0;
