@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 # file is unchanged (the capture and its command are summarised in profiles/)
 NCU_TRAFFIC = {
     "allpairs": ("paper_2502_14446_gb300/csrc/k_verify.cu",
-                 "fd9ae94f67804e251fe0d986956cd57ab3acdcd7a7d8e87220193b34dc532ccb", 6629376),
+                 "b28c6ae0e63429c304d36f8ac08eae9bd737547e7e05ba9ad24cf5e472796393", 6761472),
 }
 
 
