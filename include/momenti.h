@@ -81,8 +81,8 @@ typedef struct momenti_params {
   uint32_t reserved;
 } momenti_params;
 
-/* flags: count collisions at prefix length 1 with the pair tiles instead of
- * splitting buckets by a second dimension (same candidates; for tests). */
+/* flags: count collisions at every prefix length with the pair tiles instead
+ * of the bucket jobs of prefix lengths 1..3 (same candidates; for tests). */
 #define MOMENTI_FLAG_TILES_ONLY 1u
 /* flags: follow Algorithm 1's loop to its end before the exact path (no
  * cost switch).  By default each level starts with a one-repetition probe

@@ -132,7 +132,6 @@ struct Pool {
 
   double kth() const { return int(top.size()) == k ? top.back().dd : INFINITY; }
   bool valid() const { return int(top.size()) == k && top.back().dd < tau_trunc; }
-  size_t size() const { return items.size(); }
 
   void sort_all() {
     if (sorted < items.size()) {
