@@ -536,7 +536,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
   };
   // no pair has an approximate distance above this
   const float all_edge = float(2.0 * std::sqrt(double(ix.w)) * h->p.d * 1.01 + 0.02);
-  constexpr int64_t kBatch = int64_t(1) << 16;
+  constexpr int64_t kBatch = int64_t(1) << 13;   // pairs verified per batch (smallest first)
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   const uint64_t cap_max = std::max<uint64_t>(uint64_t(1) << 22,
