@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -231,8 +232,25 @@ struct momenti_handle {
 
 namespace {
 
-int fail(momenti_handle* h, int code, const std::string& msg) {
-  if (h) h->err = msg;
+// Records the message of a failing call (never throws: a message that
+// cannot be stored is dropped, the code still reports the failure).
+int fail(momenti_handle* h, int code, const char* msg) noexcept {
+  if (h) {
+    try {
+      h->err = msg;
+    } catch (...) {
+    }
+  }
+  return code;
+}
+
+int fail(momenti_handle* h, int code, const std::string& msg) noexcept {
+  if (h) {
+    try {
+      h->err = msg;
+    } catch (...) {
+    }
+  }
   return code;
 }
 
@@ -662,7 +680,7 @@ int momenti_default_params(momenti_params* p) {
   return MOMENTI_OK;
 }
 
-int momenti_create(momenti_handle** out, const momenti_params* p) {
+static int create_impl(momenti_handle** out, const momenti_params* p) {
   if (!out || !p) return MOMENTI_ERR_ARG;
   *out = nullptr;
   if (p->w < 2 || p->d < 1 || p->k < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->K < 1 ||
@@ -689,7 +707,7 @@ const char* momenti_last_error(const momenti_handle* h) {
   return h->err.c_str();
 }
 
-int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
+static int set_hash_params_impl(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
                             const float* a, const float* u) {
   if (!h) return MOMENTI_ERR_ARG;
   if (!a || !u || D < 1 || D > MOMENTI_MAX_D || L < 1 || K != h->p.K || w != h->p.w)
@@ -706,7 +724,7 @@ int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, 
   return MOMENTI_OK;
 }
 
-int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n, int32_t D,
+static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, int64_t n, int32_t D,
                      int64_t ld, int32_t on_device, void* stream) {
   if (!h) return MOMENTI_ERR_ARG;
   const auto& p = h->p;
@@ -959,7 +977,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
   return MOMENTI_OK;
 }
 
-int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
+static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
   if (!h) return MOMENTI_ERR_ARG;
   if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
   if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk before hash_all");
@@ -1171,7 +1189,7 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
   return MOMENTI_OK;
 }
 
-int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
+static int topk_exact_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
   if (!h) return MOMENTI_ERR_ARG;
   if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk_exact: NULL output");
   if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk_exact before hash_all");
@@ -1179,7 +1197,7 @@ int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
   return exact_path(h, 0.0, out, n_out, &err);
 }
 
-int momenti_topk_batch(int32_t B, const momenti_params* params, const void* const* series,
+static int topk_batch_impl(int32_t B, const momenti_params* params, const void* const* series,
                        const int32_t* dtype, const int64_t* n, const int32_t* D, int32_t on_device,
                        int32_t threads, momenti_motif* out, int32_t out_stride, int32_t* n_out,
                        momenti_stats* stats, int32_t* rc, char* err, int32_t err_len) {
@@ -1203,12 +1221,14 @@ int momenti_topk_batch(int32_t B, const momenti_params* params, const void* cons
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MOMENTI_ERR_CUDA;
   const uint64_t share = uint64_t(0.8 * double(free_b) / T);
-  std::vector<int> status(size_t(B), MOMENTI_OK);
+  // a series nobody finished (a worker that could not start) reports an error
+  std::vector<int> status(size_t(B), MOMENTI_ERR_CUDA);
   std::vector<std::string> messages(static_cast<size_t>(B));
   std::atomic<int32_t> next{0};
   auto worker = [&]() {
     cudaSetDevice(dev);
-    momenti_handle* h = new momenti_handle();
+    momenti_handle* h = new (std::nothrow) momenti_handle();
+    if (!h) return;
     bool stream_ok = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) == cudaSuccess;
     for (;;) {
       const int32_t q = next.fetch_add(1);
@@ -1218,7 +1238,7 @@ int momenti_topk_batch(int32_t B, const momenti_params* params, const void* cons
       n_out[b] = 0;
       momenti_handle* probe = nullptr;
       if (!stream_ok) {
-        h->err = "topk_batch: cannot create a stream";
+        fail(h, MOMENTI_ERR_CUDA, "topk_batch: cannot create a stream");
       } else if ((r = momenti_create(&probe, &params[b])) == MOMENTI_OK) {
         momenti_destroy(probe);
         h->p = params[b];
@@ -1227,15 +1247,26 @@ int momenti_topk_batch(int32_t B, const momenti_params* params, const void* cons
         if (r == MOMENTI_OK)
           r = momenti_topk(h, out + int64_t(b) * out_stride, n_out + b, stats ? stats + b : nullptr);
       } else {
-        h->err = "topk_batch: invalid parameters";
+        fail(h, r, "topk_batch: invalid parameters");
       }
       status[size_t(b)] = r;
-      if (r != MOMENTI_OK) messages[size_t(b)] = h->err;
+      if (r != MOMENTI_OK) {
+        try {
+          messages[size_t(b)] = h->err;
+        } catch (...) {                 // the status alone still reports the failure
+        }
+      }
     }
     momenti_destroy(h);
   };
   std::vector<std::thread> pool;
-  for (int t = 1; t < T; ++t) pool.emplace_back(worker);
+  for (int t = 1; t < T; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {
+      break;                        // fewer workers: the others take the rest
+    }
+  }
   worker();
   for (auto& th : pool) th.join();
   int first = MOMENTI_OK;
@@ -1355,4 +1386,71 @@ int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int
   return MOMENTI_OK;
 }
 
+
+// ---- entry points: no C++ exception crosses the ABI ----
+
+int momenti_create(momenti_handle** out, const momenti_params* p) {
+  try {
+    return create_impl(out, p);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(nullptr, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
+                            const float* a, const float* u) {
+  try {
+    return set_hash_params_impl(h, D, L, K, w, a, u);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n, int32_t D,
+                     int64_t ld, int32_t on_device, void* stream) {
+  try {
+    return hash_all_impl(h, series, dtype, n, D, ld, on_device, stream);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
+  try {
+    return topk_impl(h, out, n_out, stats);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
+  try {
+    return topk_exact_impl(h, out, n_out);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_topk_batch(int32_t B, const momenti_params* params, const void* const* series,
+                       const int32_t* dtype, const int64_t* n, const int32_t* D, int32_t on_device,
+                       int32_t threads, momenti_motif* out, int32_t out_stride, int32_t* n_out,
+                       momenti_stats* stats, int32_t* rc, char* err, int32_t err_len) {
+  try {
+    return topk_batch_impl(B, params, series, dtype, n, D, on_device, threads, out, out_stride, n_out, stats, rc, err, err_len);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(nullptr, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
 }  // extern "C"
