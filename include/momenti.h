@@ -15,7 +15,8 @@
  *
  * Conventions for every entry point:
  *   - return value: MOMENTI_OK (0) or a negative MOMENTI_ERR_* code; no C++
- *     exception crosses the ABI; momenti_last_error() gives a message;
+ *     exception crosses the ABI (host memory exhaustion is reported as
+ *     MOMENTI_ERR_MEMORY); momenti_last_error() gives a message;
  *   - pointers are host pointers unless a parameter says otherwise; the
  *     caller owns every buffer it passes and the handle owns everything it
  *     allocates (released by momenti_destroy);
@@ -26,7 +27,8 @@
  *     must stay valid until the next momenti_hash_all or momenti_destroy
  *     (device buffers are released on it);
  *   - device memory comes from a stream-ordered pool of the library, one per
- *     device, trimmed by momenti_destroy and at the end of a batch.
+ *     device, trimmed by momenti_destroy (the batching form's worker
+ *     handles are destroyed, so the pool is trimmed when a batch ends).
  */
 #ifndef MOMENTI_H
 #define MOMENTI_H
@@ -185,8 +187,11 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
 /* Algorithm 1, lines 3-20 with Algorithm 2: traverses prefixes i = K..1 and
  * repetitions j = 1..L, counts per pair the dimensions sharing the length-i
  * prefix (W), verifies pairs with W >= d, keeps TOP and stops when STOP
- * holds; otherwise returns the exact top-k over all pairs.  Distances of
- * the result are re-verified in float64.
+ * holds; otherwise returns the exact top-k over all pairs — after the
+ * whole loop, or (by default) as soon as the work model predicts the rest
+ * of the traversal to cost more than the exact path (MOMENTI_FLAG_NO_COST_
+ * SWITCH; stats->switch_level).  Distances of the result are re-verified
+ * in float64.
  *   out   : room for k motifs, sorted by (dist_d, a, b);
  *   n_out : number written (k unless fewer than k non-trivial pairs exist);
  *   stats : optional counters (may be NULL).
