@@ -35,7 +35,7 @@
 
 using namespace momenti;
 
-constexpr int kChunkReps = 32;   // repetitions per device round trip of the traversal
+constexpr int kChunkReps = 64;   // repetitions per device round trip of the traversal
 
 namespace {
 
