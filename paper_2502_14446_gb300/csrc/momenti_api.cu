@@ -769,10 +769,10 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                              + uint64_t(D) * M * kRepStride * 8 / 100;       // rehash flags
     const int L_cap = p.L > 0 ? p.L : 4096;
     const int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
-    // sort scratch: a batch of repetitions whose ping-pong buffers hold about 320 MB
+    // sort scratch: a batch of repetitions whose ping-pong buffers hold about 640 MB
     // (fewer, fuller launches; measured faster than batches that stay in L2)
     const uint64_t seg_bytes = uint64_t(M) * (8 + 8 + 4 + 4);
-    int sort_reps = int(std::max<uint64_t>(1, (uint64_t(320) << 20) / (seg_bytes * D)));
+    int sort_reps = int(std::max<uint64_t>(1, (uint64_t(640) << 20) / (seg_bytes * D)));
     // traversal scratch
     const int64_t C = (M + 31) / 32;
     int chunk = std::min(kChunkReps, L_user);
