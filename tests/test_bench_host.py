@@ -1,0 +1,52 @@
+"""Host-side pieces of bench.py: the roofline object's arithmetic, the
+measured-traffic lookup (reported only while the kernel source is the one
+the ncu capture was taken from) and the timing defaults."""
+import hashlib
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _Wl:
+    w = 300
+
+
+def test_timing_defaults(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.warmup >= 3 and a.steps >= 1 and a.impl == "momenti"
+
+
+def test_measured_traffic_follows_the_source():
+    for kernel, (path, sha, nbytes) in bench.NCU_TRAFFIC.items():
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            same = hashlib.sha256(fh.read()).hexdigest() == sha
+        assert bench.measured_traffic(kernel) == (nbytes if same else None)
+    assert bench.measured_traffic("no_such_kernel") is None
+
+
+def test_roofline_arithmetic():
+    pk = {"hbm_gbs": 6779.0, "tflops": 1933.3, "tflops_sustained": 1727.1,
+          "sm_max_mhz": 2070.0, "src": "measured"}
+    info = {"M": 99701, "D": 8, "L": 200, "K": 8}
+    st = {"n_candidates": 1000}
+    steps, ms = 5, 5 * 44.0
+    r = bench.roofline("allpairs", ms, steps, info, st, _Wl, steps, pk)
+    excl = _Wl.w // 2
+    pairs = (info["M"] - excl - 1) * (info["M"] - excl) / 2.0
+    work = 18.0 * info["D"] * pairs
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(work * steps / (ms / 1e3) / 1e12)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2070.0 * 1e6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["ms_per_launch"] == pytest.approx(44.0)
+    t = bench.roofline("proj_hash_tc", 5 * 2.9, steps, info, st, _Wl, steps, pk)
+    assert t["bound"] == "tensor" and t["peak"] == pk["tflops_sustained"]
+    assert t["achieved"] == pytest.approx(2.0 * 99701 * 8 * 200 * 8 * 300 / 2.9e-3 / 1e12)
+    assert bench.roofline("allpairs", 0.0, 0, info, st, _Wl, steps, pk) is None
