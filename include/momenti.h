@@ -167,7 +167,7 @@ const char* momenti_last_error(const momenti_handle* h);
 int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
                             const float* a, const float* u);
 
-/* Algorithm 1, line 2 and the index of Section 4 ("Index construction"):
+/* The hashing step of Algorithm 1 and the index of Section 4 ("Index construction"):
  * rolling mean / std of every window (population sigma, float64 running
  * sums), r by the heuristic of Section 6.1 unless fixed, the composite hash
  * h_{K,j}^f of every window, dimension and repetition, and for every (j, f)
@@ -184,7 +184,7 @@ int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, 
 int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n,
                      int32_t D, int64_t ld, int32_t on_device, void* stream);
 
-/* Algorithm 1, lines 3-20 with Algorithm 2: traverses prefixes i = K..1 and
+/* Algorithm 1 after hashing, with Algorithm 2: traverses prefixes i = K..1 and
  * repetitions j = 1..L, counts per pair the dimensions sharing the length-i
  * prefix (W), verifies pairs with W >= d, keeps TOP and stops when STOP
  * holds; otherwise returns the exact top-k over all pairs — after the
@@ -198,7 +198,7 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
  * MOMENTI_ERR_STATE before momenti_hash_all. */
 int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats);
 
-/* Algorithm 1, line 20 alone: the exact top-k over all pairs (the quantity
+/* The final fallback of Algorithm 1 alone: the exact top-k over all pairs (the quantity
  * of Definition top-k), on the GPU, float64 re-verified.  Same outputs and
  * errors as momenti_topk. */
 int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out);
@@ -259,7 +259,7 @@ int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys);
  * index), lcp[p] = hash values shared with rank p - 1 (lcp[0] = 0). */
 int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, uint8_t* lcp);
 
-/* Algorithm 1, lines 6-14 for one (i, j), 1-based i and 0-based j: the
+/* The collision count of Algorithm 1 for one (i, j), 1-based i and 0-based j: the
  * non-trivial pairs (a < b) with W >= d at prefix length i in repetition j,
  * each once, without the cross-level and cross-repetition de-duplication
  * of the traversal.  pairs: room for 2*cap int64; *count = total found

@@ -426,7 +426,7 @@ def build_index(keys: np.ndarray):
 # ---------------------------------------------------------------------------
 
 def colliding_pairs(keys_jf: np.ndarray, i: int) -> np.ndarray:
-    """Algorithm 1, line 8: all pairs (a < b) whose hash strings share the
+    """Collision step of Algorithm 1: all pairs (a < b) whose hash strings share the
     prefix of length i, for one (j, f).  Returns codes a * M + b (int64)."""
     M = keys_jf.size
     pre = prefix(keys_jf, i)
@@ -474,7 +474,7 @@ class _Pool:
 
 def momenti_traverse(keys: np.ndarray, pair_distances, d: int, k: int, delta: float,
                      r: float, eps: int, K: int | None = None):
-    """Algorithm 1, lines 3-19, over given composite hash keys
+    """The prefix traversal of Algorithm 1 over given composite hash keys
     (uint64, shape (L, M, D)): for i = K..1, for j = 1..L, W(a, b) counts the
     dimensions in which a and b share the length-i prefix; every pair with
     W >= d that is not a trivial match is verified with
@@ -511,9 +511,9 @@ def momenti(T: np.ndarray, w: int, d: int, k: int, delta: float, A: np.ndarray,
             U: np.ndarray, r: float, excl: int | None = None, all_k: bool = False,
             fallback_tau: float | None = None):
     """Algorithm 1 (MOMENTI) with Algorithm 2 (STOP), in the paper's order:
-    hash every window, dimension and repetition (line 2), traverse the
-    prefixes (lines 3-19, ``momenti_traverse``) and, if STOP never holds,
-    return the exact top-k over all pairs (line 20).
+    hash every window, dimension and repetition, traverse the prefixes
+    (``momenti_traverse``) and, if STOP never holds, return the exact top-k
+    over all pairs (the algorithm's final fallback).
 
     ``all_k`` uses delta / k (Lemma topkdip).  A has shape (D, L, K, w),
     U (D, L, K).  Returns a dict with the motifs [(dist_d, a, b, dims,

@@ -134,7 +134,7 @@ struct HashSet {
   uint64_t* keys = nullptr;   // a << 32 | b, EMPTY = ~0ull
   uint64_t cap = 0;           // power of two
 };
-// A candidate of Algorithm 1, line 14: pair (a < b) with W >= d in repetition j.
+// A candidate of Algorithm 1: pair (a < b) with W >= d in repetition j.
 struct Event {
   uint32_t a, b;
   int32_t j;

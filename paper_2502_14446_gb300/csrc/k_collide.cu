@@ -1,4 +1,4 @@
-// Index traversal of Algorithm 1 (lines 6-14) on the sorted index: at
+// Index traversal of Algorithm 1 (the collision count W per pair) on the sorted index: at
 // prefix length i, in repetition j, every pair of windows sharing the
 // length-i prefix in some dimension is a collision; W(a, b) is the number
 // of dimensions in which they collide, and pairs with W >= d become

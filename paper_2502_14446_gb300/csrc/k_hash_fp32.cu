@@ -1,4 +1,4 @@
-// Plain FP32 form of the projections and hashes of Algorithm 1, line 2:
+// Plain FP32 form of the projections and hashes of Algorithm 1 (its hashing step):
 // h_{K,j}^f(T_a) = floor((a . z_a + b) / r) (Eq. drp) for every window a,
 // dimension f and repetition j, packed into one 64-bit key per (j, a, f).
 //

@@ -1,4 +1,4 @@
-// Tensor-core form of the projections and hashes of Algorithm 1, line 2
+// Tensor-core form of the projections and hashes of Algorithm 1 (its hashing step)
 // (Eq. drp on z-normalised windows), for sm_103a: tcgen05.mma with TMEM
 // accumulators, projection vectors staged by TMA.
 //

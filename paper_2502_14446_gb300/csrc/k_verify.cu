@@ -1,5 +1,5 @@
-// Candidate verification (Algorithm 1, line 15) and the exact all-pairs
-// path (Algorithm 1, line 20).
+// Candidate verification (the distance check of Algorithm 1's inner loop)
+// and the exact all-pairs path (the final fallback of Algorithm 1).
 //
 // Per pair: the z-normalised Euclidean distance of Eq. (zned) in every
 // dimension, computed directly from the centred windows,
@@ -662,15 +662,19 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
                          live && f1 < D ? -ix.mu_hi[int64_t(f1) * ix.M + a0 + delta] : 0.f);
   }
   // Necessary conditions of dist_d <= thr on the sorted per-dim distances
-  // x(1) <= x(2) <= ...: x(1) <= thr / d and x(d) <= thr (the middle ones,
-  // x(i) <= thr / (d - i + 1), reject few more pairs than they cost).
-  // dist_f <= t  <=>  corr >= c = 1 - t^2 / 2w  <=>  C >= c sqrt(VA VB)
+  // x(1) <= x(2) <= ...: x(1) <= thr / d and x(d) <= thr; with more than 8
+  // dims (where d reaches 3..6) also x(2) <= thr / (d - 1).  The other
+  // middle ones, x(i) <= thr / (d - i + 1), reject few more pairs than they
+  // cost.  dist_f <= t  <=>  corr >= c = 1 - t^2 / 2w  <=>  C >= c sqrt(VA VB)
   // <=>  C |C| >= c |c| VA VB (x -> x |x| is monotone).
-  const float t1 = thr / float(d);
-  const float c1 = 1.f - t1 * t1 / (2.f * wf);
+  constexpr bool kMid = DP >= 16;
+  const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
+  const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
   const float cd = 1.f - thr * thr / (2.f * wf);
   const float2 k1 = make_float2(c1 * fabsf(c1), c1 * fabsf(c1));
+  const float2 k2 = make_float2(c2 * fabsf(c2), c2 * fabsf(c2));
   const float2 kd = make_float2(cd * fabsf(cd), cd * fabsf(cd));
+  const uint32_t need2 = d >= 2 ? 2u : 1u;
   const float2 flat = make_float2(1e-4f * wf, 1e-4f * wf);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* qst = qall + warp * 32 * QS;
@@ -799,7 +803,7 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
           s2b[p] = __ffma2_rn(vi, vi, __ffma2_rn(make_float2(-vo.x, -vo.y), vo, s2b[p]));
         }
       }
-      uint32_t cnt = 0;            // tests passed: low half x(1), high half x(d)
+      uint32_t cnt = 0;            // tests passed: byte 0 x(1), byte 1 x(2), high half x(d)
       bool unsure = rflag[r] != 0;
 #pragma unroll
       for (int p = 0; p < DH; ++p) {
@@ -812,9 +816,14 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
         const float2 FB = __fmul2_rn(flat, s2b[p]);
         unsure |= (VB.x < FB.x) | (VB.y < FB.y);
         cnt += (S.x >= T1.x) + (S.y >= T1.y) + ((S.x >= Td.x) + (S.y >= Td.y)) * 65536u;
+        if constexpr (kMid) {
+          const float2 T2 = __fmul2_rn(k2, P);
+          cnt += ((S.x >= T2.x) + (S.y >= T2.y)) * 256u;
+        }
       }
       if (!ROWMIN) {
-        const bool cand = act && (unsure || ((cnt & 255u) >= 1u && (cnt >> 16) >= uint32_t(d)));
+        const bool cand = act && (unsure || ((cnt & 255u) >= 1u && (!kMid || ((cnt >> 8) & 255u) >= need2) &&
+                                             (cnt >> 16) >= uint32_t(d)));
         const unsigned m = __ballot_sync(0xffffffffu, cand);
         if (!m) continue;
         const int n = __popc(m);

@@ -1,8 +1,9 @@
 // Host side of the C ABI declared in include/momenti.h: argument checks,
-// the memory planner, the hash-all pipeline (Algorithm 1, line 2, and the
-// index of Section 4), the traversal driver with TOP and STOP (Algorithm 1,
-// lines 3-19, Algorithm 2), the exact all-pairs path (line 20) and the
-// float64 re-verification of the result.
+// the memory planner, the hash-all pipeline (the hashing step of
+// Algorithm 1 and the index of Section 4), the traversal driver with TOP and
+// STOP (the prefix loop of Algorithm 1, with Algorithm 2), the exact
+// all-pairs path (Algorithm 1's final fallback) and the float64
+// re-verification of the result.
 //
 // TOP: Algorithm 1 keeps a bounded priority queue; with the trivial-match
 // rule of the top-k definition (Section 3.1) one new pair can displace two
@@ -467,7 +468,7 @@ int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out,
   return MOMENTI_OK;
 }
 
-// Exact all-pairs top-k (Algorithm 1, line 20).  tau0 <= 0: derive the
+// Exact all-pairs top-k (the final fallback of Algorithm 1).  tau0 <= 0: derive the
 // first threshold from per-window nearest distances.
 int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_out, double* max_err) {
   Index& ix = h->ix;
