@@ -98,7 +98,7 @@ typedef struct momenti_params {
 /* One motif: windows a < b (0-based), dist_d (Definition distdims),
  * dist_d^max (Eq. distdmax), the dims_d set as a bit mask (bit f = dim f),
  * and fail_bound = the miss-probability bound of Lemma stop at return
- * (0 when the exact all-pairs path of Algorithm 1's last line produced it). */
+ * (0 when Algorithm 1's exact all-pairs fallback produced it). */
 typedef struct momenti_motif {
   int64_t  a, b;
   double   dist_d;
@@ -116,7 +116,7 @@ typedef struct momenti_stats {
   int64_t  n_candidates;     /* (pair, repetition) events with W >= d, first dim only */
   int64_t  n_verified;       /* distinct pairs whose distances were computed          */
   int64_t  n_pool;           /* distinct verified pairs held by TOP's pool            */
-  int32_t  fallback;         /* 1 if Algorithm 1's last line (all pairs) ran          */
+  int32_t  fallback;         /* 1 if Algorithm 1's exact fallback (all pairs) ran    */
   int32_t  n_chunks;         /* device round trips of the traversal                   */
   double   t_hash_ms;        /* momenti_hash_all: stats, r, projections, hashes       */
   double   t_sort_ms;        /*   of which the index sort                             */

@@ -517,7 +517,7 @@ def momenti(T: np.ndarray, w: int, d: int, k: int, delta: float, A: np.ndarray,
 
     ``all_k`` uses delta / k (Lemma topkdip).  A has shape (D, L, K, w),
     U (D, L, K).  Returns a dict with the motifs [(dist_d, a, b, dims,
-    dist_max)], the stopping (i, j) (None when the last line ran), the
+    dist_max)], the stopping (i, j) (None when the exact fallback ran), the
     number of distance computations (verified pairs, repeats included, as
     the paper counts them), the failure bound at return and the number of
     distinct verified pairs."""
