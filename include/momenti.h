@@ -178,7 +178,8 @@ int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, 
  *   stream : cudaStream_t for all work of this handle, or NULL.
  * The index stays on the device, owned by the handle; a later call
  * replaces it.  MOMENTI_ERR_ARG: NULL series, D not in 1..64 or not the D
- * of set_hash_params, d > D, n < w, ld < n, n - w + 1 >= 2^31.
+ * of set_hash_params, d > D, n < w, ld < n, n - w + 1 >= 65535 * 2048
+ * (134,215,680 windows).
  * MOMENTI_ERR_MEMORY: the limit cannot hold the series, its statistics and
  * one repetition. */
 int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64_t n,

@@ -8,8 +8,10 @@
 
 namespace momenti {
 
-// Window count above which a 32-bit window index would overflow.
-constexpr int64_t kMaxWindows = (int64_t(1) << 31) - 1;
+// Window count limit: the index sort puts tiles of 2048 windows on the
+// grid's y dimension (at most 65535 blocks), which is tighter than the
+// 32-bit window index.
+constexpr int64_t kMaxWindows = int64_t(65535) * 2048;
 constexpr int kKeyBytes = 8;          // one byte per concatenated hash value
 constexpr int kRepStride = 8;         // projections per repetition in the layouts
 constexpr double kFlatRel = 1e-8;     // flat window: sigma <= kFlatRel (1 + |mu|)

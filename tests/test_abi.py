@@ -67,3 +67,18 @@ def test_calls_out_of_order(mom):
     assert mom.lib.momenti_hash_all(h, None, 0, 100, 1, 100, 0, None) == mom.ERR_ARG
     mom.lib.momenti_destroy(h)
     mom.lib.momenti_destroy(None)
+
+
+def test_window_limit_of_the_index_sort(mom):
+    # at most 65535 * 2048 windows: the sort's tiles of 2048 windows sit on
+    # the grid's y dimension; the check precedes any read of the series or
+    # any device call
+    w = 10
+    p = mom.default_params(w=w, d=1, k=1)
+    h = C.c_void_p()
+    assert mom.lib.momenti_create(C.byref(h), C.byref(p)) == mom.OK
+    dummy = (C.c_float * 4)()
+    n = 65535 * 2048 + w - 1          # exactly 65535 * 2048 windows
+    assert mom.lib.momenti_hash_all(h, dummy, mom.F32, n, 1, n, 0, None) == mom.ERR_ARG
+    assert b"too many windows" in mom.lib.momenti_last_error(h)
+    mom.lib.momenti_destroy(h)
