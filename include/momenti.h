@@ -308,11 +308,12 @@ uint64_t momenti_launch_count(void);
 
 /* Starts timing every launch of the kernel called name with CUDA events on
  * the launching stream, and clears the accumulated time; NULL stops timing.
- * Kernel names: split_f32, split_f64, window_stats, r_sample, draw,
- * layout_hash, layout_boff, proj_hash_fp32, proj_hash_tc, rehash,
- * sort_hist, sort_scan, sort_scatter, sort_finish, chunk_agg, chunk_scan,
- * scan_local, scan_top, scan_add, collide, hs_clear, collect_tag,
- * verify_new, verify_pairs, allpairs. */
+ * Kernel names: split_f32, split_f64, point_major, window_stats,
+ * stats_pm, mean16, r_sample, draw, layout_hash, layout_boff,
+ * proj_hash_fp32, proj_hash_tc, rehash, sort_hist, sort_scan,
+ * sort_scatter, sort_finish, chunk_agg, chunk_scan, scan_local, scan_top,
+ * scan_add, collide, bucket_jobs, subbucket, subwarp, hs_clear,
+ * verify_events, verify_pairs, allpairs, select_pairs. */
 int momenti_time_kernel(const char* name);
 
 /* Device time in milliseconds accumulated by the timed kernel since the

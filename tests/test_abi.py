@@ -82,3 +82,17 @@ def test_window_limit_of_the_index_sort(mom):
     assert mom.lib.momenti_hash_all(h, dummy, mom.F32, n, 1, n, 0, None) == mom.ERR_ARG
     assert b"too many windows" in mom.lib.momenti_last_error(h)
     mom.lib.momenti_destroy(h)
+
+
+def test_header_names_every_timed_kernel():
+    # momenti_time_kernel documents the names it accepts: exactly the
+    # names the sources pass to the launch accounting
+    csrc = os.path.join(ROOT, "paper_2502_14446_gb300", "csrc")
+    used = set()
+    for fn in os.listdir(csrc):
+        if fn.endswith(".cu"):
+            used |= set(re.findall(r'MOMENTI_LAUNCH\("([a-z0-9_]+)"', open(os.path.join(csrc, fn)).read()))
+    text = open(os.path.join(ROOT, "include", "momenti.h")).read()
+    block = re.search(r"Kernel names:(.*?)\*/", text, re.S).group(1)
+    listed = set(re.findall(r"[a-z0-9_]+", block.replace("*", " ")))
+    assert used and listed == used
