@@ -268,6 +268,39 @@ int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, 
 int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int64_t cap,
                     int64_t* count);
 
+/* ---- host arithmetic of the search (no device needed) ----------------- */
+
+/* Eq. (eucl-collision-probability): the probability that one hash function
+ * h(x) = floor((a . x + b) / r) gives two vectors at Euclidean distance R
+ * the same value; 1 for R <= 0.  The function momenti_topk uses. */
+double momenti_collision_probability(double R, double r);
+
+/* The miss-probability bound of Lemma stop (Eq. probnotcolliding) that
+ * Algorithm 2 compares with delta, for a pair with dist_d^max = dist_max
+ * after repetition j of prefix length i (both 1-based, 1 <= i <= K,
+ * 0 <= j <= L): with p = P(dist_max)^d, (1 - p^i)^j when i = K, else
+ * (1 - p^i)^j (1 - p^(i+1))^(L - j).  The function momenti_topk uses;
+ * NaN for arguments outside those ranges or d < 1. */
+double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, int32_t L,
+                             int32_t d, double r);
+
+/* TOP of Algorithm 1 over given candidates, through the pool momenti_topk
+ * keeps: the m pairs (a[q] < b[q]) with distances dd[q] (float, as the
+ * device records them) enter in order, batch at a time, as verified pairs
+ * enter the pool during the search (a pair seen before keeps its first
+ * distance); afterwards TOP is the top-k motif set of Section 3.1 (trivial-
+ * match exclusion eps) over the distinct pairs: taken in ascending
+ * (dd, a, b) order, a pair is accepted iff b - a > eps and both of its
+ * indices are more than eps away from both indices of every accepted
+ * pair, until k are accepted.  idx (room for k) receives the positions q
+ * (first occurrences) of TOP's pairs in order, *n_out their number.  Host
+ * arrays, caller-owned; nothing is kept; no device is used.
+ * MOMENTI_ERR_ARG: NULL arrays (m > 0), idx or n_out NULL, m < 0, k < 1,
+ * eps < 0, batch < 1, a NaN distance, or an index outside 0 .. 2^32 - 1
+ * or a >= b. */
+int momenti_top_select(const float* dd, const int64_t* a, const int64_t* b, int64_t m,
+                       int32_t k, int64_t eps, int64_t batch, int64_t* idx, int32_t* n_out);
+
 /* ---- index sort without allocation ------------------------------------ */
 
 /* Largest key count momenti_index_sort_noalloc accepts. */

@@ -31,6 +31,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -1448,6 +1449,56 @@ int momenti_topk_batch(int32_t B, const momenti_params* params, const void* cons
                        momenti_stats* stats, int32_t* rc, char* err, int32_t err_len) {
   try {
     return topk_batch_impl(B, params, series, dtype, n, D, on_device, threads, out, out_stride, n_out, stats, rc, err, err_len);
+  } catch (const std::bad_alloc&) {
+    return fail(nullptr, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(nullptr, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+// ---- host arithmetic of the search, callable without a device ----
+
+double momenti_collision_probability(double R, double r) { return collision_probability(R, r); }
+
+double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, int32_t L,
+                             int32_t d, double r) {
+  if (K < 1 || i < 1 || i > K || j < 0 || j > L || d < 1) return std::nan("");
+  return failure_bound(dist_max, i, j, K, L, d, r);
+}
+
+static int top_select_impl(const float* dd, const int64_t* a, const int64_t* b, int64_t m,
+                           int32_t k, int64_t eps, int64_t batch, int64_t* idx, int32_t* n_out) {
+  if (m < 0 || k < 1 || eps < 0 || batch < 1 || !idx || !n_out) return MOMENTI_ERR_ARG;
+  if (m > 0 && (!dd || !a || !b)) return MOMENTI_ERR_ARG;
+  *n_out = 0;
+  std::vector<PairRec> rec(static_cast<size_t>(m));
+  std::unordered_map<uint64_t, int64_t> first;     // pair -> first position
+  for (int64_t q = 0; q < m; ++q) {
+    if (std::isnan(dd[q]) || a[q] < 0 || b[q] <= a[q] || b[q] > int64_t(UINT32_MAX))
+      return MOMENTI_ERR_ARG;
+    PairRec& r = rec[size_t(q)];
+    r = PairRec{};
+    r.a = uint32_t(a[q]);
+    r.b = uint32_t(b[q]);
+    r.dist_d = dd[q];
+    r.dist_max = dd[q];
+    first.emplace((uint64_t(r.a) << 32) | r.b, q);
+  }
+  Pool pool;
+  pool.k = k;
+  pool.eps = eps;
+  for (int64_t q0 = 0; q0 < m; q0 += batch)
+    pool.add(rec.data() + q0, size_t(std::min<int64_t>(batch, m - q0)));
+  int32_t n = 0;
+  for (const PoolEntry& e : pool.top) idx[n++] = first.at((uint64_t(e.a) << 32) | e.b);
+  *n_out = n;
+  return MOMENTI_OK;
+}
+
+int momenti_top_select(const float* dd, const int64_t* a, const int64_t* b, int64_t m,
+                       int32_t k, int64_t eps, int64_t batch, int64_t* idx, int32_t* n_out) {
+  try {
+    return top_select_impl(dd, a, b, m, k, eps, batch, idx, n_out);
   } catch (const std::bad_alloc&) {
     return fail(nullptr, MOMENTI_ERR_MEMORY, "host memory exhausted");
   } catch (...) {

@@ -33,6 +33,7 @@ EXPORTS = (
     "momenti_verify", "momenti_get_info", "momenti_get_window_stats", "momenti_get_keys",
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
     "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
+    "momenti_collision_probability", "momenti_failure_bound", "momenti_top_select",
 )
 
 
@@ -91,6 +92,11 @@ def _load():
         "momenti_time_kernel": (C.c_int, [C.c_char_p]),
         "momenti_kernel_time": (C.c_int, [P(C.c_double), P(C.c_uint64)]),
         "momenti_index_sort_noalloc": (C.c_int, [vp, C.c_int64, C.c_int32, vp, vp, vp]),
+        "momenti_collision_probability": (C.c_double, [C.c_double, C.c_double]),
+        "momenti_failure_bound": (C.c_double, [C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                                               C.c_int32, C.c_int32, C.c_double]),
+        "momenti_top_select": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int64,
+                                         C.c_int64, vp, P(C.c_int32)]),
         "momenti_topk_batch": (C.c_int, [C.c_int32, P(momenti_params), P(vp), P(C.c_int32),
                                          P(C.c_int64), P(C.c_int32), C.c_int32, C.c_int32,
                                          P(momenti_motif), C.c_int32, P(C.c_int32),
@@ -141,6 +147,33 @@ def kernel_time():
     if rc != OK:
         raise MomentiError(rc, "momenti_kernel_time")
     return ms.value, int(n.value)
+
+
+def collision_probability(R: float, r: float) -> float:
+    """Eq. (eucl-collision-probability) as the library's search evaluates it."""
+    return float(lib.momenti_collision_probability(R, r))
+
+
+def failure_bound(dist_max: float, i: int, j: int, K: int, L: int, d: int, r: float) -> float:
+    """The bound of Lemma stop that Algorithm 2 compares with delta (i, j 1-based)."""
+    return float(lib.momenti_failure_bound(dist_max, i, j, K, L, d, r))
+
+
+def top_select(dd, a, b, k: int, eps: int, batch: int = 1 << 30):
+    """TOP over given candidate pairs through the search's pool, fed
+    ``batch`` pairs at a time; returns the positions of TOP's pairs."""
+    dd = np.ascontiguousarray(dd, dtype=np.float32)
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    b = np.ascontiguousarray(b, dtype=np.int64)
+    if not (dd.shape == a.shape == b.shape and dd.ndim == 1):
+        raise ValueError("dd, a, b: equal-length vectors")
+    idx = np.zeros(max(k, 1), dtype=np.int64)
+    n = C.c_int32()
+    rc = lib.momenti_top_select(_ptr(dd), _ptr(a), _ptr(b), dd.size, k, eps, batch, _ptr(idx),
+                                C.byref(n))
+    if rc != OK:
+        raise MomentiError(rc, "momenti_top_select")
+    return [int(q) for q in idx[:n.value]]
 
 
 def topk_batch(params, series_list, threads: int = 8):
