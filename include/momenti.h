@@ -272,7 +272,8 @@ int momenti_collide(momenti_handle* h, int32_t i, int32_t j, int64_t* pairs, int
 
 /* Eq. (eucl-collision-probability): the probability that one hash function
  * h(x) = floor((a . x + b) / r) gives two vectors at Euclidean distance R
- * the same value; 1 for R <= 0.  The function momenti_topk uses. */
+ * the same value; 1 for R <= 0, NaN for r <= 0 or a NaN R.  The function
+ * momenti_topk uses. */
 double momenti_collision_probability(double R, double r);
 
 /* The miss-probability bound of Lemma stop (Eq. probnotcolliding) that
@@ -280,7 +281,7 @@ double momenti_collision_probability(double R, double r);
  * after repetition j of prefix length i (both 1-based, 1 <= i <= K,
  * 0 <= j <= L): with p = P(dist_max)^d, (1 - p^i)^j when i = K, else
  * (1 - p^i)^j (1 - p^(i+1))^(L - j).  The function momenti_topk uses;
- * NaN for arguments outside those ranges or d < 1. */
+ * NaN for arguments outside those ranges, d < 1, r <= 0 or a NaN dist_max. */
 double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, int32_t L,
                              int32_t d, double r);
 

@@ -1458,11 +1458,15 @@ int momenti_topk_batch(int32_t B, const momenti_params* params, const void* cons
 
 // ---- host arithmetic of the search, callable without a device ----
 
-double momenti_collision_probability(double R, double r) { return collision_probability(R, r); }
+double momenti_collision_probability(double R, double r) {
+  if (!(r > 0.0) || std::isnan(R)) return std::nan("");
+  return collision_probability(R, r);
+}
 
 double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, int32_t L,
                              int32_t d, double r) {
-  if (K < 1 || i < 1 || i > K || j < 0 || j > L || d < 1) return std::nan("");
+  if (K < 1 || i < 1 || i > K || j < 0 || j > L || d < 1 || !(r > 0.0) || std::isnan(dist_max))
+    return std::nan("");
   return failure_bound(dist_max, i, j, K, L, d, r);
 }
 

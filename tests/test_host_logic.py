@@ -43,6 +43,10 @@ def test_failure_bound_rejects_out_of_range_indices(mom):
     assert math.isnan(mom.failure_bound(1.0, 9, 1, 8, 200, 1, 1.0))      # i > K
     assert math.isnan(mom.failure_bound(1.0, 2, 201, 8, 200, 1, 1.0))    # j > L
     assert math.isnan(mom.failure_bound(1.0, 2, 1, 8, 200, 0, 1.0))      # d < 1
+    assert math.isnan(mom.failure_bound(1.0, 2, 1, 8, 200, 1, 0.0))      # r <= 0
+    assert math.isnan(mom.collision_probability(1.0, 0.0))
+    assert math.isnan(mom.collision_probability(float("nan"), 1.0))
+    assert mom.collision_probability(-1.0, 1.0) == 1.0
 
 
 def _candidates(rng, m, M):
