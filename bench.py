@@ -138,19 +138,29 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        text = open(self.f.name).read()
         os.unlink(self.f.name)
+        return self.parse(text)
+
+    @staticmethod
+    def parse(text: str) -> dict:
+        """Median SM clock, the maximum clock and the throttle reasons seen
+        in nvidia-smi rows of the query Q (csv, no header, no units);
+        malformed rows are skipped."""
+        rows = [r.split(",") for r in text.strip().splitlines() if r.strip()]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-                for nm, v in zip(names, r[5:9]):
-                    if v.strip() == "Active":
-                        reasons.add(nm)
+                clk, top = float(r[1]), float(r[2])
+                flags = [v.strip() for v in r[5:9]]
             except (ValueError, IndexError):
                 continue
+            sm.append(clk)
+            mx = top
+            for nm, v in zip(names, flags):
+                if v == "Active":
+                    reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
 

@@ -50,3 +50,18 @@ def test_roofline_arithmetic():
     assert t["bound"] == "tensor" and t["peak"] == pk["tflops_sustained"]
     assert t["achieved"] == pytest.approx(2.0 * 99701 * 8 * 200 * 8 * 300 / 2.9e-3 / 1e12)
     assert bench.roofline("allpairs", 0.0, 0, info, st, _Wl, steps, pk) is None
+
+
+def test_clock_samples_parse():
+    rows = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2040, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.Clocks.parse(rows)
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.Clocks.parse("0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, Not Active")
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.Clocks.parse("") == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
