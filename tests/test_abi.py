@@ -96,3 +96,21 @@ def test_header_names_every_timed_kernel():
     block = re.search(r"Kernel names:(.*?)\*/", text, re.S).group(1)
     listed = set(re.findall(r"[a-z0-9_]+", block.replace("*", " ")))
     assert used and listed == used
+
+
+def test_plain_c_client(mom, tmp_path):
+    # the header is C99 and the library links and answers from a C program
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pkg = os.path.dirname(mom.LIB_PATH)
+    exe = str(tmp_path / "c_client")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    os.path.join(ROOT, "tests", "c_client.c"), "-I", os.path.join(ROOT, "include"),
+                    "-L", pkg, "-lmomenti", f"-Wl,-rpath,{pkg}", "-lm", "-o", exe],
+                   check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "FAIL" not in r.stdout and r.stdout.count("ok ") == 9
