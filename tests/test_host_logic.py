@@ -96,3 +96,22 @@ def test_top_select_argument_errors(mom):
     with pytest.raises(mom.MomentiError):
         mom.top_select(one, np.array([0]), np.array([5]), 0, 0)           # k < 1
     assert mom.top_select(np.zeros(0, np.float32), np.zeros(0), np.zeros(0), 3, 0) == []
+
+
+def test_top_select_through_pool_truncation(mom):
+    # more candidates than the pool holds (2^22): it keeps the smaller half
+    # and drops what lies above; TOP, far below that edge, is unchanged
+    rng = np.random.default_rng(77)
+    m, M = (1 << 22) + 300_000, 1 << 30
+    a = rng.integers(0, M - 1000, m, dtype=np.int64)
+    b = a + rng.integers(1, 1000, m, dtype=np.int64)
+    key = a * M + b
+    _, first = np.unique(key, return_index=True)
+    first.sort()
+    a, b = a[first], b[first]
+    dd = rng.uniform(0.0, 100.0, a.size).astype(np.float32)
+    k, eps = 10, 5
+    order = np.lexsort((b, a, dd))[:20_000]          # (dd, a, b) order, a prefix
+    ref = O.greedy_topk([(float(dd[q]), int(a[q]), int(b[q]), int(q)) for q in order], k, eps)
+    assert len(ref) == k
+    assert mom.top_select(dd, a, b, k, eps, 1 << 20) == [c[3] for c in ref]
