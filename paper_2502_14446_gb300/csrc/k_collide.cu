@@ -474,7 +474,7 @@ __global__ void k_bucket_jobs(const uint8_t* __restrict__ lcp, Seg sg, int segs,
       const unsigned long long pos = bbase[cls] + wcnt[warp][cls] + __popc(m[cls] & lt);
       if (pos < quarter) jobs[cls * quarter + pos] = BucketJob{seg, p, n, 0u};
     }
-    __syncthreads();                               // wcnt / bbase reused by the next round
+    __syncthreads();                               // wcnt / bbase reused by the next iteration
   }
 }
 
