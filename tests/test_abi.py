@@ -114,3 +114,18 @@ def test_plain_c_client(mom, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "FAIL" not in r.stdout and r.stdout.count("ok ") == 9
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # no CPU fallback: a copy of the binding next to no libmomenti.so
+    # refuses to import
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "nolib"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2502_14446_gb300", "momenti.py"), pkg / "momenti.py")
+    r = subprocess.run([sys.executable, "-c", "import momenti"], cwd=str(pkg),
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libmomenti.so is missing" in r.stderr
