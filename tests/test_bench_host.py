@@ -65,3 +65,21 @@ def test_clock_samples_parse():
     hot = bench.Clocks.parse("0, 1500, 2070, 1400, 0x8, Not Active, Active, Not Active, Not Active")
     assert hot["reasons"] == ["hw_thermal_slowdown"]
     assert bench.Clocks.parse("") == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_clock_sampler_end_to_end(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi on PATH: the sampler starts it, stops it and
+    # parses what it wrote
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 800, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2060, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    c = bench.Clocks(0)
+    c.start()
+    time.sleep(1.0)
+    out = c.stop()
+    assert out == {"sm_mhz": 2065.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 2}
