@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -129,3 +130,36 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
                        capture_output=True, text=True, timeout=120)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "libmomenti.so is missing" in r.stderr
+
+
+def test_topk_batch_argument_errors(mom):
+    P = C.POINTER
+    one = (mom.momenti_params * 1)(mom.default_params(w=10, d=1, k=3))
+    series = (C.c_void_p * 1)(None)
+    dtype, n, D = (C.c_int32 * 1)(0), (C.c_int64 * 1)(100), (C.c_int32 * 1)(1)
+    out = (mom.momenti_motif * 3)()
+    n_out, rc = (C.c_int32 * 1)(), (C.c_int32 * 1)()
+    call = mom.lib.momenti_topk_batch
+    assert call(-1, one, series, dtype, n, D, 0, 1, out, 3, n_out, None, rc, None, 0) == mom.ERR_ARG
+    assert call(0, None, None, None, None, None, 0, 1, None, 0, None, None, None, None, 0) == mom.OK
+    assert call(1, None, series, dtype, n, D, 0, 1, out, 3, n_out, None, rc, None, 0) == mom.ERR_ARG
+    # k = 3 motifs do not fit an output stride of 2
+    assert call(1, one, series, dtype, n, D, 0, 1, out, 2, n_out, None, rc, None, 0) == mom.ERR_ARG
+
+
+def test_no_device_is_an_error_not_a_fallback(mom):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    x = np.arange(200, dtype=np.float32)
+    one = (mom.momenti_params * 1)(mom.default_params(w=10, d=1, k=1))
+    series = (C.c_void_p * 1)(x.ctypes.data)
+    dtype, n, D = (C.c_int32 * 1)(0), (C.c_int64 * 1)(200), (C.c_int32 * 1)(1)
+    out = (mom.momenti_motif * 1)()
+    n_out, rc = (C.c_int32 * 1)(), (C.c_int32 * 1)()
+    r = mom.lib.momenti_topk_batch(1, one, series, dtype, n, D, 0, 1, out, 1, n_out, None, rc,
+                                   None, 0)
+    assert r == mom.ERR_CUDA
+    with mom.Momenti(w=10, d=1, k=1, delta=0.1) as h:
+        with pytest.raises(mom.MomentiError):
+            h.hash_all(x.reshape(1, -1))
