@@ -41,3 +41,22 @@ def test_two_gloo_ranks_combine_like_bench():
     assert t0 == t1 == 200.0                 # max over ranks
     assert v0 == pytest.approx(world * 1000 * 5 / 0.2)
     assert s0 != s1                          # each rank searches its own series
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    # two ranks: rank 0 times the oracle and prints one line, rank 1 exits 0
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1
+    assert d["value"] == pytest.approx(d["cpu_baseline"]["value"])
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
