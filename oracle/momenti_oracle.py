@@ -536,3 +536,63 @@ def momenti(T: np.ndarray, w: int, d: int, k: int, delta: float, A: np.ndarray,
                 "fail_bound": failure_bound(top[-1][4], i, j, K, L, d, r), "pool": pool}
     return {"motifs": exact_topk_auto(T, w, d, k, excl, fallback_tau), "stop": None,
             "n_dist": n_dist, "fail_bound": 0.0, "pool": pool}
+
+
+def momenti_multi(T: np.ndarray, w: int, d_low: int, d_high: int, k: int, delta: float,
+                  A: np.ndarray, U: np.ndarray, r: float, excl: int | None = None):
+    """Section 6.3, motifs of every dimensionality d in [d_low, d_high] in
+    one traversal: one TOP per d; a verified pair's per-dimension distances
+    give dist_d for every d at once, and the pair is offered to the TOP of
+    every d not yet confirmed; the collision condition W >= d uses the
+    smallest unconfirmed d, which rises as dimensionalities are confirmed;
+    after each repetition every unconfirmed d whose TOP is full and passes
+    STOP (Algorithm 2 with that d) is confirmed with its own (i, j).  When
+    the loop ends, each d still unconfirmed gets the exact top-k (the final
+    fallback of Algorithm 1).
+
+    Returns {d: {"motifs", "stop", "fail_bound"}} and the number of
+    distance computations under the key "n_dist"."""
+    T = np.asarray(T, dtype=np.float64)
+    D, n = T.shape
+    L, K = A.shape[1], A.shape[2]
+    if not 1 <= d_low <= d_high <= D:
+        raise ValueError("need 1 <= d_low <= d_high <= D")
+    eps = exclusion_zone(w, excl)
+    keys, _ = hash_all(T, w, A, U, r)
+    M = keys.shape[1]
+    Z = [znorm_windows(T[f], w) for f in range(D)]
+    pools = {d: _Pool(k, eps) for d in range(d_low, d_high + 1)}
+    done = {}
+    n_dist = 0
+    for i in range(K, 0, -1):
+        for j in range(1, L + 1):
+            open_d = [d for d in pools if d not in done]
+            if not open_d:
+                break
+            d_cur = min(open_d)
+            codes = [colliding_pairs(keys[j - 1, :, f], i) for f in range(D)]
+            allc = np.concatenate(codes) if codes else np.zeros(0, np.int64)
+            uniq, W = np.unique(allc, return_counts=True)
+            sel = uniq[W >= d_cur]
+            a, b = sel // M, sel % M
+            nt = (b - a) > eps
+            a, b = a[nt], b[nt]
+            if a.size:
+                dist = _pair_distances(Z, a, b)
+                n_dist += int(a.size)
+                for d in open_d:
+                    dd, _, dmax, order = _select_d_many(dist, d)
+                    pools[d].add_many(a, b, dd, order, dmax)
+            for d in open_d:
+                top = pools[d].top()
+                if len(top) == k and stop_condition(top[-1][4], i, j, K, L, d, delta, r):
+                    done[d] = {"motifs": top, "stop": (i, j),
+                               "fail_bound": failure_bound(top[-1][4], i, j, K, L, d, r)}
+        if len(done) == len(pools):
+            break
+    out = {}
+    for d in pools:
+        out[d] = done.get(d) or {"motifs": exact_topk_auto(T, w, d, k, excl), "stop": None,
+                                 "fail_bound": 0.0}
+    out["n_dist"] = n_dist
+    return out

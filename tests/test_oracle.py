@@ -330,3 +330,63 @@ def test_momenti_matches_exact_on_small_series(seed):
     assert res["fail_bound"] <= wl.delta
     assert [(m[1], m[2]) for m in res["motifs"]] == [(m[1], m[2]) for m in ex]
     assert {(m[1], m[2]) for m in ex} == {(a, b) for a, b, _ in wl.planted}
+
+
+# --------------------------------------- Section 6.3: several dimensionalities
+
+def test_multi_with_one_dimensionality_is_algorithm_1():
+    wl = synth.tiny(1, 1500, 3, 50, 2, k=2, n_motifs=2)
+    A, U = synth.hash_draws(wl.D, 100, 8, wl.w, 1)
+    r = O.estimate_r(wl.series, wl.w, A)
+    one = O.momenti(wl.series, wl.w, 2, wl.k, wl.delta, A, U, r)
+    multi = O.momenti_multi(wl.series, wl.w, 2, 2, wl.k, wl.delta, A, U, r)
+    assert one["stop"] is not None
+    assert multi[2]["stop"] == one["stop"] and multi[2]["motifs"] == one["motifs"]
+    assert multi[2]["fail_bound"] == one["fail_bound"] and multi["n_dist"] == one["n_dist"]
+
+
+def test_multi_when_every_pair_collides_at_once():
+    # r far above every projection and offsets b = r / 2: every hash value
+    # is floor(1/2 + tiny) = 0, every pair collides in every dim at (K, 1),
+    # each TOP is the exact top-k at once and STOP holds for every d there
+    wl = synth.tiny(9, 400, 3, 30, 1, k=2, n_motifs=0)
+    A, U = synth.hash_draws(wl.D, 4, 8, wl.w, 9)
+    U = np.full_like(U, 0.5)
+    multi = O.momenti_multi(wl.series, wl.w, 1, 3, wl.k, 0.1, A, U, 1e9)
+    for d in (1, 2, 3):
+        assert multi[d]["stop"] == (8, 1)
+        ref = O.naive_topk(wl.series, wl.w, d, wl.k)
+        assert [(m[1], m[2], tuple(m[3])) for m in multi[d]["motifs"]] == \
+               [(m[1], m[2], tuple(m[3])) for m in ref]
+
+
+def test_multi_without_stop_is_exact_and_collides_at_the_lowest_d():
+    # delta too small for STOP: every d ends in the exact top-k, and the
+    # collision threshold stays at d_low (as many distance computations as
+    # the single search for d_low)
+    wl = synth.tiny(10, 400, 3, 30, 1, k=2, n_motifs=1)
+    A, U = synth.hash_draws(wl.D, 3, 8, wl.w, 10)
+    r = O.estimate_r(wl.series, wl.w, A)
+    multi = O.momenti_multi(wl.series, wl.w, 1, 3, wl.k, 1e-300, A, U, r)
+    one = O.momenti(wl.series, wl.w, 1, wl.k, 1e-300, A, U, r)
+    assert one["stop"] is None and multi["n_dist"] == one["n_dist"]
+    for d in (1, 2, 3):
+        assert multi[d]["stop"] is None and multi[d]["fail_bound"] == 0.0
+        ref = O.naive_topk(wl.series, wl.w, d, wl.k)
+        assert [(m[1], m[2], tuple(m[3])) for m in multi[d]["motifs"]] == \
+               [(m[1], m[2], tuple(m[3])) for m in ref]
+
+
+def test_multi_confirms_each_dimensionality_by_its_own_bound():
+    wl = synth.tiny(2, 1500, 3, 50, 2, k=2, n_motifs=2)
+    A, U = synth.hash_draws(wl.D, 100, 8, wl.w, 2)
+    r = O.estimate_r(wl.series, wl.w, A)
+    multi = O.momenti_multi(wl.series, wl.w, 1, 3, wl.k, wl.delta, A, U, r)
+    confirmed = [d for d in (1, 2, 3) if multi[d]["stop"] is not None]
+    assert confirmed
+    for d in confirmed:
+        i, j = multi[d]["stop"]
+        top = multi[d]["motifs"]
+        assert len(top) == wl.k
+        fb = O.failure_bound(top[-1][4], i, j, 8, 100, d, r)
+        assert multi[d]["fail_bound"] == fb and fb <= wl.delta
