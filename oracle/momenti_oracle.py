@@ -18,6 +18,7 @@ Everything is float64 numpy, written to be read against the paper:
   repetitions L.
 * Algorithm 1 (MOMENTI) and Algorithm 2 (STOP), in the paper's loop order.
 * Section 6.1: the heuristic for the quantisation width r.
+* Section 6.3: motifs of several dimensionalities in one traversal.
 
 Readings of points the paper leaves open (each is listed with its reason in
 the design notes of the repository):
