@@ -17,7 +17,8 @@ Everything is float64 numpy, written to be read against the paper:
   collision probability (Eq. eucl-collision-probability), concatenation K and
   repetitions L.
 * Algorithm 1 (MOMENTI) and Algorithm 2 (STOP), in the paper's loop order.
-* Section 6.1: the heuristic for the quantisation width r.
+* Section 6.1: the heuristic for the quantisation width r, and a
+  re-derived miss-probability bound for tensoring.
 * Section 6.3: motifs of several dimensionalities in one traversal.
 
 Readings of points the paper leaves open (each is listed with its reason in
@@ -314,6 +315,80 @@ def failure_bound(dist_max: float, i: int, j: int, K: int, L: int, d: int, r: fl
     if i == K:
         return (1.0 - p ** i) ** j
     return (1.0 - p ** i) ** j * (1.0 - p ** (i + 1)) ** (L - j)
+
+
+def tensoring_failure_bound(p: float, i: int, j: int, K: int, L: int) -> float:
+    """Miss probability of a pair under tensoring (Section 6.1), re-derived.
+
+    Tensoring builds repetition j (0-based j' = j - 1 -> left function
+    l = j' div m, right function r = j' mod m, m = sqrt(L)) from m left and
+    m right functions of K/2 concatenated hashes each; the composite key
+    interleaves them (left value first), so a prefix of length t collides
+    iff the left prefix of ceil(t/2) values and the right prefix of
+    floor(t/2) values both collide.  ``p`` is the probability that one
+    hash function collides in all d dims of the pair (the caller passes
+    P(dist_max)^d, a lower bound, as in Lemma stop); the K/2 values of one
+    function collide independently, so the collision depth G of a function
+    has P(G >= u) = p^u, and all 2m functions are independent.
+
+    After j repetitions at prefix length i, every repetition has been seen
+    at length i + 1 (i < K), the first j also at length i.  The pair was
+    missed iff no visited (repetition, length) collides.  Rows l and
+    columns r fall into groups that are visited alike (rows before the
+    current one, the current one, rows after it; columns before the
+    current one and the rest), and within a pair of groups every
+    (row, column) combination is visited, so only the largest depth class
+    of each group matters: the result sums over those classes exactly.
+    The miss probability decreases as p grows, so a lower bound on p gives
+    an upper bound.  Needs L = m^2, K even, 1 <= i <= K, 0 <= j <= L."""
+    m = math.isqrt(L)
+    if m * m != L or K % 2 or not 1 <= i <= K or not 0 <= j <= L:
+        raise ValueError("tensoring needs L = m^2, K even, 1 <= i <= K, 0 <= j <= L")
+    top = i == K
+    # depth thresholds: length i and length i + 1, rows (left) and columns (right)
+    ug = (-(-i // 2), -(-(i + 1) // 2) if not top else -(-i // 2))
+    uh = (i // 2, (i + 1) // 2 if not top else i // 2)
+
+    def class_probs(u):
+        # class 0: depth < u[0]; 1: u[0] <= depth < u[1]; 2: depth >= u[1]
+        s1, s2 = p ** u[0], p ** u[1]
+        return [1.0 - s1, s1 - s2, s2]
+
+    def max_class_probs(cp, size):
+        # distribution of the largest class among `size` iid rows (-1: none)
+        if size == 0:
+            return {-1: 1.0}
+        cdf = np.cumsum(cp)
+        out, prev = {}, 0.0
+        for c in range(3):
+            cur = min(1.0, cdf[c]) ** size
+            out[c] = cur - prev
+            prev = cur
+        return out
+
+    a, b = divmod(j, m)
+    rows = [a, 1 if a < m else 0, max(0, m - a - 1)]     # before, current, after
+    cols = [b, m - b]                                     # before the current, the rest
+    # (row group, column group, 0 = length i / 1 = length i + 1) visited
+    visits = [(0, 0, 0), (0, 1, 0), (1, 0, 0)]
+    if not top:
+        visits += [(1, 1, 1), (2, 0, 1), (2, 1, 1)]
+    gdist = [max_class_probs(class_probs(ug), n) for n in rows]
+    hdist = [max_class_probs(class_probs(uh), n) for n in cols]
+    miss = 0.0
+    for g0, pg0 in gdist[0].items():
+        for g1, pg1 in gdist[1].items():
+            for g2, pg2 in gdist[2].items():
+                gm = (g0, g1, g2)
+                for h0, ph0 in hdist[0].items():
+                    for h1, ph1 in hdist[1].items():
+                        hm = (h0, h1)
+                        # a visit at length i needs class >= 1 on both
+                        # sides, at length i + 1 class 2 on both
+                        hit = any(gm[rg] >= 1 + lv and hm[cg] >= 1 + lv for rg, cg, lv in visits)
+                        if not hit:
+                            miss += pg0 * pg1 * pg2 * ph0 * ph1
+    return float(miss)
 
 
 def projections(T: np.ndarray, w: int, A: np.ndarray, f: int, windows=None) -> np.ndarray:

@@ -390,3 +390,65 @@ def test_multi_confirms_each_dimensionality_by_its_own_bound():
         assert len(top) == wl.k
         fb = O.failure_bound(top[-1][4], i, j, 8, 100, d, r)
         assert multi[d]["fail_bound"] == fb and fb <= wl.delta
+
+
+# ------------------------------------------- Section 6.1: tensoring bound
+
+def _tensoring_miss_mc(p, i, j, K, L, trials, rng):
+    """Direct simulation of the tensored hash collisions of one pair: each
+    of the m left and m right functions has K/2 values, each colliding
+    with probability p; repetition j' (0-based) pairs left j' div m with
+    right j' mod m and interleaves them (left first); prefix length t
+    collides iff its first t interleaved values all collide.  Counts the
+    trials in which none of the first j repetitions collides at length i
+    and (for i < K) none of the L repetitions collides at length i + 1."""
+    m = math.isqrt(L)
+    half = K // 2
+    left = rng.random((trials, m, half)) < p
+    right = rng.random((trials, m, half)) < p
+    inter = np.empty((trials, m, m, K), bool)
+    inter[..., 0::2] = left[:, :, None, :]
+    inter[..., 1::2] = right[:, None, :, :]
+    pref = np.cumprod(inter, axis=-1).astype(bool)          # pref[..., t-1]: length t collides
+    rep = np.arange(L)
+    hit_i = pref[:, rep // m, rep % m, i - 1][:, :j].any(axis=1)
+    hit = hit_i
+    if i < K:
+        hit = hit | pref[:, rep // m, rep % m, i].any(axis=1)
+    return 1.0 - hit.mean()
+
+
+@pytest.mark.parametrize("p,i,j,K,L", [
+    (0.5, 4, 5, 8, 16), (0.5, 3, 9, 8, 16), (0.7, 8, 7, 8, 16), (0.6, 1, 2, 8, 9),
+    (0.8, 6, 0, 8, 9), (0.4, 2, 16, 8, 16), (0.9, 7, 20, 8, 25), (0.5, 8, 16, 8, 16)])
+def test_tensoring_bound_is_the_simulated_miss_probability(p, i, j, K, L):
+    rng = np.random.default_rng(hash((p, i, j, K, L)) % 2**32)
+    trials = 200_000
+    mc = _tensoring_miss_mc(p, i, j, K, L, trials, rng)
+    exact = O.tensoring_failure_bound(p, i, j, K, L)
+    sigma = math.sqrt(max(exact * (1 - exact), 1e-12) / trials)
+    assert abs(mc - exact) <= 5 * sigma + 1e-9
+
+
+def test_tensoring_bound_special_cases():
+    # nothing visited: certain miss; p = 1: any visit collides
+    assert O.tensoring_failure_bound(0.5, 8, 0, 8, 16) == pytest.approx(1.0)
+    assert O.tensoring_failure_bound(1.0, 5, 3, 8, 16) == pytest.approx(0.0, abs=1e-15)
+    # one repetition at the top level: the interleaved K values all collide
+    assert O.tensoring_failure_bound(0.6, 8, 1, 8, 16) == pytest.approx(1 - 0.6 ** 8)
+    # more repetitions and a larger p never raise the miss probability
+    seq = [O.tensoring_failure_bound(0.5, 4, j, 8, 16) for j in range(17)]
+    assert all(x >= y - 1e-15 for x, y in zip(seq, seq[1:]))
+    ps = [O.tensoring_failure_bound(p, 4, 6, 8, 16) for p in (0.3, 0.5, 0.7, 0.9)]
+    assert all(x >= y for x, y in zip(ps, ps[1:]))
+    with pytest.raises(ValueError):
+        O.tensoring_failure_bound(0.5, 4, 1, 8, 200)          # L not a square
+
+
+def test_printed_tensoring_lemma_is_not_a_bound():
+    # the lemma's P_t(i/2, j) = (1 - p^ceil(i/2))^(j div m) (1 - p^floor(i/2))^(j mod m)
+    # at i = K falls below the simulated and re-derived miss probability
+    p, K, L, m = 0.5, 8, 16, 4
+    for j in (4, 8, 12):
+        printed = (1 - p ** 4) ** (j // m) * (1 - p ** 4) ** (j % m)
+        assert O.tensoring_failure_bound(p, K, j, K, L) > printed + 0.04
