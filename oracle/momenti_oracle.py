@@ -17,8 +17,9 @@ Everything is float64 numpy, written to be read against the paper:
   collision probability (Eq. eucl-collision-probability), concatenation K and
   repetitions L.
 * Algorithm 1 (MOMENTI) and Algorithm 2 (STOP), in the paper's loop order.
-* Section 6.1: the heuristic for the quantisation width r, and a
-  re-derived miss-probability bound for tensoring.
+* Section 6.1: the heuristic for the quantisation width r, and tensoring:
+  interleaved keys, a re-derived miss-probability bound, and Algorithm 1
+  with STOP on that bound.
 * Section 6.3: motifs of several dimensionalities in one traversal.
 
 Readings of points the paper leaves open (each is listed with its reason in
@@ -549,13 +550,16 @@ class _Pool:
 
 
 def momenti_traverse(keys: np.ndarray, pair_distances, d: int, k: int, delta: float,
-                     r: float, eps: int, K: int | None = None):
+                     r: float, eps: int, K: int | None = None, bound=None):
     """The prefix traversal of Algorithm 1 over given composite hash keys
     (uint64, shape (L, M, D)): for i = K..1, for j = 1..L, W(a, b) counts the
     dimensions in which a and b share the length-i prefix; every pair with
     W >= d that is not a trivial match is verified with
     ``pair_distances(a, b) -> (D, m)`` and offered to TOP; the loop returns
     when |TOP| = k and STOP(TOP.max(), i, j, delta) (Algorithm 2).
+
+    ``bound(dist_max, i, j)``, when given, replaces Lemma stop's bound in
+    the STOP test (tensoring).
 
     Returns (top, (i, j) or None, n_dist, pool_size)."""
     L, M, D = keys.shape
@@ -578,8 +582,11 @@ def momenti_traverse(keys: np.ndarray, pair_distances, d: int, k: int, delta: fl
                 dd, masks, dmax, order = _select_d_many(dist, d)
                 pool.add_many(a, b, dd, order, dmax)
             top = pool.top()
-            if len(top) == k and stop_condition(top[-1][4], i, j, K, L, d, delta, r):
-                return top, (i, j), n_dist, len(pool.pairs)
+            if len(top) == k:
+                done = (stop_condition(top[-1][4], i, j, K, L, d, delta, r) if bound is None
+                        else bound(top[-1][4], i, j) <= delta)
+                if done:
+                    return top, (i, j), n_dist, len(pool.pairs)
     return None, None, n_dist, len(pool.pairs)
 
 
@@ -672,3 +679,57 @@ def momenti_multi(T: np.ndarray, w: int, d_low: int, d_high: int, k: int, delta:
                                  "fail_bound": 0.0}
     out["n_dist"] = n_dist
     return out
+
+
+def tensored_keys(T: np.ndarray, w: int, Al: np.ndarray, Ul: np.ndarray, Ar: np.ndarray,
+                  Ur: np.ndarray, r: float) -> np.ndarray:
+    """Tensoring (Section 6.1): m left and m right hash functions of K/2
+    values each (Al, Ar of shape (D, m, K/2, w), Ul, Ur (D, m, K/2));
+    repetition j' (0-based) interleaves the values of left function
+    j' div m and right function j' mod m, a left value first.  Only K m
+    projections per window and dimension are evaluated for m^2
+    repetitions.  Returns keys uint64 (m^2, M, D) packed like pack_keys."""
+    T = np.asarray(T, dtype=np.float64)
+    D = T.shape[0]
+    m, half = Al.shape[1], Al.shape[2]
+    M = T.shape[1] - w + 1
+    keys = np.empty((m * m, M, D), dtype=np.uint64)
+    for f in range(D):
+        hl, _ = hash_values(T, w, Al, Ul, r, f)                 # (M, m, K/2)
+        hr, _ = hash_values(T, w, Ar, Ur, r, f)
+        for jj in range(m * m):
+            lf, rf = divmod(jj, m)
+            h = np.empty((M, 2 * half), dtype=np.int16)
+            h[:, 0::2] = hl[:, lf, :]
+            h[:, 1::2] = hr[:, rf, :]
+            keys[jj, :, f] = pack_keys(h)
+    return keys
+
+
+def momenti_tensored(T: np.ndarray, w: int, d: int, k: int, delta: float, Al: np.ndarray,
+                     Ul: np.ndarray, Ar: np.ndarray, Ur: np.ndarray, r: float,
+                     excl: int | None = None):
+    """Algorithm 1 on tensored keys (``tensored_keys``, L = m^2
+    repetitions, K = 2 x the values per function) with STOP on the
+    re-derived tensoring bound (``tensoring_failure_bound`` of
+    p = P(dist_max)^d); the exact top-k when STOP never holds.  Returns
+    the same record as ``momenti``."""
+    T = np.asarray(T, dtype=np.float64)
+    D = T.shape[0]
+    m, K = Al.shape[1], 2 * Al.shape[2]
+    L = m * m
+    eps = exclusion_zone(w, excl)
+    keys = tensored_keys(T, w, Al, Ul, Ar, Ur, r)
+    Z = [znorm_windows(T[f], w) for f in range(D)]
+
+    def bound(dist_max, i, j):
+        return tensoring_failure_bound(collision_probability(dist_max, r) ** d, i, j, K, L)
+
+    top, stop, n_dist, pool = momenti_traverse(
+        keys, lambda a, b: _pair_distances(Z, a, b), d, k, delta, r, eps, K, bound=bound)
+    if stop is not None:
+        i, j = stop
+        return {"motifs": top, "stop": stop, "n_dist": n_dist,
+                "fail_bound": bound(top[-1][4], i, j), "pool": pool}
+    return {"motifs": exact_topk_auto(T, w, d, k, excl), "stop": None,
+            "n_dist": n_dist, "fail_bound": 0.0, "pool": pool}

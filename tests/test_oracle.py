@@ -452,3 +452,48 @@ def test_printed_tensoring_lemma_is_not_a_bound():
     for j in (4, 8, 12):
         printed = (1 - p ** 4) ** (j // m) * (1 - p ** 4) ** (j % m)
         assert O.tensoring_failure_bound(p, K, j, K, L) > printed + 0.04
+
+
+def _tensored_draws(D, m, K, w, seed):
+    Al, Ul = synth.hash_draws(D, m, K // 2, w, seed)
+    Ar, Ur = synth.hash_draws(D, m, K // 2, w, seed + 1000)
+    return Al, Ul, Ar, Ur
+
+
+def test_tensored_keys_are_keys_of_interleaved_functions():
+    # repetition j' = (l, r) is the plain composite hash of the functions
+    # whose values alternate left l and right r
+    wl = synth.tiny(12, 600, 2, 40, 1, n_motifs=0)
+    m, K = 3, 8
+    Al, Ul, Ar, Ur = _tensored_draws(wl.D, m, K, wl.w, 12)
+    r = O.estimate_r(wl.series, wl.w, Al)
+    A = np.empty((wl.D, m * m, K, wl.w), np.float32)
+    U = np.empty((wl.D, m * m, K), np.float32)
+    for jj in range(m * m):
+        lf, rf = divmod(jj, m)
+        A[:, jj, 0::2], A[:, jj, 1::2] = Al[:, lf], Ar[:, rf]
+        U[:, jj, 0::2], U[:, jj, 1::2] = Ul[:, lf], Ur[:, rf]
+    plain, t = O.hash_all(wl.series, wl.w, A, U, r)
+    tens = O.tensored_keys(wl.series, wl.w, Al, Ul, Ar, Ur, r)
+    # equal except where a value sits within rounding of a bucket edge
+    near = (np.abs(t - np.round(t)) < 1e-9).any(axis=-1).transpose(2, 1, 0)   # (L, M, D)
+    assert np.array_equal(tens[~near], plain[~near]) and near.mean() < 1e-3
+
+
+def test_tensored_search_stops_on_its_bound_or_is_exact():
+    # close planted motifs (noise 0.01), m = 15 (L = 225), delta = 0.2:
+    # STOP holds on these seeds; the result is the exact top-k either way
+    stopped = 0
+    for seed in (1, 2, 3):
+        wl = synth.tiny(seed, 1500, 3, 50, 2, k=2, n_motifs=2, noise=0.01)
+        Al, Ul, Ar, Ur = _tensored_draws(wl.D, 15, 8, wl.w, seed)
+        r = O.estimate_r(wl.series, wl.w, Al)
+        res = O.momenti_tensored(wl.series, wl.w, wl.d, wl.k, 0.2, Al, Ul, Ar, Ur, r)
+        ex = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+        assert [(m[1], m[2]) for m in res["motifs"]] == [(m[1], m[2]) for m in ex]
+        if res["stop"] is not None:
+            stopped += 1
+            i, j = res["stop"]
+            p = O.collision_probability(res["motifs"][-1][4], r) ** wl.d
+            assert res["fail_bound"] == O.tensoring_failure_bound(p, i, j, 8, 225) <= 0.2
+    assert stopped >= 2
