@@ -285,6 +285,17 @@ double momenti_collision_probability(double R, double r);
 double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, int32_t L,
                              int32_t d, double r);
 
+/* Tensoring (Section 6.1), its miss-probability bound re-derived: the
+ * probability that a pair whose hash values collide independently with
+ * probability p (pass P(dist_max)^d) was missed after j repetitions at
+ * prefix length i, when the L = m^2 repetitions pair m left and m right
+ * functions of K/2 values each (repetition j', 0-based: left j' div m,
+ * right j' mod m) and keys interleave their values, left first; for i < K
+ * every repetition has also been seen at length i + 1.  Exact under that
+ * model, so an upper bound for any p at most the true one.  NaN unless
+ * 0 <= p <= 1, K even >= 2, 1 <= i <= K, L a square, 0 <= j <= L. */
+double momenti_tensoring_failure_bound(double p, int32_t i, int32_t j, int32_t K, int32_t L);
+
 /* TOP of Algorithm 1 over given candidates, through the pool momenti_topk
  * keeps: the m pairs (a[q] < b[q]) with distances dd[q] (float, as the
  * device records them) enter in order, batch at a time, as verified pairs

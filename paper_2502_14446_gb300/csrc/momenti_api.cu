@@ -1470,6 +1470,70 @@ double momenti_failure_bound(double dist_max, int32_t i, int32_t j, int32_t K, i
   return failure_bound(dist_max, i, j, K, L, d, r);
 }
 
+// Miss probability of a pair under tensoring after j repetitions at prefix
+// length i (Section 6.1, bound re-derived): L = m^2 repetitions, repetition
+// j' (0-based) pairs left function j' div m with right function j' mod m,
+// keys interleave their K/2 values (left first), so length t needs the
+// left prefix ceil(t/2) and the right prefix floor(t/2) to collide.  Each
+// value collides independently with probability p, so a function's
+// collision depth G has P(G >= u) = p^u.  Rows (left functions) and
+// columns (right functions) fall into groups visited alike; the largest
+// depth class of each group decides the miss, and the sum runs over them.
+double momenti_tensoring_failure_bound(double p, int32_t i, int32_t j, int32_t K, int32_t L) {
+  if (!(p >= 0.0 && p <= 1.0) || K < 2 || K % 2 || i < 1 || i > K || L < 1 || j < 0 || j > L)
+    return std::nan("");
+  int32_t m = 0;
+  while (int64_t(m + 1) * (m + 1) <= L) ++m;
+  if (m * m != L) return std::nan("");
+  const bool top = i == K;
+  const int ug0 = (i + 1) / 2, ug1 = top ? ug0 : (i + 2) / 2;   // ceil(i/2), ceil((i+1)/2)
+  const int uh0 = i / 2, uh1 = top ? uh0 : (i + 1) / 2;         // floor(i/2), floor((i+1)/2)
+  // largest class among n iid functions: -1 (none) or 0, 1, 2
+  auto max_class = [&](int u0, int u1, int64_t n, double out[4]) {
+    const double s1 = std::pow(p, u0), s2 = std::pow(p, u1);
+    const double cdf[3] = {1.0 - s1, 1.0 - s2, 1.0};
+    for (int c = 0; c < 4; ++c) out[c] = 0.0;
+    if (n == 0) {
+      out[0] = 1.0;                                                // class -1 at index 0
+      return;
+    }
+    double prev = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double cur = std::pow(std::min(1.0, cdf[c]), double(n));
+      out[c + 1] = cur - prev;
+      prev = cur;
+    }
+  };
+  const int64_t a = j / m, b = j % m;
+  const int64_t rows[3] = {a, a < m ? 1 : 0, std::max<int64_t>(0, m - a - 1)};
+  const int64_t cols[2] = {b, m - b};
+  // (row group, column group, 0: length i / 1: length i + 1)
+  int visits[6][3] = {{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {1, 1, 1}, {2, 0, 1}, {2, 1, 1}};
+  const int nv = top ? 3 : 6;
+  double g[3][4], hc[2][4];
+  for (int q = 0; q < 3; ++q) max_class(ug0, ug1, rows[q], g[q]);
+  for (int q = 0; q < 2; ++q) max_class(uh0, uh1, cols[q], hc[q]);
+  double miss = 0.0;
+  int gm[3], hm[2];
+  for (gm[0] = 0; gm[0] < 4; ++gm[0])
+    for (gm[1] = 0; gm[1] < 4; ++gm[1])
+      for (gm[2] = 0; gm[2] < 4; ++gm[2])
+        for (hm[0] = 0; hm[0] < 4; ++hm[0])
+          for (hm[1] = 0; hm[1] < 4; ++hm[1]) {
+            const double pr = g[0][gm[0]] * g[1][gm[1]] * g[2][gm[2]] * hc[0][hm[0]] * hc[1][hm[1]];
+            if (pr == 0.0) continue;
+            bool hit = false;
+            for (int v = 0; v < nv && !hit; ++v) {
+              // stored index = class + 1; a visit at length i needs class >= 1
+              // on both sides, at length i + 1 class 2
+              const int need = 2 + visits[v][2];
+              hit = gm[visits[v][0]] >= need && hm[visits[v][1]] >= need;
+            }
+            if (!hit) miss += pr;
+          }
+  return miss;
+}
+
 static int top_select_impl(const float* dd, const int64_t* a, const int64_t* b, int64_t m,
                            int32_t k, int64_t eps, int64_t batch, int64_t* idx, int32_t* n_out) {
   if (m < 0 || k < 1 || eps < 0 || batch < 1 || !idx || !n_out) return MOMENTI_ERR_ARG;

@@ -34,6 +34,7 @@ EXPORTS = (
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
     "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
     "momenti_collision_probability", "momenti_failure_bound", "momenti_top_select",
+    "momenti_tensoring_failure_bound",
 )
 
 
@@ -97,6 +98,8 @@ def _load():
                                                C.c_int32, C.c_int32, C.c_double]),
         "momenti_top_select": (C.c_int, [vp, vp, vp, C.c_int64, C.c_int32, C.c_int64,
                                          C.c_int64, vp, P(C.c_int32)]),
+        "momenti_tensoring_failure_bound": (C.c_double, [C.c_double, C.c_int32, C.c_int32,
+                                                         C.c_int32, C.c_int32]),
         "momenti_topk_batch": (C.c_int, [C.c_int32, P(momenti_params), P(vp), P(C.c_int32),
                                          P(C.c_int64), P(C.c_int32), C.c_int32, C.c_int32,
                                          P(momenti_motif), C.c_int32, P(C.c_int32),
@@ -157,6 +160,11 @@ def collision_probability(R: float, r: float) -> float:
 def failure_bound(dist_max: float, i: int, j: int, K: int, L: int, d: int, r: float) -> float:
     """The bound of Lemma stop that Algorithm 2 compares with delta (i, j 1-based)."""
     return float(lib.momenti_failure_bound(dist_max, i, j, K, L, d, r))
+
+
+def tensoring_failure_bound(p: float, i: int, j: int, K: int, L: int) -> float:
+    """The re-derived miss bound of tensoring (L a square, K even)."""
+    return float(lib.momenti_tensoring_failure_bound(p, i, j, K, L))
 
 
 def top_select(dd, a, b, k: int, eps: int, batch: int = 1 << 30):

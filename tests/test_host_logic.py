@@ -115,3 +115,16 @@ def test_top_select_through_pool_truncation(mom):
     ref = O.greedy_topk([(float(dd[q]), int(a[q]), int(b[q]), int(q)) for q in order], k, eps)
     assert len(ref) == k
     assert mom.top_select(dd, a, b, k, eps, 1 << 20) == [c[3] for c in ref]
+
+
+def test_tensoring_bound_matches_the_oracle(mom):
+    for p in (0.0, 0.3, 0.5, 0.8, 1.0):
+        for K, L in ((8, 16), (8, 225), (4, 9), (2, 4)):
+            for i in range(1, K + 1):
+                for j in sorted({0, 1, L // 3, L // 2, L - 1, L}):
+                    got = mom.tensoring_failure_bound(p, i, j, K, L)
+                    ref = O.tensoring_failure_bound(p, i, j, K, L)
+                    assert got == pytest.approx(ref, rel=1e-12, abs=1e-14), (p, i, j, K, L)
+    for bad in ((0.5, 4, 1, 8, 200), (0.5, 0, 1, 8, 16), (0.5, 9, 1, 8, 16), (1.5, 4, 1, 8, 16),
+                (0.5, 4, 17, 8, 16), (0.5, 3, 1, 7, 16)):
+        assert math.isnan(mom.tensoring_failure_bound(*bad)), bad
