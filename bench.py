@@ -59,8 +59,10 @@ def measured_traffic(kernel):
 
 
 # dominant kernels and their algorithmic work per launch
-DOMINANT = ("proj_hash_tc", "collide", "subbucket", "sort_scatter", "allpairs", "proj_hash_fp32",
+DOMINANT = ("proj_hash_tc", "collide", "subbucket", "sort_*", "allpairs", "proj_hash_fp32",
             "verify_events")
+# kernels whose roofline is reported beside the dominant one
+SECONDARY = ("sort_*", "proj_hash_tc", "allpairs")
 
 
 def parse():
@@ -170,7 +172,13 @@ def params_for(mom, wl, precision):
                               K=8, L=200, precision=precision)
 
 
-def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
+def sm_count(device=None) -> int:
+    """Streaming multiprocessors of the GPU (152 on a GB300)."""
+    import torch
+    return torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count
+
+
+def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
     """Roofline object of one kernel from its live CUDA-event time over the
     timed steps: achieved = algorithmic work of the timed launches / their
     device time.  Algorithmic work per unit (per step, from the step's own
@@ -181,20 +189,22 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
       allpairs        18 flop per pair and dim: the diagonal recurrence of
                       the centred dot product and both window sums (10) and
                       the Pearson threshold test (8)
-      sort_scatter    24 bytes per index entry per 8-bit pass (K passes)
+      sort_*          20 bytes per index entry (window, dim, repetition):
+                      its 8-byte key read, the sorted 12-byte (key, window)
+                      written; every kernel of the index sort together
     """
     if not k_n or k_ms <= 0:
         return None
     M, D, L, K, w = info["M"], info["D"], info["L"], info["K"], wl.w
     secs = k_ms / 1e3
-    sm_peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    sm_peak = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    sm_src = f"{sms} SMs x 128 FP32 lanes x 2 flop x max SM clock"
     if kernel in ("proj_hash_tc", "proj_hash_fp32"):
         work = 2.0 * M * D * L * K * w * steps
         bound, unit = ("tensor", "TFLOP/s") if kernel == "proj_hash_tc" else ("alu", "TFLOP/s")
         achieved = work / secs / 1e12
         peak = pk["tflops_sustained"] if bound == "tensor" else sm_peak
-        src = (pk["src"] + " sustained bf16 (fp16 same rate)") if bound == "tensor" else \
-            "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        src = (pk["src"] + " sustained bf16 (fp16 same rate)") if bound == "tensor" else sm_src
     elif kernel == "verify_events":
         work = 8.0 * D * w * st["n_candidates"] * steps
         bound, unit = "hbm", "GB/s"
@@ -206,9 +216,9 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk):
         work = 18.0 * D * pairs * steps
         bound, unit = "alu", "TFLOP/s"
         achieved = work / secs / 1e12
-        peak, src = sm_peak, "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
-    elif kernel == "sort_scatter":
-        work = 24.0 * M * D * L * steps * K
+        peak, src = sm_peak, sm_src
+    elif kernel == "sort_*":
+        work = 20.0 * M * D * L * steps
         bound, unit = "hbm", "GB/s"
         achieved = work / secs / 1e9
         peak, src = pk["hbm_gbs"], pk["src"] + " copy bandwidth"

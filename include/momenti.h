@@ -256,6 +256,20 @@ int momenti_get_window_stats(momenti_handle* h, double* mu, double* sigma);
  * (k = 0 most significant) holds h_k + 128, bytes beyond K are zero. */
 int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys);
 
+/* The random numbers of the hash functions the index was built with
+ * (Eq. drp: a ~ N(0,1)^w, b = u r with u ~ U[0,1)), for the first L_used
+ * repetitions (momenti_get_info's L): a D*L*K*w floats, layout [f][j][k][t],
+ * as the projections use them (rounded to half precision); u D*L*K floats,
+ * layout [f][j][k].  Drawn on the device from seed (Philox4x32-10, Salmon
+ * et al. SC'11: counter {q, q >> 32, stream, 0}, key {seed, seed >> 32};
+ * element 4q + e of a takes Box-Muller on outputs (2h, 2h + 1) of counter q,
+ * stream 0, h = e / 2, cos for even e, sin for odd, with u1 = ((x >> 8) + 1)
+ * 2^-24 and u2 = (x >> 8) 2^-24; element 4q + e of u is output e of counter
+ * q, stream 1, as (x >> 8) 2^-24), or the values given to
+ * momenti_set_hash_params.  Either output may be NULL (not both).
+ * MOMENTI_ERR_STATE before momenti_hash_all. */
+int momenti_get_hash_draws(momenti_handle* h, float* a, float* u);
+
 /* Sorted index of (j, f): order[p] = window at rank p (ties by window
  * index), lcp[p] = hash values shared with rank p - 1 (lcp[0] = 0). */
 int momenti_get_index(momenti_handle* h, int32_t j, int32_t f, uint32_t* order, uint8_t* lcp);
@@ -335,13 +349,19 @@ int momenti_top_select(const float* dd, const int64_t* a, const int64_t* b, int6
  * It allocates nothing: its scratch is a fixed array inside the library
  * (about 6.4 MB per device that loads the library, held until the process
  * exits).  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the array and
- * leaves the last call's contents in it; calls whose work overlaps on the
- * GPU race on it, so serialise them (one stream, or events).
+ * (cudaGetSymbolAddress, with that device current) and keeps it with the
+ * id of the current CUDA context; a call made in another context (after
+ * cudaDeviceReset, for instance, which invalidates the kept address) looks
+ * it up again.  Make the first call on a device, and the first after a
+ * reset, before any stream capture.  Every call on a device shares the
+ * array and leaves the last call's contents in it; calls whose work
+ * overlaps on the GPU race on it, so serialise them (one stream, or
+ * events).
  * Errors: MOMENTI_ERR_OVERFLOW if m > MOMENTI_NOALLOC_MAX_KEYS;
  * MOMENTI_ERR_ARG for NULL arrays (m > 0), m < 0 or K outside 1..8;
- * MOMENTI_ERR_CUDA if the address lookup or a launch fails. */
+ * MOMENTI_ERR_CUDA if a CUDA error is already pending in the calling
+ * thread (left by earlier work; it is not cleared and nothing is
+ * launched), or if the address lookup or a launch fails. */
 int momenti_index_sort_noalloc(const uint64_t* keys, int64_t m, int32_t K, uint32_t* order,
                                uint8_t* lcp, void* stream);
 
@@ -353,10 +373,12 @@ uint64_t momenti_launch_count(void);
 
 /* Starts timing every launch of the kernel called name with CUDA events on
  * the launching stream, and clears the accumulated time; NULL stops timing.
+ * A name ending in '*' selects every kernel whose name starts with the part
+ * before it (for example "sort_*": all kernels of the index sort).
  * Kernel names: split_f32, split_f64, point_major, window_stats,
  * stats_pm, mean16, r_sample, draw, layout_hash, layout_boff,
- * proj_hash_fp32, proj_hash_tc, rehash, sort_hist, sort_scan,
- * sort_scatter, sort_finish, chunk_agg, chunk_scan, scan_local, scan_top,
+ * proj_hash_fp32, proj_hash_tc, rehash, sort_init, sort_hist, sort_scan,
+ * sort_scatter, sort_local, chunk_agg, chunk_scan, scan_local, scan_top,
  * scan_add, collide, bucket_jobs, subbucket, subwarp, hs_clear,
  * verify_events, verify_pairs, allpairs, select_pairs. */
 int momenti_time_kernel(const char* name);

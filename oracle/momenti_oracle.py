@@ -342,6 +342,8 @@ def tensoring_failure_bound(p: float, i: int, j: int, K: int, L: int) -> float:
     of each group matters: the result sums over those classes exactly.
     The miss probability decreases as p grows, so a lower bound on p gives
     an upper bound.  Needs L = m^2, K even, 1 <= i <= K, 0 <= j <= L."""
+    if L < 1:
+        raise ValueError("tensoring needs L = m^2 >= 1")
     m = math.isqrt(L)
     if m * m != L or K % 2 or not 1 <= i <= K or not 0 <= j <= L:
         raise ValueError("tensoring needs L = m^2, K even, 1 <= i <= K, 0 <= j <= L")

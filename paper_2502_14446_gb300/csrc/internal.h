@@ -63,6 +63,9 @@ void prof_end(const char* name, cudaStream_t s);
 // device.  The limit only ever rises (under a lock), so a launch on one
 // thread never sees it lowered by another thread's smaller request.
 cudaError_t allow_smem(const void* func, size_t bytes);
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// queried once per device); grids are sized in multiples of it.
+int sm_count();
 #define MOMENTI_LAUNCH(name, stream, ...)      \
   do {                                         \
     ::momenti::prof_begin(name, stream);       \
@@ -106,14 +109,71 @@ cudaError_t launch_rehash_fp32(const Index& ix, const uint64_t* flags, const uin
                                uint32_t flag_cap, cudaStream_t s);
 
 // ---- k_sort.cu ----------------------------------------------------------
-struct SortScratch {
-  uint64_t* k0 = nullptr; uint64_t* k1 = nullptr;
-  uint32_t* v0 = nullptr; uint32_t* v1 = nullptr;
-  uint32_t* hist = nullptr;    // [segs][256][tiles]
-  int64_t cap_entries = 0;     // segs * M capacity of k0/k1/v0/v1
-  int64_t hist_entries = 0;
+// Largest chunk one CTA sorts in shared memory (the most-significant-digit
+// partition goes one hash value deeper for larger buckets).
+constexpr int kSortLocalMax = 4096;
+// A range of one segment that one level partitions by one hash value.
+struct SortItem {
+  uint32_t seg;      // segment (repetition-major within the batch)
+  uint32_t start;    // first rank of the range in its segment
+  uint32_t size;
+  uint32_t hist0;    // first histogram tile of the range
+  uint32_t lcp0;     // hash values its first entry shares with its predecessor
+  uint32_t pad[3];
 };
-int64_t sort_hist_entries(int64_t M, int segs);
+// A range of one segment sorted completely in shared memory (or, equal keys,
+// already in order).
+struct SortChunk {
+  uint32_t seg, start, size;
+  uint8_t lcp0, buf, equal, pad;
+};
+struct SortCaps {
+  int64_t item_cap = 0, tile_cap = 0, chunk_cap = 0;
+};
+struct SortScratch {
+  uint64_t* k0 = nullptr; uint64_t* k1 = nullptr;   // [segs][M] ping-pong keys
+  uint32_t* v0 = nullptr; uint32_t* v1 = nullptr;   // [segs][M] ping-pong windows
+  uint32_t* hist = nullptr;                         // [tiles][256] digit counts / offsets
+  SortItem* items[2] = {nullptr, nullptr};          // this level's and the next level's
+  uint64_t* tile_item[2] = {nullptr, nullptr};      // launch tile -> (tile in item << 32 | item)
+  SortChunk* chunks = nullptr;
+  uint32_t* cnt = nullptr;                          // 64 device counters
+  uint32_t* host_cnt = nullptr;   // pinned copy of the counters: levels sized by the host;
+                                  // nullptr: every level launched with fixed grids
+  SortCaps caps;
+  int64_t M = 0, cap_entries = 0;
+  int segs = 0;
+};
+constexpr int kSortTile = 2048;           // entries per partition tile
+// Capacities for segs segments of M entries: items of one level (buckets
+// above kSortLocalMax are disjoint), launch tiles of one level, chunks of
+// all levels together (greedy packing leaves at most two chunks per
+// kSortLocalMax entries, plus one per bucket boundary that a large bucket
+// or an item makes).
+constexpr SortCaps sort_caps(int64_t M, int segs) {
+  SortCaps c;
+  const int64_t entries = M * segs;
+  const int64_t tpm = (M + kSortTile - 1) / kSortTile;
+  const int64_t big = entries / kSortLocalMax + 1;
+  c.item_cap = int64_t(segs) > big ? int64_t(segs) : big;
+  const int64_t t0 = int64_t(segs) * tpm, t1 = entries / kSortTile + c.item_cap + 1;
+  c.tile_cap = t0 > t1 ? t0 : t1;
+  c.chunk_cap = 2 * int64_t(segs) + (2 + 2 * 8) * big + 16;
+  return c;
+}
+constexpr size_t sort_up256(size_t b) { return (b + 255) & ~size_t(255); }
+// Bytes of one region holding every scratch array for segs segments of M.
+constexpr size_t sort_scratch_bytes(int64_t M, int segs) {
+  const SortCaps c = sort_caps(M, segs);
+  const size_t e = size_t(M) * size_t(segs);
+  return 2 * sort_up256(e * 8) + 2 * sort_up256(e * 4) + sort_up256(size_t(c.tile_cap) * 256 * 4) +
+         2 * sort_up256(size_t(c.item_cap) * sizeof(SortItem)) +
+         2 * sort_up256(size_t(c.tile_cap) * 8) + sort_up256(size_t(c.chunk_cap) * sizeof(SortChunk)) +
+         sort_up256(64 * 4);
+}
+// The scratch arrays laid out in one region of sort_scratch_bytes(M, segs)
+// bytes (256-byte aligned); host_cnt is left null.
+SortScratch sort_scratch_carve(void* base, int64_t M, int segs);
 // Sort repetitions [j0, j1): all D segments of each, writing order/lcp.
 cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch& sc,
                              cudaStream_t s);

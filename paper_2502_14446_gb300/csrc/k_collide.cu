@@ -766,7 +766,7 @@ template <bool PLAIN, int I>
 static cudaError_t run_collide(const CollideArgs& g, size_t smem, cudaStream_t s) {
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_collide<PLAIN, I>), smem);
   if (e != cudaSuccess) return e;
-  MOMENTI_LAUNCH("collide", s, k_collide<PLAIN, I><<<152 * 8, 128, smem, s>>>(g));
+  MOMENTI_LAUNCH("collide", s, k_collide<PLAIN, I><<<sm_count() * 8, 128, smem, s>>>(g));
   return cudaGetLastError();
 }
 
@@ -794,7 +794,7 @@ cudaError_t launch_bucket_jobs(const Index& ix, int i, int j0, int j1, int d, Bu
   const int segs = (j1 - j0) * ix.D;
   Seg sg{ix.M, ix.D, j0, int((ix.M + 31) / 32)};
   int64_t gx = (ix.M + 255) / 256;
-  const int64_t per_seg = std::max<int64_t>(1, (152 * 16 + segs - 1) / segs);
+  const int64_t per_seg = std::max<int64_t>(1, (sm_count() * 16 + segs - 1) / segs);
   if (gx > per_seg) gx = per_seg;
   dim3 grid{unsigned(gx), unsigned(segs), 1u};
   MOMENTI_LAUNCH("bucket_jobs", s, k_bucket_jobs<<<grid, 256, 0, s>>>(ix.lcp, sg, segs, i, d, jobs, job_cap, counts));
@@ -819,10 +819,10 @@ static cudaError_t run_subbucket(const SubArgs& g, size_t smem, cudaStream_t s) 
   int per_sm = int((size_t(200) * 1024) / smem);
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 8) per_sm = 8;
-  MOMENTI_LAUNCH("subbucket", s, k_subbucket<NW, I><<<152 * per_sm, 256, smem, s>>>(g));
-  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 32><<<152 * 8, 256, 0, s>>>(g, 1));
-  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 8><<<152 * 8, 256, 0, s>>>(g, 2));
-  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 4><<<152 * 8, 256, 0, s>>>(g, 3));
+  MOMENTI_LAUNCH("subbucket", s, k_subbucket<NW, I><<<sm_count() * per_sm, 256, smem, s>>>(g));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 32><<<sm_count() * 8, 256, 0, s>>>(g, 1));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 8><<<sm_count() * 8, 256, 0, s>>>(g, 2));
+  MOMENTI_LAUNCH("subwarp", s, k_subwarp<NW, I, 4><<<sm_count() * 8, 256, 0, s>>>(g, 3));
   return cudaGetLastError();
 }
 
@@ -844,7 +844,7 @@ cudaError_t launch_subbucket(const Index& ix, int i, int j0, int j1, int d, cons
 }
 
 cudaError_t launch_hashset_clear(const HashSet& hs, cudaStream_t s) {
-  MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<152 * 8, 256, 0, s>>>(hs.keys, hs.cap));
+  MOMENTI_LAUNCH("hs_clear", s, k_hs_clear<<<sm_count() * 8, 256, 0, s>>>(hs.keys, hs.cap));
   return cudaGetLastError();
 }
 

@@ -494,7 +494,7 @@ cudaError_t launch_proj_hash_tc(const Index& ix, int j0, int j1, uint64_t* flags
 
 cudaError_t launch_rehash_fp32(const Index& ix, const uint64_t* flags, const uint32_t* flag_count,
                                uint32_t flag_cap, cudaStream_t s) {
-  MOMENTI_LAUNCH("rehash", s, k_rehash<<<152 * 8, 256, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.mu_hi, ix.mu_lo,
+  MOMENTI_LAUNCH("rehash", s, k_rehash<<<sm_count() * 8, 256, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.mu_hi, ix.mu_lo,
                                    ix.inv_sig, ix.a32, ix.boff, ix.inv_r, ix.n, ix.M, ix.D, ix.w,
                                    ix.Wp, ix.L * kRepStride, flags, flag_count, flag_cap,
                                    reinterpret_cast<unsigned long long*>(ix.keys)));

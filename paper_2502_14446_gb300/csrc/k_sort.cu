@@ -2,16 +2,31 @@
 // the windows ordered lexicographically by their K-value hash strings, so
 // that every prefix length i groups colliding windows into contiguous runs.
 //
-// A batched, stable least-significant-digit radix sort over the K key bytes
-// (8-bit digits, last concatenation first), one segment per (j, f), all
-// segments of a batch of repetitions in the same launches.  Each pass is
-// three kernels: per-tile digit histograms, a per-segment scan of
-// (digit, tile) counts, and a stable scatter that ranks equal digits with
-// warp-level match masks and writes each tile in digit order through
-// shared memory, so that equal digits leave as contiguous runs.  The final
-// kernel writes the sorted window order
-// and, per rank, the number of hash values shared with the previous rank
-// (the longest common prefix, 0..K), which is all the traversal needs.
+// A most-significant-digit radix partition followed by shared-memory
+// sorts.  Level t (t = 0, 1, ...) partitions ranges ("items") stably by
+// hash value t (one byte of the big-endian composite key); a partition
+// never moves an entry out of its item, so every entry lands in its final
+// position's bucket.  Buckets of at most kLocalMax entries are packed, in
+// order, into chunks that one CTA then sorts completely in shared memory
+// (a stable least-significant-digit sort over the bytes that vary inside
+// the chunk); larger buckets become the items of level t + 1.  After level
+// K - 1 every bucket holds equal keys and is already in order.  On the
+// hash strings of z-normalised windows one level usually suffices: the
+// largest bucket of the first hash value holds a few percent of the
+// windows.
+//
+// Each level is three kernels: per-tile digit histograms, a per-item scan
+// of (digit, tile) counts that also classifies the buckets (chunks for the
+// shared-memory sort, items for the next level), and a stable scatter that
+// ranks equal digits with warp match masks and writes each tile in digit
+// order through shared memory.  The final kernel writes, per rank, the
+// sorted window and the number of hash values shared with the previous
+// rank (the longest common prefix, 0..K), which is all the traversal needs.
+//
+// Every kernel reads its work counts from device counters (grid-stride
+// loops), so the levels can run without the host: the index build reads
+// the counts after each level to size the next launch exactly, the
+// allocation-free entry point launches all K levels with fixed grids.
 #include "internal.h"
 
 #include <algorithm>
@@ -22,160 +37,392 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 8;                      // per thread
-constexpr int kTile = kThreads * kItems;       // 2048 entries per CTA
+constexpr int kTile = kSortTile;               // entries per partition tile
+static_assert(kTile == kThreads * kItems, "partition tile");
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSpan = kTile / kWarps;      // 256 entries per warp
 constexpr int kRounds = kWarpSpan / 32;        // 8
 
-struct Src {
-  // pass 0 reads keys [j][a][f] and the implicit value a; later passes read
-  // the ping-pong buffers [seg][M]
+constexpr int kLocalThreads = 256;
+constexpr int kLocalWarps = kLocalThreads / 32;
+constexpr int kLocalRounds = kSortLocalMax / (kLocalWarps * 32);   // 16
+
+// counters: [2 t] items and [2 t + 1] tiles of level t (t = 0..8), then
+constexpr int kCntChunks = 20;   // chunks for the shared-memory sort
+constexpr int kCntWork = 21;     // next chunk to take
+constexpr int kCntOverflow = 22; // a capacity was exceeded
+
+struct Level {
+  // level 0 reads keys [j][a][f] and the implicit value a; later levels
+  // read the ping-pong buffers [seg][M]
   const uint64_t* keys;
   const uint64_t* kin;
   const uint32_t* vin;
+  uint64_t* kout;
+  uint32_t* vout;
   int64_t M;
-  int D, j0;
-  bool first;
-  __device__ __forceinline__ uint64_t load_key(int seg, int64_t p) const {
-    if (first) {
-      int j = j0 + seg / D, f = seg - (seg / D) * D;
+  int D, j0, t, K, segs;
+  const SortItem* items;
+  SortItem* items_next;
+  const uint64_t* tile_item;
+  uint64_t* tile_next;
+  uint32_t* hist;
+  SortChunk* chunks;
+  uint32_t* cnt;
+  uint32_t item_cap, tile_cap, chunk_cap;
+  __device__ __forceinline__ uint64_t load_key(uint32_t seg, int64_t p) const {
+    if (t == 0) {
+      const int j = j0 + int(seg) / D, f = int(seg) - (int(seg) / D) * D;
       return keys[(int64_t(j) * M + p) * D + f];
     }
     return kin[int64_t(seg) * M + p];
   }
-  __device__ __forceinline__ void load(int seg, int64_t p, uint64_t& k, uint32_t& v) const {
-    if (first) {
-      int j = j0 + seg / D, f = seg - (seg / D) * D;
-      k = keys[(int64_t(j) * M + p) * D + f];
+  __device__ __forceinline__ void load(uint32_t seg, int64_t p, uint64_t& k, uint32_t& v) const {
+    if (t == 0) {
+      k = load_key(seg, p);
       v = uint32_t(p);
     } else {
       k = kin[int64_t(seg) * M + p];
       v = vin[int64_t(seg) * M + p];
     }
   }
+  __device__ __forceinline__ uint32_t digit(uint64_t k) const {
+    return uint32_t(k >> (56 - 8 * t)) & 255u;
+  }
+  // the item of a launch tile, false for an entry that is not a valid tile of
+  // a valid item (only after an overflow; nothing outside the buffers is read)
+  __device__ __forceinline__ bool tile_of(uint32_t tile, SortItem& it, uint32_t& tt) const {
+    const uint64_t te = tile_item[tile];
+    const uint32_t ii = uint32_t(te);
+    tt = uint32_t(te >> 32);
+    if (ii >= min(cnt[2 * t], item_cap)) return false;
+    it = items[ii];
+    return it.seg < uint32_t(segs) && int64_t(it.start) + it.size <= M &&
+           tt < (it.size + kTile - 1) / kTile &&
+           int64_t(it.hist0) + (it.size + kTile - 1) / kTile <= int64_t(tile_cap);
+  }
 };
 
-__global__ void __launch_bounds__(kThreads)
-k_hist(Src src, int shift, int tiles, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[256];
-  // segments fastest: the first pass reads [j][a][0..D) rows of all dims together
-  const int seg = blockIdx.x, tile = blockIdx.y;
-  for (int d = threadIdx.x; d < 256; d += kThreads) h[d] = 0;
-  __syncthreads();
-  const int64_t base = int64_t(tile) * kTile;
-  uint64_t k[kItems];
-#pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int64_t p = base + r * kThreads + threadIdx.x;
-    k[r] = p < src.M ? src.load_key(seg, p) : 0ull;
-  }
-#pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int64_t p = base + r * kThreads + threadIdx.x;
-    if (p < src.M) atomicAdd(&h[uint32_t(k[r] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  uint32_t* out = hist + int64_t(seg) * 256 * tiles;
-  for (int d = threadIdx.x; d < 256; d += kThreads) out[int64_t(d) * tiles + tile] = h[d];
-}
+__device__ __forceinline__ uint32_t ntiles(uint32_t size) { return (size + kTile - 1) / kTile; }
 
-// Exclusive scan over the digit-major (digit, tile) counts of one segment.
-__global__ void __launch_bounds__(256) k_scan(int tiles, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t tot[256];
-  const int seg = blockIdx.x, d = threadIdx.x;
-  uint32_t* hs = hist + int64_t(seg) * 256 * tiles + int64_t(d) * tiles;
-  uint32_t s = 0;
-  int t0 = 0;
-  for (; t0 + 8 <= tiles; t0 += 8) {          // eight independent loads in flight
-    uint32_t c[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) c[q] = hs[t0 + q];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s += c[q];
+// Level 0: one item per segment.
+// Launch tiles run segment-fastest, so that the D segments of a repetition,
+// which read the same rows of the key array, are processed together.
+__global__ void k_sort_init(int segs, int64_t M, SortItem* items, uint64_t* tile_item,
+                            uint32_t* cnt) {
+  const uint32_t tpm = uint32_t((M + kTile - 1) / kTile);
+  const int64_t total = int64_t(segs) * tpm;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t seg = uint32_t(q % segs), tt = uint32_t(q / segs);
+    tile_item[q] = (uint64_t(tt) << 32) | seg;
+    if (tt == 0) items[seg] = SortItem{seg, 0u, uint32_t(M), seg * tpm, 0u, {0u, 0u, 0u}};
   }
-  for (; t0 < tiles; ++t0) s += hs[t0];
-  tot[d] = s;
-  __syncthreads();
-  // Hillis-Steele inclusive scan of the 256 digit totals
-  for (int off = 1; off < 256; off <<= 1) {
-    uint32_t v = d >= off ? tot[d - off] : 0u;
-    __syncthreads();
-    tot[d] += v;
-    __syncthreads();
-  }
-  uint32_t run = tot[d] - s;   // exclusive
-  int t1 = 0;
-  for (; t1 + 8 <= tiles; t1 += 8) {
-    uint32_t c[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) c[q] = hs[t1 + q];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      hs[t1 + q] = run;
-      run += c[q];
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    for (int c = threadIdx.x; c < 32; c += 32) cnt[c] = 0;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      cnt[0] = uint32_t(segs);
+      cnt[1] = uint32_t(total);
     }
   }
-  for (; t1 < tiles; ++t1) {
-    uint32_t c = hs[t1];
-    hs[t1] = run;
-    run += c;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_hist(Level lv) {
+  __shared__ uint32_t h[256];
+  // the next level's counts start from zero (its items are added by the
+  // scan kernel of this level, which runs after this one)
+  if (blockIdx.x == 0 && threadIdx.x < 2 && lv.t < 8) lv.cnt[2 * (lv.t + 1) + threadIdx.x] = 0;
+  const uint32_t nt = min(lv.cnt[2 * lv.t + 1], lv.tile_cap);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    SortItem it;
+    uint32_t tt;
+    if (!lv.tile_of(tile, it, tt)) continue;
+    for (int d = threadIdx.x; d < 256; d += kThreads) h[d] = 0;
+    __syncthreads();
+    const int64_t base = int64_t(it.start) + int64_t(tt) * kTile;
+    const int64_t end = int64_t(it.start) + it.size;
+    uint64_t k[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t p = base + r * kThreads + threadIdx.x;
+      k[r] = p < end ? lv.load_key(it.seg, p) : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t p = base + r * kThreads + threadIdx.x;
+      if (p < end) atomicAdd(&h[lv.digit(k[r])], 1u);
+    }
+    __syncthreads();
+    const uint32_t nti = ntiles(it.size);
+    uint32_t* out = lv.hist + int64_t(it.hist0) * 256;
+    for (int d = threadIdx.x; d < 256; d += kThreads) out[int64_t(d) * nti + tt] = h[d];
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
-          uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+// Exclusive scan over the digit-major (digit, tile) counts of one item, then
+// the item's buckets become chunks (at most kSortLocalMax entries, packed in
+// order) or items of the next level.
+__global__ void __launch_bounds__(256) k_sort_scan(Level lv) {
+  __shared__ uint32_t tot[256], bstart[256];
+  const uint32_t ni = min(lv.cnt[2 * lv.t], lv.item_cap);
+  const int d = threadIdx.x;
+  for (uint32_t item = blockIdx.x; item < ni; item += gridDim.x) {
+    const SortItem it = lv.items[item];
+    const uint32_t tiles = ntiles(it.size);
+    if (it.seg >= uint32_t(lv.segs) || int64_t(it.start) + it.size > lv.M ||
+        int64_t(it.hist0) + tiles > int64_t(lv.tile_cap))
+      continue;                                   // only after an overflow
+    uint32_t* hs = lv.hist + int64_t(it.hist0) * 256 + int64_t(d) * tiles;
+    uint32_t s = 0;
+    uint32_t t0 = 0;
+    for (; t0 + 8 <= tiles; t0 += 8) {          // eight independent loads in flight
+      uint32_t c[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c[q] = hs[t0 + q];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += c[q];
+    }
+    for (; t0 < tiles; ++t0) s += hs[t0];
+    tot[d] = s;
+    bstart[d] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the 256 digit totals
+    for (int off = 1; off < 256; off <<= 1) {
+      uint32_t v = d >= off ? bstart[d - off] : 0u;
+      __syncthreads();
+      bstart[d] += v;
+      __syncthreads();
+    }
+    uint32_t run = bstart[d] - s;   // exclusive, relative to the item's start
+    __syncthreads();
+    bstart[d] = run;
+    uint32_t t1 = 0;
+    for (; t1 + 8 <= tiles; t1 += 8) {
+      uint32_t c[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c[q] = hs[t1 + q];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        hs[t1 + q] = run;
+        run += c[q];
+      }
+    }
+    for (; t1 < tiles; ++t1) {
+      uint32_t c = hs[t1];
+      hs[t1] = run;
+      run += c;
+    }
+    __syncthreads();
+    if (d == 0) {
+      // classification, in digit order: a bucket's first entry shares t
+      // hash values with its predecessor (the item's own first entry keeps
+      // the item's count)
+      const bool last_level = lv.t + 1 >= lv.K;
+      uint32_t c_start = 0, c_size = 0, c_lcp = 0;
+      bool open = false, first = true;
+      auto emit = [&](uint32_t st, uint32_t sz, uint32_t l0, uint32_t equal) {
+        const uint32_t slot = atomicAdd(&lv.cnt[kCntChunks], 1u);
+        if (slot < lv.chunk_cap) {
+          SortChunk ch;
+          ch.seg = it.seg;
+          ch.start = st;
+          ch.size = sz;
+          ch.lcp0 = uint8_t(l0);
+          ch.buf = uint8_t(lv.t & 1);
+          ch.equal = uint8_t(equal);
+          ch.pad = 0;
+          lv.chunks[slot] = ch;
+        } else {
+          lv.cnt[kCntOverflow] = 1u;
+        }
+      };
+      for (int g = 0; g < 256; ++g) {
+        const uint32_t sz = tot[g];
+        if (!sz) continue;
+        const uint32_t l0 = first ? it.lcp0 : uint32_t(lv.t);
+        first = false;
+        const uint32_t st = it.start + bstart[g];
+        if (sz > uint32_t(kSortLocalMax)) {
+          if (open) emit(c_start, c_size, c_lcp, 0u);
+          open = false;
+          if (last_level) {
+            emit(st, sz, l0, 1u);            // equal keys: already in order
+          } else {
+            const uint32_t nt = ntiles(sz);
+            const uint32_t slot = atomicAdd(&lv.cnt[2 * (lv.t + 1)], 1u);
+            const uint32_t tb = atomicAdd(&lv.cnt[2 * (lv.t + 1) + 1], nt);
+            if (slot < lv.item_cap && tb + nt <= lv.tile_cap) {
+              lv.items_next[slot] = SortItem{it.seg, st, sz, tb, l0, {0u, 0u, 0u}};
+              for (uint32_t q = 0; q < nt; ++q) lv.tile_next[tb + q] = (uint64_t(q) << 32) | slot;
+            } else {
+              lv.cnt[kCntOverflow] = 1u;
+            }
+          }
+        } else if (open && c_size + sz <= uint32_t(kSortLocalMax)) {
+          c_size += sz;
+        } else {
+          if (open) emit(c_start, c_size, c_lcp, 0u);
+          open = true;
+          c_start = st;
+          c_size = sz;
+          c_lcp = l0;
+        }
+      }
+      if (open) emit(c_start, c_size, c_lcp, 0u);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_scatter(Level lv) {
   __shared__ uint32_t wh[kWarps][256];
   __shared__ uint32_t loff[256];             // tile-local start of each digit
   __shared__ uint64_t sk[kTile];             // the tile in digit order
   __shared__ uint32_t sv[kTile];
-  const int seg = blockIdx.x, tile = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = threadIdx.x; q < kWarps * 256; q += kThreads) (&wh[0][0])[q] = 0;
-  __syncthreads();
-  const int64_t base = int64_t(tile) * kTile + int64_t(warp) * kWarpSpan;
   const uint32_t lt = (1u << lane) - 1u;
-  uint64_t key[kRounds];
-  uint32_t val[kRounds], dig[kRounds], loc[kRounds];
-  // all loads of the warp's span first (independent, in flight together)
+  const uint32_t nt = min(lv.cnt[2 * lv.t + 1], lv.tile_cap);
+  for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    SortItem it;
+    uint32_t tt;
+    if (!lv.tile_of(tile, it, tt)) continue;
+    for (int q = threadIdx.x; q < kWarps * 256; q += kThreads) (&wh[0][0])[q] = 0;
+    __syncthreads();
+    const int64_t end = int64_t(it.start) + it.size;
+    const int64_t base = int64_t(it.start) + int64_t(tt) * kTile + int64_t(warp) * kWarpSpan;
+    uint64_t key[kRounds];
+    uint32_t val[kRounds], dig[kRounds], loc[kRounds];
+    // all loads of the warp's span first (independent, in flight together)
 #pragma unroll
-  for (int r = 0; r < kRounds; ++r) {
-    const int64_t p = base + r * 32 + lane;
-    key[r] = 0;
-    val[r] = 0;
-    if (p < src.M) src.load(seg, p, key[r], val[r]);
+    for (int r = 0; r < kRounds; ++r) {
+      const int64_t p = base + r * 32 + lane;
+      key[r] = 0;
+      val[r] = 0;
+      if (p < end) lv.load(it.seg, p, key[r], val[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int64_t p = base + r * 32 + lane;
+      // out of range: a digit no valid entry has
+      const uint32_t dg = p < end ? lv.digit(key[r]) : 256u + lane;
+      dig[r] = dg;
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      const uint32_t rank = __popc(peers & lt);
+      const uint32_t cnt = __popc(peers);
+      uint32_t b = 0;
+      if (dg < 256u) b = wh[warp][dg];
+      __syncwarp();
+      if (dg < 256u && rank == 0) wh[warp][dg] = b + cnt;
+      __syncwarp();
+      loc[r] = b + rank;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += kThreads) {
+      uint32_t run = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wh[w][d];
+        wh[w][d] = run;
+        run += c;
+      }
+      loff[d] = run;                           // digit total, scanned below
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {                    // exclusive scan of the 256 totals
+      uint32_t v[8], run = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { v[q] = loff[lane * 8 + q]; run += v[q]; }
+      uint32_t incl = run;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      uint32_t b = incl - run;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { loff[lane * 8 + q] = b; b += v[q]; }
+    }
+    __syncthreads();
+    // the tile in digit order in shared memory (stable within each digit) ...
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      if (dig[r] < 256u) {
+        const uint32_t q = loff[dig[r]] + wh[warp][dig[r]] + loc[r];
+        sk[q] = key[r];
+        sv[q] = val[r];
+      }
+    }
+    __syncthreads();
+    // ... then written out in that order: runs of equal digits are contiguous
+    const uint32_t nti = ntiles(it.size);
+    const uint32_t* hs = lv.hist + int64_t(it.hist0) * 256;
+    const int64_t n_tile = min(int64_t(kTile), end - (int64_t(it.start) + int64_t(tt) * kTile));
+    const int64_t obase = int64_t(it.seg) * lv.M + it.start;
+    for (int q = threadIdx.x; q < n_tile; q += kThreads) {
+      const uint64_t k = sk[q];
+      const uint32_t d = lv.digit(k);
+      const uint32_t dst = hs[int64_t(d) * nti + tt] + (uint32_t(q) - loff[d]);
+      lv.kout[obase + dst] = k;
+      lv.vout[obase + dst] = sv[q];
+    }
+    __syncthreads();
   }
+}
+
+struct LocalArgs {
+  const uint64_t* k[2];
+  const uint32_t* v[2];
+  const SortChunk* chunks;
+  uint32_t* cnt;
+  uint32_t chunk_cap;
+  int64_t M;
+  int D, j0, K, segs;
+  uint64_t kmask;                 // the K leading bytes of a key
+  uint32_t* order;
+  uint8_t* lcp;
+};
+
+// Stable LSD pass of one byte over n entries in shared memory (src -> dst).
+__device__ __forceinline__ void local_pass(const uint64_t* sk, const uint32_t* sv, uint64_t* dk,
+                                           uint32_t* dv, int n, int shift, uint32_t (*wh)[256],
+                                           uint32_t* doff) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int q = threadIdx.x; q < kLocalWarps * 256; q += kLocalThreads) (&wh[0][0])[q] = 0;
+  __syncthreads();
+  const int span = ((n + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
+  const int w0 = warp * span;
+  uint32_t pk[kLocalRounds];            // digit | local rank << 9
 #pragma unroll
-  for (int r = 0; r < kRounds; ++r) {
-    const int64_t p = base + r * 32 + lane;
-    // out of range: a digit no valid item has
-    const uint32_t dg = p < src.M ? uint32_t(key[r] >> shift) & 255u : 256u + lane;
-    dig[r] = dg;
-    uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    uint32_t rank = __popc(peers & lt);
-    uint32_t cnt = __popc(peers);
+  for (int r = 0; r < kLocalRounds; ++r) {
+    const int q = w0 + r * 32 + lane;
+    const bool in = r * 32 < span && q < n;
+    const uint32_t dg = in ? uint32_t(sk[q] >> shift) & 255u : 256u + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    const uint32_t rank = __popc(peers & lt);
     uint32_t b = 0;
     if (dg < 256u) b = wh[warp][dg];
     __syncwarp();
-    if (dg < 256u && rank == 0) wh[warp][dg] = b + cnt;
+    if (dg < 256u && rank == 0) wh[warp][dg] = b + __popc(peers);
     __syncwarp();
-    loc[r] = b + rank;
+    pk[r] = dg | ((b + rank) << 9);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += kThreads) {
+  {
+    const int d = threadIdx.x;           // kLocalThreads == 256: one digit each
     uint32_t run = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      uint32_t c = wh[w][d];
+    for (int w = 0; w < kLocalWarps; ++w) {
+      const uint32_t c = wh[w][d];
       wh[w][d] = run;
       run += c;
     }
-    loff[d] = run;                           // digit total, scanned below
+    doff[d] = run;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {                    // exclusive scan of the 256 totals
+  if (threadIdx.x < 32) {
     uint32_t v[8], run = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { v[q] = loff[lane * 8 + q]; run += v[q]; }
+    for (int q = 0; q < 8; ++q) { v[q] = doff[lane * 8 + q]; run += v[q]; }
     uint32_t incl = run;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
@@ -183,81 +430,212 @@ k_scatter(Src src, int shift, int tiles, const uint32_t* __restrict__ hist,
     }
     uint32_t b = incl - run;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { loff[lane * 8 + q] = b; b += v[q]; }
+    for (int q = 0; q < 8; ++q) { doff[lane * 8 + q] = b; b += v[q]; }
   }
   __syncthreads();
-  // the tile in digit order in shared memory (stable within each digit) ...
 #pragma unroll
-  for (int r = 0; r < kRounds; ++r) {
-    if (dig[r] < 256u) {
-      const uint32_t q = loff[dig[r]] + wh[warp][dig[r]] + loc[r];
-      sk[q] = key[r];
-      sv[q] = val[r];
+  for (int r = 0; r < kLocalRounds; ++r) {
+    const uint32_t dg = pk[r] & 511u;
+    if (dg < 256u) {
+      const int q = w0 + r * 32 + lane;
+      const uint32_t dst = doff[dg] + wh[warp][dg] + (pk[r] >> 9);
+      dk[dst] = sk[q];
+      dv[dst] = sv[q];
     }
   }
   __syncthreads();
-  // ... then written out in that order: runs of equal digits are contiguous
-  const uint32_t* hs = hist + int64_t(seg) * 256 * tiles;
-  const int64_t n_tile = min(int64_t(kTile), src.M - int64_t(tile) * kTile);
-  for (int q = threadIdx.x; q < n_tile; q += kThreads) {
-    const uint64_t k = sk[q];
-    const uint32_t d = uint32_t(k >> shift) & 255u;
-    const uint32_t dst = hs[int64_t(d) * tiles + tile] + (uint32_t(q) - loff[d]);
-    kout[int64_t(seg) * src.M + dst] = k;
-    vout[int64_t(seg) * src.M + dst] = sv[q];
+}
+
+// Each chunk sorted completely in shared memory, then order and common-
+// prefix lengths written to their final ranks.  Chunks are taken from a
+// device counter (dynamic balance over chunks of uneven size).
+__global__ void __launch_bounds__(kLocalThreads, 2) k_sort_local(LocalArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* sk0 = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* sk1 = sk0 + kSortLocalMax;
+  uint32_t* sv0 = reinterpret_cast<uint32_t*>(sk1 + kSortLocalMax);
+  uint32_t* sv1 = sv0 + kSortLocalMax;
+  uint32_t (*wh)[256] = reinterpret_cast<uint32_t (*)[256]>(sv1 + kSortLocalMax);
+  uint32_t* doff = &wh[kLocalWarps][0];
+  __shared__ uint32_t s_chunk;
+  __shared__ unsigned long long s_or[kLocalWarps], s_and[kLocalWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t nc = min(a.cnt[kCntChunks], a.chunk_cap);
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(&a.cnt[kCntWork], 1u);
+    __syncthreads();
+    const uint32_t c = s_chunk;
+    __syncthreads();
+    if (c >= nc) break;
+    const SortChunk ch = a.chunks[c];
+    if (ch.seg >= uint32_t(a.segs) || int64_t(ch.start) + ch.size > a.M) continue;   // only after an overflow
+    const int64_t ib = int64_t(ch.seg) * a.M + ch.start;
+    const int64_t ob = (int64_t(a.j0) * a.D + ch.seg) * a.M + ch.start;
+    const uint64_t* kin = (ch.buf ? a.k[1] : a.k[0]) + ib;
+    const uint32_t* vin = (ch.buf ? a.v[1] : a.v[0]) + ib;
+    const int n = int(ch.size);
+    if (ch.equal || n > kSortLocalMax) {
+      // equal keys (after the last level): already in order
+      for (int q = threadIdx.x; q < n; q += kLocalThreads) {
+        a.order[ob + q] = vin[q];
+        a.lcp[ob + q] = q == 0 ? ch.lcp0 : uint8_t(a.K);
+      }
+      continue;
+    }
+    uint64_t o = 0, nd = ~0ull;
+    for (int q = threadIdx.x; q < n; q += kLocalThreads) {
+      const uint64_t k = kin[q] & a.kmask;
+      sk0[q] = k;
+      sv0[q] = vin[q];
+      o |= k;
+      nd &= k;
+    }
+    for (int off = 16; off; off >>= 1) {
+      o |= __shfl_xor_sync(0xffffffffu, o, off);
+      nd &= __shfl_xor_sync(0xffffffffu, nd, off);
+    }
+    if (lane == 0) {
+      s_or[warp] = o;
+      s_and[warp] = nd;
+    }
+    __syncthreads();
+    uint64_t vary = 0;
+    {
+      uint64_t oo = 0, aa = ~0ull;
+      for (int w = 0; w < kLocalWarps; ++w) {
+        oo |= s_or[w];
+        aa &= s_and[w];
+      }
+      vary = oo ^ aa;                     // bits that differ somewhere in the chunk
+    }
+    uint64_t* ck = sk0;
+    uint32_t* cv = sv0;
+    uint64_t* ok = sk1;
+    uint32_t* ov = sv1;
+    for (int shift = 0; shift < 64; shift += 8) {
+      if (!((vary >> shift) & 255u)) continue;
+      local_pass(ck, cv, ok, ov, n, shift, wh, doff);
+      uint64_t* tk = ck; ck = ok; ok = tk;
+      uint32_t* tv = cv; cv = ov; ov = tv;
+    }
+    for (int q = threadIdx.x; q < n; q += kLocalThreads) {
+      a.order[ob + q] = cv[q];
+      uint32_t l = ch.lcp0;
+      if (q > 0) {
+        const uint64_t x = ck[q] ^ ck[q - 1];
+        l = x == 0 ? 8u : uint32_t(__clzll(x)) / 8u;
+        if (l > uint32_t(a.K)) l = uint32_t(a.K);
+      }
+      a.lcp[ob + q] = uint8_t(l);
+    }
+    __syncthreads();
   }
 }
 
-__global__ void k_finish(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                         int64_t M, int D, int j0, int segs, int K, uint32_t* __restrict__ order,
-                         uint8_t* __restrict__ lcp) {
-  int64_t total = int64_t(segs) * M;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total;
-       q += int64_t(gridDim.x) * blockDim.x) {
-    int64_t seg = q / M, p = q - seg * M;
-    int64_t j = j0 + seg / D, f = seg % D;
-    int64_t o = (j * D + f) * M + p;
-    order[o] = vin[q];
-    uint32_t l = 0;
-    if (p > 0) {
-      uint64_t x = kin[q] ^ kin[q - 1];
-      l = x == 0 ? 8u : uint32_t(__clzll(x)) / 8u;
-      if (l > uint32_t(K)) l = uint32_t(K);
-    }
-    lcp[o] = uint8_t(l);
-  }
-}
+constexpr size_t kLocalSmem = size_t(kSortLocalMax) * (8 + 8 + 4 + 4) +
+                              size_t(kLocalWarps + 1) * 256 * 4;
 
 }  // namespace
 
-int64_t sort_hist_entries(int64_t M, int segs) {
-  int64_t tiles = (M + kTile - 1) / kTile;
-  return int64_t(segs) * 256 * tiles;
+SortScratch sort_scratch_carve(void* base, int64_t M, int segs) {
+  const SortCaps c = sort_caps(M, segs);
+  const int64_t e = M * segs;
+  const auto up = sort_up256;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  SortScratch sc;
+  sc.k0 = reinterpret_cast<uint64_t*>(p); p += up(size_t(e) * 8);
+  sc.k1 = reinterpret_cast<uint64_t*>(p); p += up(size_t(e) * 8);
+  sc.v0 = reinterpret_cast<uint32_t*>(p); p += up(size_t(e) * 4);
+  sc.v1 = reinterpret_cast<uint32_t*>(p); p += up(size_t(e) * 4);
+  sc.hist = reinterpret_cast<uint32_t*>(p); p += up(size_t(c.tile_cap) * 256 * 4);
+  sc.items[0] = reinterpret_cast<SortItem*>(p); p += up(size_t(c.item_cap) * sizeof(SortItem));
+  sc.items[1] = reinterpret_cast<SortItem*>(p); p += up(size_t(c.item_cap) * sizeof(SortItem));
+  sc.tile_item[0] = reinterpret_cast<uint64_t*>(p); p += up(size_t(c.tile_cap) * 8);
+  sc.tile_item[1] = reinterpret_cast<uint64_t*>(p); p += up(size_t(c.tile_cap) * 8);
+  sc.chunks = reinterpret_cast<SortChunk*>(p); p += up(size_t(c.chunk_cap) * sizeof(SortChunk));
+  sc.cnt = reinterpret_cast<uint32_t*>(p);
+  sc.cap_entries = e;
+  sc.caps = c;
+  sc.M = M;
+  sc.segs = segs;
+  return sc;
 }
 
 cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch& sc,
                              cudaStream_t s) {
   if (j1 <= j0) return cudaSuccess;
   const int segs = (j1 - j0) * ix.D;
-  if (int64_t(segs) * ix.M > sc.cap_entries || sort_hist_entries(ix.M, segs) > sc.hist_entries)
-    return cudaErrorInvalidValue;
-  const int tiles = int((ix.M + kTile - 1) / kTile);
-  dim3 grid{unsigned(segs), unsigned(tiles), 1u};
-  uint64_t* kb[2] = {sc.k0, sc.k1};
-  uint32_t* vb[2] = {sc.v0, sc.v1};
-  for (int pass = 0; pass < ix.K; ++pass) {
-    const int byte = ix.K - 1 - pass;          // 0 = most significant hash value
-    const int shift = 56 - 8 * byte;
-    Src src{ix.keys, pass ? kb[(pass - 1) & 1] : nullptr, pass ? vb[(pass - 1) & 1] : nullptr,
-            ix.M, ix.D, j0, pass == 0};
-    MOMENTI_LAUNCH("sort_hist", s, k_hist<<<grid, kThreads, 0, s>>>(src, shift, tiles, sc.hist));
-    MOMENTI_LAUNCH("sort_scan", s, k_scan<<<segs, 256, 0, s>>>(tiles, sc.hist));
-    MOMENTI_LAUNCH("sort_scatter", s, k_scatter<<<grid, kThreads, 0, s>>>(src, shift, tiles, sc.hist, kb[pass & 1], vb[pass & 1]));
+  if (sc.M != ix.M || segs > sc.segs) return cudaErrorInvalidValue;
+  const SortCaps& c = sc.caps;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_sort_local), kLocalSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t tpm = (ix.M + kTile - 1) / kTile;
+  const int sm = sm_count();
+  {
+    const int64_t total = int64_t(segs) * tpm;
+    const int g = int(std::min<int64_t>((total + 255) / 256, int64_t(sm) * 8));
+    MOMENTI_LAUNCH("sort_init", s, k_sort_init<<<std::max(g, 1), 256, 0, s>>>(segs, ix.M, sc.items[0], sc.tile_item[0], sc.cnt));
   }
-  const int last = (ix.K - 1) & 1;
-  int64_t total = int64_t(segs) * ix.M;
-  int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
-  MOMENTI_LAUNCH("sort_finish", s, k_finish<<<g, 256, 0, s>>>(kb[last], vb[last], ix.M, ix.D, j0, segs, ix.K, ix.order, ix.lcp));
+  uint32_t n_items = uint32_t(segs), n_tiles = uint32_t(int64_t(segs) * tpm);
+  const bool host = sc.host_cnt != nullptr;
+  for (int t = 0; t < ix.K; ++t) {
+    Level lv;
+    lv.keys = ix.keys;
+    lv.kin = t ? (((t - 1) & 1) ? sc.k1 : sc.k0) : nullptr;
+    lv.vin = t ? (((t - 1) & 1) ? sc.v1 : sc.v0) : nullptr;
+    lv.kout = (t & 1) ? sc.k1 : sc.k0;
+    lv.vout = (t & 1) ? sc.v1 : sc.v0;
+    lv.M = ix.M;
+    lv.D = ix.D;
+    lv.j0 = j0;
+    lv.t = t;
+    lv.K = ix.K;
+    lv.segs = segs;
+    lv.items = sc.items[t & 1];
+    lv.items_next = sc.items[(t + 1) & 1];
+    lv.tile_item = sc.tile_item[t & 1];
+    lv.tile_next = sc.tile_item[(t + 1) & 1];
+    lv.hist = sc.hist;
+    lv.chunks = sc.chunks;
+    lv.cnt = sc.cnt;
+    lv.item_cap = uint32_t(c.item_cap);
+    lv.tile_cap = uint32_t(c.tile_cap);
+    lv.chunk_cap = uint32_t(c.chunk_cap);
+    // with the host in the loop the grids are exact; without it, the
+    // largest a level can need (the kernels stop at the device counts)
+    const unsigned gt = unsigned(std::max<int64_t>(1, host ? n_tiles : c.tile_cap));
+    const unsigned gi = unsigned(std::max<int64_t>(1, host ? n_items : c.item_cap));
+    MOMENTI_LAUNCH("sort_hist", s, k_sort_hist<<<gt, kThreads, 0, s>>>(lv));
+    MOMENTI_LAUNCH("sort_scan", s, k_sort_scan<<<gi, 256, 0, s>>>(lv));
+    MOMENTI_LAUNCH("sort_scatter", s, k_sort_scatter<<<gt, kThreads, 0, s>>>(lv));
+    if (host) {
+      e = cudaMemcpyAsync(sc.host_cnt, sc.cnt, 32 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return e;
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      if (sc.host_cnt[kCntOverflow]) return cudaErrorInvalidValue;   // capacities are bounds: not expected
+      n_items = sc.host_cnt[2 * (t + 1)];
+      n_tiles = sc.host_cnt[2 * (t + 1) + 1];
+      if (n_items == 0) break;
+    }
+  }
+  LocalArgs la;
+  la.k[0] = sc.k0;
+  la.k[1] = sc.k1;
+  la.v[0] = sc.v0;
+  la.v[1] = sc.v1;
+  la.chunks = sc.chunks;
+  la.cnt = sc.cnt;
+  la.chunk_cap = uint32_t(c.chunk_cap);
+  la.M = ix.M;
+  la.D = ix.D;
+  la.j0 = j0;
+  la.K = ix.K;
+  la.segs = segs;
+  la.kmask = ix.K >= 8 ? ~0ull : ~((~0ull) >> (8 * ix.K));
+  la.order = ix.order;
+  la.lcp = ix.lcp;
+  MOMENTI_LAUNCH("sort_local", s, k_sort_local<<<sm * 2, kLocalThreads, kLocalSmem, s>>>(la));
   return cudaGetLastError();
 }
 

@@ -319,7 +319,7 @@ __global__ void k_stats_pm(const float* __restrict__ mh, const float* __restrict
 
 inline int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > sm_count() * 32) g = sm_count() * 32;
   if (g < 1) g = 1;
   return int(g);
 }

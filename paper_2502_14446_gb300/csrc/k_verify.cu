@@ -1000,7 +1000,7 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
 cudaError_t launch_verify_events(const Index& ix, int d, const HashSet& hs,
                                  const CollideScratch& cs, float tau, PairRec* rec,
                                  uint64_t rec_cap, cudaStream_t s) {
-#define MOMENTI_VE(DM, PM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, PM, LO><<<152 * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
+#define MOMENTI_VE(DM, PM, LO) MOMENTI_LAUNCH("verify_events", s, k_verify_events<DM, PM, LO><<<sm_count() * 8, 256, 0, s>>>(ix, d, hs, cs.events, cs.counters, cs.ev_cap, tau, rec, rec_cap))
   const bool lo = ix.has_lo;
   if (ix.xT && ix.Dp == 4) { if (lo) MOMENTI_VE(4, true, true); else MOMENTI_VE(4, true, false); }
   else if (ix.xT && ix.Dp == 8) { if (lo) MOMENTI_VE(8, true, true); else MOMENTI_VE(8, true, false); }
@@ -1016,7 +1016,7 @@ cudaError_t launch_verify_pairs(const Index& ix, int d, const uint64_t* pairs, i
                                 cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   int64_t g = (m + 7) / 8;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > sm_count() * 16) g = sm_count() * 16;
   MOMENTI_LAUNCH("verify_pairs", s, k_verify_pairs<<<unsigned(g), 256, 0, s>>>(ix, d, pairs, m, fp64, per_dim, dist_d, dims));
   return cudaGetLastError();
 }
@@ -1042,7 +1042,7 @@ cudaError_t launch_select_pairs(const uint64_t* pairs, const float* dd, uint64_t
                                 float hi, uint64_t* out, unsigned long long* count, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   uint64_t g = (m + 255) / 256;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > sm_count() * 8) g = sm_count() * 8;
   MOMENTI_LAUNCH("select_pairs", s, k_select_pairs<<<unsigned(g), 256, 0, s>>>(pairs, dd, m, lo, hi, out, count));
   return cudaGetLastError();
 }

@@ -216,6 +216,7 @@ struct momenti_handle {
   uint64_t job_cap = 0;
   unsigned long long* job_counts = nullptr;
   unsigned long long* cnt_host = nullptr;
+  uint32_t* sort_cnt_host = nullptr;        // pinned copy of the index sort's level counters
   int chunk_reps = 32;
   double t_hash_ms = 0, t_sort_ms = 0;
   bool used_tc = false;
@@ -326,6 +327,8 @@ void free_all(momenti_handle* h, bool host = false) {
     else cudaDeviceSynchronize();
     if (h->rec_host) cudaFreeHost(h->rec_host);
     if (h->cnt_host) cudaFreeHost(h->cnt_host);
+    if (h->sort_cnt_host) cudaFreeHost(h->sort_cnt_host);
+    h->sort_cnt_host = nullptr;
     h->rec_host = nullptr;
     h->cnt_host = nullptr;
     h->rec_host_cap = 0;
@@ -782,7 +785,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     const uint64_t hs_cap = std::min<uint64_t>(
         uint64_t(1) << 25, std::max<uint64_t>(uint64_t(1) << 20, next_pow2(uint64_t(M) * 64)));
     auto scratch_bytes = [&](int sreps, int creps) {
-      return uint64_t(sreps) * D * seg_bytes + sort_hist_entries(M, sreps * D) * 4 +
+      return uint64_t(sort_scratch_bytes(M, sreps * D)) +
              uint64_t(creps) * D * (C + 1) * (4 + 4 + 8) + new_cap * 32 + hs_cap * 8 +
              (uint64_t(1) << 22) * sizeof(Event);
     };
@@ -852,15 +855,9 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     CK(dalloc(h, &h->flags, size_t(h->flag_cap)));
     CK(dalloc(h, &h->small, 16));
     // index sort scratch
-    SortScratch& sc = h->sort;
-    const int64_t sent = int64_t(sort_reps) * D * M;
-    CK(dalloc(h, &sc.k0, size_t(sent)));
-    CK(dalloc(h, &sc.k1, size_t(sent)));
-    CK(dalloc(h, &sc.v0, size_t(sent)));
-    CK(dalloc(h, &sc.v1, size_t(sent)));
-    sc.hist_entries = sort_hist_entries(M, sort_reps * D);
-    CK(dalloc(h, &sc.hist, size_t(sc.hist_entries)));
-    sc.cap_entries = sent;
+    unsigned char* sort_region = nullptr;
+    CK(dalloc(h, &sort_region, sort_scratch_bytes(M, sort_reps * D)));
+    h->sort = sort_scratch_carve(sort_region, M, sort_reps * D);
     // traversal scratch
     CollideScratch& cs = h->cs;
     cs.seg_cap = int64_t(chunk) * D;
@@ -895,6 +892,8 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
       h->rec_host_cap = new_cap;
     }
     if (!h->cnt_host) CK(cudaMallocHost(&h->cnt_host, 8 * sizeof(unsigned long long)));
+    if (!h->sort_cnt_host) CK(cudaMallocHost(&h->sort_cnt_host, 64 * sizeof(uint32_t)));
+    h->sort.host_cnt = h->sort_cnt_host;
     h->built_gen = h->hp_gen;
     h->built_p = h->p;
   }
@@ -1345,6 +1344,22 @@ int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys) {
   if (!keys || j < 0 || j >= h->ix.L) return fail(h, MOMENTI_ERR_ARG, "get_keys: bad arguments");
   const size_t cnt = size_t(h->ix.D) * h->ix.M;
   CK(cudaMemcpyAsync(keys, h->ix.keys + size_t(j) * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MOMENTI_OK;
+}
+
+int momenti_get_hash_draws(momenti_handle* h, float* a, float* u) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "get_hash_draws before hash_all");
+  if (!a && !u) return fail(h, MOMENTI_ERR_ARG, "get_hash_draws: no output");
+  const Index& ix = h->ix;
+  // the device copies hold L_src repetitions per dim (L_src = L_used for
+  // device draws, the supplied count for set_hash_params): copy the first L_used
+  const int L_src = h->user_a.empty() ? ix.L : h->user_L;
+  const size_t ra = size_t(ix.L) * ix.K * ix.w, rs = size_t(L_src) * ix.K * ix.w;
+  const size_t ua = size_t(ix.L) * ix.K, us = size_t(L_src) * ix.K;
+  if (a) CK(cudaMemcpy2DAsync(a, ra * 4, h->draw_a, rs * 4, ra * 4, ix.D, cudaMemcpyDeviceToHost, h->stream));
+  if (u) CK(cudaMemcpy2DAsync(u, ua * 4, h->draw_u, us * 4, ua * 4, ix.D, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return MOMENTI_OK;
 }

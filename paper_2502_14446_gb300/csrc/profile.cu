@@ -35,6 +35,17 @@ thread_local Ev t_cur{nullptr, nullptr};
 thread_local bool t_timing = false;
 }  // namespace
 
+int sm_count() {
+  static std::atomic<int> cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int c = cache[dev].load(std::memory_order_relaxed);
+  if (c > 0) return c;
+  if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) c = 1;
+  cache[dev].store(c, std::memory_order_relaxed);
+  return c;
+}
+
 cudaError_t allow_smem(const void* func, size_t bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> granted;
@@ -53,7 +64,11 @@ void prof_begin(const char* name, cudaStream_t s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on) return;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (g_name != name) return;
+  // "prefix*" selects every kernel whose name starts with prefix
+  const size_t n = g_name.size();
+  const bool match = (n > 0 && g_name[n - 1] == '*') ? std::strncmp(g_name.c_str(), name, n - 1) == 0
+                                                    : g_name == name;
+  if (!match) return;
   t_cur = take_ev();
   t_timing = true;
   cudaEventRecord(t_cur.a, s);

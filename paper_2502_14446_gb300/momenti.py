@@ -34,7 +34,7 @@ EXPORTS = (
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
     "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
     "momenti_collision_probability", "momenti_failure_bound", "momenti_top_select",
-    "momenti_tensoring_failure_bound",
+    "momenti_tensoring_failure_bound", "momenti_get_hash_draws",
 )
 
 
@@ -88,6 +88,7 @@ def _load():
         "momenti_get_window_stats": (C.c_int, [vp, vp, vp]),
         "momenti_get_keys": (C.c_int, [vp, C.c_int32, vp]),
         "momenti_get_index": (C.c_int, [vp, C.c_int32, C.c_int32, vp, vp]),
+        "momenti_get_hash_draws": (C.c_int, [vp, vp, vp]),
         "momenti_collide": (C.c_int, [vp, C.c_int32, C.c_int32, vp, C.c_int64, P(C.c_int64)]),
         "momenti_launch_count": (C.c_uint64, []),
         "momenti_time_kernel": (C.c_int, [C.c_char_p]),
@@ -357,6 +358,15 @@ class Momenti:
         out = np.zeros((inf["M"], inf["D"]), dtype=np.uint64)
         self._check(lib.momenti_get_keys(self.h, j, _ptr(out)), "momenti_get_keys")
         return out
+
+    def hash_draws(self):
+        """(a (D, L, K, w), u (D, L, K)) float32: the hash functions' random
+        numbers of the current index."""
+        inf = self.info()
+        a = np.zeros((inf["D"], inf["L"], inf["K"], self.params.w), dtype=np.float32)
+        u = np.zeros((inf["D"], inf["L"], inf["K"]), dtype=np.float32)
+        self._check(lib.momenti_get_hash_draws(self.h, _ptr(a), _ptr(u)), "momenti_get_hash_draws")
+        return a, u
 
     def index(self, j: int, f: int):
         M = self.info()["M"]

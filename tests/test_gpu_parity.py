@@ -263,16 +263,25 @@ def test_topk_follows_algorithm_1(mom, seed):
     r = O.estimate_r(wl.series, wl.w, A)
     # Algorithm 1's loop to its end (no cost switch)
     h, _, _ = make(mom, wl, L=L, r=r, hash_seed=seed, flags=mom.FLAG_NO_COST_SWITCH)
-    keys_o, ok = agreeing_segments(h, wl, A, U, r, L)
     got, st = h.topk()
     res = O.momenti(wl.series, wl.w, wl.d, wl.k, wl.delta, A, U, r)
     assert_same_motifs(got, res["motifs"])
-    if ok.all():
-        exp = res["stop"] or (0, 0)
-        assert (st["stop_i"], st["stop_j"]) == exp
-        assert st["fallback"] == (res["stop"] is None)
-        if res["stop"] is not None:
-            assert got[-1]["fail_bound"] == pytest.approx(res["fail_bound"], rel=1e-3)
+    # The device keys equal the oracle's except for values in the float32
+    # band around a bucket edge (about 0.2% of them here, checked by the
+    # hash tests), which can move a collision by one repetition.  The
+    # traversal itself is compared unconditionally: the oracle's Algorithm 1
+    # loop run on the device's own keys must stop at the device's (i, j),
+    # with the same TOP and the same Lemma stop bound.
+    keys_dev = np.stack([h.keys(j) for j in range(L)])
+    Z = [O.znorm_windows(wl.series[f], wl.w) for f in range(wl.D)]
+    top, stop, _, _ = O.momenti_traverse(keys_dev, lambda a, b: O._pair_distances(Z, a, b),
+                                         wl.d, wl.k, wl.delta, r, O.exclusion_zone(wl.w))
+    assert (st["stop_i"], st["stop_j"]) == (stop or (0, 0))
+    assert st["fallback"] == (stop is None)
+    if stop is not None:
+        assert_same_motifs(got, top)
+        fb = O.failure_bound(top[-1][4], stop[0], stop[1], 8, L, wl.d, r)
+        assert got[-1]["fail_bound"] == pytest.approx(fb, rel=1e-3)
 
 
 def test_topk_plain_small_matches_exact(mom):

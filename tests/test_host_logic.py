@@ -126,5 +126,5 @@ def test_tensoring_bound_matches_the_oracle(mom):
                     ref = O.tensoring_failure_bound(p, i, j, K, L)
                     assert got == pytest.approx(ref, rel=1e-12, abs=1e-14), (p, i, j, K, L)
     for bad in ((0.5, 4, 1, 8, 200), (0.5, 0, 1, 8, 16), (0.5, 9, 1, 8, 16), (1.5, 4, 1, 8, 16),
-                (0.5, 4, 17, 8, 16), (0.5, 3, 1, 7, 16)):
+                (0.5, 4, 17, 8, 16), (0.5, 3, 1, 7, 16), (0.5, 4, 0, 8, 0)):
         assert math.isnan(mom.tensoring_failure_bound(*bad)), bad

@@ -317,6 +317,38 @@ def test_estimate_r_bounds_and_invariance():
     assert r2 == pytest.approx(r, rel=1e-10)
 
 
+def test_estimate_r_hand_computed():
+    # w = 2: a rising window z-normalises to (-1, 1), a falling one to
+    # (1, -1) (population sigma = half the step), so each projection is
+    # +-(a_1 - a_0) and the heuristic of Section 6.1 can be written out by
+    # hand.  Dim 0 rises twice: projections a_1 - a_0 = 3 and 1 for the two
+    # vectors of repetition 0.  Dim 1 falls then rises: 2, 0, then -2, 0.
+    # Pooled over both dims the range is 3 - (-2) = 5, so r = 5 / 256.
+    # Per-dim ranges are 2 and 4 (largest 4, mean 3); dividing by 255 gives
+    # 5 / 255: each of those misreadings fails the equality below.
+    T = np.array([[0.0, 1.0, 3.0],
+                  [5.0, 2.0, 4.0]])
+    A = np.zeros((2, 2, 2, 2))
+    A[0, 0] = [[0.0, 3.0], [0.0, 1.0]]
+    A[1, 0] = [[2.0, 0.0], [1.0, 1.0]]
+    A[:, 1] = 100.0                    # repetition 1 is not part of the sample
+    assert O.estimate_r(T, 2, A) == pytest.approx(5.0 / 256.0, rel=1e-12)
+
+
+def test_estimate_r_uses_the_evenly_spaced_sample():
+    # M = 5 windows, a sample of 3: positions floor(q (M - 1) / 2) = 0, 2, 4.
+    # Those windows rise (projection a_1 - a_0 = 2 for the one vector that
+    # is not constant zero, 0 for the other); window 1, left out of the
+    # sample, falls (projection -2).  With the sample the range is
+    # 2 - 0 = 2 (r = 2/256); a sample that took window 1 would give 4/256.
+    T = np.array([[0.0, 1.0, 0.5, 2.0, 3.0, 4.0]])
+    A = np.zeros((1, 1, 2, 2))
+    A[0, 0, 0] = [0.0, 2.0]
+    assert list(O.sample_positions(5, 3)) == [0, 2, 4]
+    assert O.estimate_r(T, 2, A, samples=3) == pytest.approx(2.0 / 256.0, rel=1e-12)
+    assert O.estimate_r(T, 2, A, samples=5) == pytest.approx(4.0 / 256.0, rel=1e-12)
+
+
 # ----------------------------------------------------------- Algorithm 1
 
 @pytest.mark.parametrize("seed", [1, 2])
@@ -443,6 +475,8 @@ def test_tensoring_bound_special_cases():
     assert all(x >= y for x, y in zip(ps, ps[1:]))
     with pytest.raises(ValueError):
         O.tensoring_failure_bound(0.5, 4, 1, 8, 200)          # L not a square
+    with pytest.raises(ValueError):
+        O.tensoring_failure_bound(0.5, 4, 0, 8, 0)            # no repetitions
 
 
 def test_printed_tensoring_lemma_is_not_a_bound():
