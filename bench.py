@@ -77,14 +77,29 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--batch-series", type=int, default=64,
                     help="series of the batching form timed beside the step (0: skip)")
-    ap.add_argument("--n", type=int, default=100_000,
-                    help="series length (smaller values only for profiler captures)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="series length (0: the workload's; smaller only for profiler captures)")
+    ap.add_argument("--workload", default="plain_fp32", choices=["plain_fp32", "precision_form"],
+                    help="plain_fp32: D=8 n=1e5 w=300 (the default line); precision_form: "
+                         "D=32 n=1e6 w=500 d=8 (minutes per step)")
+    ap.add_argument("--r", type=float, default=0.0, help="quantisation width (0: Section 6.1 heuristic)")
+    ap.add_argument("--no-rsweep", action="store_true", help="skip the fixed-r sweep leg")
     return ap.parse_args()
 
 
-def workload(rank: int, n: int = 100_000):
+def workload(rank: int, n: int = 0, name: str = "plain_fp32"):
     from paper_2502_14446_gb300 import synth
-    return synth.plain_fp32(seed=rank, n=n)
+    if name == "precision_form":
+        return synth.precision_form(seed=rank, n=n or 1_000_000)
+    return synth.plain_fp32(seed=rank, n=n or 100_000)
+
+
+def describe(wl) -> str:
+    """The workload line of config: what it is, with its sizes."""
+    mem = f", {wl.mem_limit >> 30} GB limit" if wl.mem_limit else ""
+    prec = " (FP64 stats and re-verification)" if wl.name == "precision_form" else ""
+    return (f"{wl.name}: D={wl.D} n={wl.n} w={wl.w} d={wl.d} k={wl.k} delta={wl.delta} "
+            f"float32{mem}{prec}, K=8 L=200")
 
 
 def combine(local_ms: float, units_per_step: int, steps: int, world: int, device=None) -> tuple:
@@ -167,9 +182,9 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def params_for(mom, wl, precision):
+def params_for(mom, wl, precision, r=0.0):
     return mom.default_params(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, mem_limit=wl.mem_limit,
-                              K=8, L=200, precision=precision)
+                              K=8, L=200, precision=precision, r=r)
 
 
 def sm_count(device=None) -> int:
@@ -250,12 +265,13 @@ def run_momenti(args):
         dist.barrier()
     from paper_2502_14446_gb300 import momenti as mom
 
-    wl = workload(rank, args.n)
+    wl = workload(rank, args.n, args.workload)
     prec = mom.PREC_F16X2 if args.precision == "f16x2" else mom.PREC_FP32
     series = torch.from_numpy(wl.series).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    h = mom.Momenti(params_for(mom, wl, prec))
+    h = mom.Momenti(params_for(mom, wl, prec, args.r))
+    sms = sm_count(dev)
 
     def step():
         h.hash_all(series, stream=stream.cuda_stream)
@@ -266,17 +282,18 @@ def run_momenti(args):
     torch.cuda.synchronize()
     info = h.info()
 
-    # dominant kernel: the one with the largest device time in one step
+    # device time of each candidate kernel over one step: the dominant one is
+    # timed live in the timed steps; the others' rooflines come from this step
+    per_kernel = {}
+    for kname in dict.fromkeys(DOMINANT + SECONDARY):
+        mom.time_kernel(kname)
+        _, st_k = step()
+        ms, n = mom.kernel_time()
+        per_kernel[kname] = (ms, n, st_k)
+    mom.time_kernel(None)
     kernel = args.kernel
     if kernel == "auto":
-        best = (None, -1.0)
-        for kname in DOMINANT:
-            mom.time_kernel(kname)
-            step()
-            ms, n = mom.kernel_time()
-            if ms > best[1]:
-                best = (kname, ms)
-        kernel = best[0]
+        kernel = max(DOMINANT, key=lambda k: per_kernel[k][0])
     mom.time_kernel(kernel)
 
     clocks = Clocks(local)
@@ -323,10 +340,19 @@ def run_momenti(args):
     out = None
     if rank == 0:
         pk = peaks()
-        roof = roofline(kernel, k_ms, k_n, info, st, wl, args.steps, pk)
+        roof = roofline(kernel, k_ms, k_n, info, st, wl, args.steps, pk, sms)
+        others = {}
+        for kname in SECONDARY:
+            if kname == kernel:
+                continue
+            ms, n, st_k = per_kernel[kname]
+            r2 = roofline(kname, ms, n, info, st_k, wl, 1, pk, sms)
+            if r2 is not None:
+                r2["timed"] = "one untimed step before the timed region"
+                others[kname] = r2
         plain = None
         if not args.no_fp32 and prec != mom.PREC_FP32:
-            h32 = mom.Momenti(params_for(mom, wl, mom.PREC_FP32))
+            h32 = mom.Momenti(params_for(mom, wl, mom.PREC_FP32, args.r))
             h32.hash_all(series, stream=stream.cuda_stream)
             h32.topk()
             ts = []
@@ -344,8 +370,14 @@ def run_momenti(args):
                      "value": units_step / (statistics.mean(ts) / 1e3),
                      "t_hash_ms": st32["t_hash_ms"]}
             h32.close()
+        rsweep = None
+        if wl.name == "plain_fp32" and not args.no_rsweep:
+            rsweep = r_sweep_leg(mom, wl, series, stream, flush, prec)
         batch = batch_leg(mom, args.batch_series, dev) if args.batch_series > 0 else None
         base = None if args.no_baseline else cpu_baseline(wl)
+        # float64 error of each result: the float32 traversal distance
+        # against the float64 re-verification (stats), and the float64
+        # distances returned
         out = {
             "metric": "time-to-top-k motifs (s) and subsequences hashed/s, BF16/batched vs plain FP32",
             "value": value, "unit": "subsequences/s", "n_gpus": world, "steps": args.steps,
@@ -354,25 +386,28 @@ def run_momenti(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16x2+f32" if prec == mom.PREC_F16X2 else "f32",
             "data": "synthetic",
-            "config": {"workload": f"plain_fp32: D=8 n={wl.n} w=300 d=3 k=10 delta=0.05 "
-                                   "float32, 8 GB limit, K=8 L=200, r auto",
+            "config": {"workload": describe(wl) + (f", r={args.r}" if args.r > 0 else ", r auto"),
                        "precision": args.precision, "L_used": info["L"], "K": info["K"],
                        "r": info["r"], "windows": info["M"], "l2": "flushed (512 MB write) before each step",
                        "parallelism": f"replicas x{world}"},
             "step": {"t_hash_ms": st["t_hash_ms"], "t_sort_ms": st["t_sort_ms"],
                      "t_traverse_ms": st["t_traverse_ms"], "t_fallback_ms": st["t_fallback_ms"],
                      "stop": [st["stop_i"], st["stop_j"]], "fallback": st["fallback"],
+                     "switch_level": st["switch_level"],
                      "n_candidates": st["n_candidates"], "n_verified": st["n_verified"],
                      "n_rehashed": st["n_rehashed"], "precision_used": st["precision_used"],
                      "max_rel_err_fp32": st["max_rel_err_fp32"],
-                     "hashed_per_s_hash_all": units_step / (st["t_hash_ms"] / 1e3)},
+                     "hashed_per_s_hash_all": units_step / (st["t_hash_ms"] / 1e3),
+                     "kernel_ms": {k: round(v[0], 3) for k, v in per_kernel.items()}},
             "motifs": [[m["a"], m["b"], round(m["dist_d"], 6), list(m["dims"])] for m in motifs],
             "plain_fp32": plain,
+            "r_sweep": rsweep,
             "batch_form": batch,
             "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
                     "time_to_topk_s": e2e_s, "h2d_bytes_per_step": h_bytes,
                     "d2h_bytes_per_step": d_bytes},
             "roofline": roof,
+            "rooflines_other": others,
             "cpu_baseline": base,
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -382,6 +417,44 @@ def run_momenti(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def r_sweep_leg(mom, wl, series, stream, flush, prec, rs=(0.0, 4.0, 8.0, 12.0, 16.0)):
+    """The paper's quantisation-width experiment (Section 7, impact of r) on
+    this workload: the Section 6.1 heuristic (r = 0) against fixed r, with
+    the library's default search (cost switch on).  Per r: the stopping
+    (i, j) or the exact path, the level at which the cost switch chose it,
+    distance computations, time to top-k (mean of two steps after one
+    warm-up, L2 flushed before each) and whether the motifs equal the
+    exact top-k the oracle wrote (tests/golden, this workload at seed 0)."""
+    import torch
+    gold = None
+    path = os.path.join(ROOT, "tests", "golden", "exact_plain_fp32_seed0.json")
+    if wl.n == 100_000 and wl.seed == 0 and os.path.exists(path):
+        gold = [(m[1], m[2]) for m in json.load(open(path))["motifs"]]
+    out = []
+    for r in rs:
+        hh = mom.Momenti(params_for(mom, wl, prec, r))
+        hh.hash_all(series, stream=stream.cuda_stream)
+        hh.topk()
+        ts = []
+        for _ in range(2):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hh.hash_all(series, stream=stream.cuda_stream)
+            m, st = hh.topk()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        hh.close()
+        out.append({"r": st["r"], "r_auto": r == 0.0, "stop": [st["stop_i"], st["stop_j"]],
+                    "fallback": st["fallback"], "switch_level": st["switch_level"],
+                    "n_verified": st["n_verified"], "time_to_topk_ms": statistics.mean(ts),
+                    "t_traverse_ms": st["t_traverse_ms"], "t_fallback_ms": st["t_fallback_ms"],
+                    "matches_exact": None if gold is None else [(x["a"], x["b"]) for x in m] == gold})
     return out
 
 
@@ -416,7 +489,7 @@ def batch_leg(mom, count: int, dev, threads: int = 8):
 
 def cpu_baseline(wl, budget_s: float = 20.0):
     """The CPU oracle (Algorithm 1 rendering, float64 numpy) on a bounded
-    prefix of the same workload: n = 2,000 points of the same series, all 8
+    prefix of the same workload: n = 2,000 points of the same series, all D
     dims, w, d, k, delta as the workload, K=8, L=200 hash functions drawn by
     the same generator."""
     from oracle import momenti_oracle as O
@@ -458,10 +531,11 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": f"plain_fp32: D=8 n={wl.n} w=300 d=3 k=10 delta=0.05 "
-                                   "float32, 8 GB limit, K=8 L=200, r auto",
+           "config": {"workload": describe(wl) + ", r auto",
                       "sample": "each step times the oracle on a bounded prefix (cpu_baseline.sample) "
-                                "and reports its throughput",
+                                "and reports its throughput there; the per-window cost of the "
+                                "search grows with n, so this throughput is above what the "
+                                "oracle reaches on the whole series",
                       "parallelism": f"replicas x{world}"},
            "cpu_baseline": {"value": value, "unit": "subsequences/s", "cores": os.cpu_count(),
                             "kind": "oracle", "sample": base["sample"]},

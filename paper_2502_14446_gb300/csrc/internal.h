@@ -111,7 +111,7 @@ cudaError_t launch_rehash_fp32(const Index& ix, const uint64_t* flags, const uin
 // ---- k_sort.cu ----------------------------------------------------------
 // Largest chunk one CTA sorts in shared memory (the most-significant-digit
 // partition goes one hash value deeper for larger buckets).
-constexpr int kSortLocalMax = 4096;
+constexpr int kSortLocalMax = 2048;
 // A range of one segment that one level partitions by one hash value.
 struct SortItem {
   uint32_t seg;      // segment (repetition-major within the batch)

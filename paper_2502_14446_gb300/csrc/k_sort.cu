@@ -43,13 +43,13 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpSpan = kTile / kWarps;      // 256 entries per warp
 constexpr int kRounds = kWarpSpan / 32;        // 8
 
-constexpr int kLocalThreads = 256;
+constexpr int kLocalThreads = 128;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kLocalRounds = kSortLocalMax / (kLocalWarps * 32);   // 16
+static_assert(kSortLocalMax <= 65536, "chunk ranks travel as 16-bit values");
 
 // counters: [2 t] items and [2 t + 1] tiles of level t (t = 0..8), then
 constexpr int kCntChunks = 20;   // chunks for the shared-memory sort
-constexpr int kCntWork = 21;     // next chunk to take
 constexpr int kCntOverflow = 22; // a capacity was exceeded
 
 struct Level {
@@ -218,59 +218,81 @@ __global__ void __launch_bounds__(256) k_sort_scan(Level lv) {
     if (d == 0) {
       // classification, in digit order: a bucket's first entry shares t
       // hash values with its predecessor (the item's own first entry keeps
-      // the item's count)
+      // the item's count).  Two walks over the digits: the first counts the
+      // chunks and items this item makes, so that one atomic reserves their
+      // slots; the second writes them.
       const bool last_level = lv.t + 1 >= lv.K;
-      uint32_t c_start = 0, c_size = 0, c_lcp = 0;
-      bool open = false, first = true;
-      auto emit = [&](uint32_t st, uint32_t sz, uint32_t l0, uint32_t equal) {
-        const uint32_t slot = atomicAdd(&lv.cnt[kCntChunks], 1u);
-        if (slot < lv.chunk_cap) {
-          SortChunk ch;
-          ch.seg = it.seg;
-          ch.start = st;
-          ch.size = sz;
-          ch.lcp0 = uint8_t(l0);
-          ch.buf = uint8_t(lv.t & 1);
-          ch.equal = uint8_t(equal);
-          ch.pad = 0;
-          lv.chunks[slot] = ch;
-        } else {
-          lv.cnt[kCntOverflow] = 1u;
-        }
-      };
-      for (int g = 0; g < 256; ++g) {
-        const uint32_t sz = tot[g];
-        if (!sz) continue;
-        const uint32_t l0 = first ? it.lcp0 : uint32_t(lv.t);
-        first = false;
-        const uint32_t st = it.start + bstart[g];
-        if (sz > uint32_t(kSortLocalMax)) {
-          if (open) emit(c_start, c_size, c_lcp, 0u);
-          open = false;
-          if (last_level) {
-            emit(st, sz, l0, 1u);            // equal keys: already in order
-          } else {
-            const uint32_t nt = ntiles(sz);
-            const uint32_t slot = atomicAdd(&lv.cnt[2 * (lv.t + 1)], 1u);
-            const uint32_t tb = atomicAdd(&lv.cnt[2 * (lv.t + 1) + 1], nt);
-            if (slot < lv.item_cap && tb + nt <= lv.tile_cap) {
-              lv.items_next[slot] = SortItem{it.seg, st, sz, tb, l0, {0u, 0u, 0u}};
-              for (uint32_t q = 0; q < nt; ++q) lv.tile_next[tb + q] = (uint64_t(q) << 32) | slot;
+      uint32_t n_chunks = 0, n_items = 0, n_tiles = 0, chunk0 = 0, item0 = 0, tile0 = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        uint32_t nch = 0, nit = 0, ntl = 0;
+        uint32_t c_start = 0, c_size = 0, c_lcp = 0;
+        bool open = false, first = true;
+        auto emit = [&](uint32_t st, uint32_t sz, uint32_t l0, uint32_t equal) {
+          if (pass == 1) {
+            const uint32_t slot = chunk0 + nch;
+            if (slot < lv.chunk_cap) {
+              SortChunk ch;
+              ch.seg = it.seg;
+              ch.start = st;
+              ch.size = sz;
+              ch.lcp0 = uint8_t(l0);
+              ch.buf = uint8_t(lv.t & 1);
+              ch.equal = uint8_t(equal);
+              ch.pad = 0;
+              lv.chunks[slot] = ch;
             } else {
               lv.cnt[kCntOverflow] = 1u;
             }
           }
-        } else if (open && c_size + sz <= uint32_t(kSortLocalMax)) {
-          c_size += sz;
-        } else {
-          if (open) emit(c_start, c_size, c_lcp, 0u);
-          open = true;
-          c_start = st;
-          c_size = sz;
-          c_lcp = l0;
+          ++nch;
+        };
+        for (int g = 0; g < 256; ++g) {
+          const uint32_t sz = tot[g];
+          if (!sz) continue;
+          const uint32_t l0 = first ? it.lcp0 : uint32_t(lv.t);
+          first = false;
+          const uint32_t st = it.start + bstart[g];
+          if (sz > uint32_t(kSortLocalMax)) {
+            if (open) emit(c_start, c_size, c_lcp, 0u);
+            open = false;
+            if (last_level) {
+              emit(st, sz, l0, 1u);            // equal keys: already in order
+            } else {
+              const uint32_t nt = ntiles(sz);
+              if (pass == 1) {
+                const uint32_t slot = item0 + nit, tb = tile0 + ntl;
+                if (slot < lv.item_cap && tb + nt <= lv.tile_cap) {
+                  lv.items_next[slot] = SortItem{it.seg, st, sz, tb, l0, {0u, 0u, 0u}};
+                  for (uint32_t q = 0; q < nt; ++q) lv.tile_next[tb + q] = (uint64_t(q) << 32) | slot;
+                } else {
+                  lv.cnt[kCntOverflow] = 1u;
+                }
+              }
+              ++nit;
+              ntl += nt;
+            }
+          } else if (open && c_size + sz <= uint32_t(kSortLocalMax)) {
+            c_size += sz;
+          } else {
+            if (open) emit(c_start, c_size, c_lcp, 0u);
+            open = true;
+            c_start = st;
+            c_size = sz;
+            c_lcp = l0;
+          }
+        }
+        if (open) emit(c_start, c_size, c_lcp, 0u);
+        if (pass == 0) {
+          n_chunks = nch;
+          n_items = nit;
+          n_tiles = ntl;
+          if (n_chunks) chunk0 = atomicAdd(&lv.cnt[kCntChunks], n_chunks);
+          if (n_items) {
+            item0 = atomicAdd(&lv.cnt[2 * (lv.t + 1)], n_items);
+            tile0 = atomicAdd(&lv.cnt[2 * (lv.t + 1) + 1], n_tiles);
+          }
         }
       }
-      if (open) emit(c_start, c_size, c_lcp, 0u);
     }
     __syncthreads();
   }
@@ -382,38 +404,53 @@ struct LocalArgs {
   uint8_t* lcp;
 };
 
-// Stable LSD pass of one byte over n entries in shared memory (src -> dst).
-__device__ __forceinline__ void local_pass(const uint64_t* sk, const uint32_t* sv, uint64_t* dk,
-                                           uint32_t* dv, int n, int shift, uint32_t (*wh)[256],
+// Stable LSD pass of one 8-bit digit over n entries in shared memory (src ->
+// dst): keys and their 16-bit ranks in the chunk move together.  Each warp
+// owns a contiguous span and ranks it with match masks against its own
+// digit counters; the warp-order scan of the counters keeps the pass
+// stable.  Keys stay in registers between counting and scatter.
+__device__ __forceinline__ void local_pass(const uint64_t* sk, const uint16_t* si, uint64_t* dk,
+                                           uint16_t* di, int n, int shift, uint16_t (*wh)[256],
                                            uint32_t* doff) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int q = threadIdx.x; q < kLocalWarps * 256; q += kLocalThreads) (&wh[0][0])[q] = 0;
-  __syncthreads();
+  {
+    uint32_t* z = reinterpret_cast<uint32_t*>(&wh[0][0]);
+    for (int q = threadIdx.x; q < kLocalWarps * 128; q += kLocalThreads) z[q] = 0u;
+  }
+  // span: a multiple of 32 covering n over the warps
   const int span = ((n + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
-  const int w0 = warp * span;
+  uint64_t key[kLocalRounds];
+  uint16_t idx[kLocalRounds];
   uint32_t pk[kLocalRounds];            // digit | local rank << 9
 #pragma unroll
   for (int r = 0; r < kLocalRounds; ++r) {
-    const int q = w0 + r * 32 + lane;
+    const int q = warp * span + r * 32 + lane;
     const bool in = r * 32 < span && q < n;
-    const uint32_t dg = in ? uint32_t(sk[q] >> shift) & 255u : 256u + lane;
+    key[r] = in ? sk[q] : 0ull;
+    idx[r] = in ? si[q] : uint16_t(0);
+    pk[r] = in ? uint32_t(key[r] >> shift) & 255u : 256u + lane;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kLocalRounds; ++r) {
+    if (r * 32 >= span) break;                 // uniform over the block
+    const uint32_t dg = pk[r];
     const uint32_t peers = __match_any_sync(0xffffffffu, dg);
     const uint32_t rank = __popc(peers & lt);
-    uint32_t b = 0;
-    if (dg < 256u) b = wh[warp][dg];
+    const uint32_t b = dg < 256u ? wh[warp][dg] : 0u;
     __syncwarp();
-    if (dg < 256u && rank == 0) wh[warp][dg] = b + __popc(peers);
+    if (dg < 256u && rank == 0) wh[warp][dg] = uint16_t(b + __popc(peers));
     __syncwarp();
     pk[r] = dg | ((b + rank) << 9);
   }
   __syncthreads();
-  {
-    const int d = threadIdx.x;           // kLocalThreads == 256: one digit each
+  for (int d = threadIdx.x; d < 256; d += kLocalThreads) {
     uint32_t run = 0;
-    for (int w = 0; w < kLocalWarps; ++w) {
-      const uint32_t c = wh[w][d];
-      wh[w][d] = run;
+#pragma unroll
+    for (int h = 0; h < kLocalWarps; ++h) {
+      const uint32_t c = wh[h][d];
+      wh[h][d] = uint16_t(run);
       run += c;
     }
     doff[d] = run;
@@ -437,36 +474,38 @@ __device__ __forceinline__ void local_pass(const uint64_t* sk, const uint32_t* s
   for (int r = 0; r < kLocalRounds; ++r) {
     const uint32_t dg = pk[r] & 511u;
     if (dg < 256u) {
-      const int q = w0 + r * 32 + lane;
       const uint32_t dst = doff[dg] + wh[warp][dg] + (pk[r] >> 9);
-      dk[dst] = sk[q];
-      dv[dst] = sv[q];
+      dk[dst] = key[r];
+      di[dst] = idx[r];
     }
   }
   __syncthreads();
 }
 
 // Each chunk sorted completely in shared memory, then order and common-
-// prefix lengths written to their final ranks.  Chunks are taken from a
-// device counter (dynamic balance over chunks of uneven size).
-__global__ void __launch_bounds__(kLocalThreads, 2) k_sort_local(LocalArgs a) {
+// prefix lengths written to their final ranks.  The keys of a chunk are
+// first compressed without changing their order: every hash value is
+// replaced by its offset from the chunk's smallest value at that position,
+// in as many bits as the chunk's range there needs, and the fields are
+// concatenated, first hash value most significant; the digit passes then
+// run over the bits the chunk actually uses.  Two keys share a hash value
+// iff they share its field, so the common-prefix length is read off the
+// compressed keys: the field of their highest differing bit.
+__global__ void __launch_bounds__(kLocalThreads, 5) k_sort_local(LocalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* sk0 = reinterpret_cast<uint64_t*>(smem);
   uint64_t* sk1 = sk0 + kSortLocalMax;
-  uint32_t* sv0 = reinterpret_cast<uint32_t*>(sk1 + kSortLocalMax);
-  uint32_t* sv1 = sv0 + kSortLocalMax;
-  uint32_t (*wh)[256] = reinterpret_cast<uint32_t (*)[256]>(sv1 + kSortLocalMax);
-  uint32_t* doff = &wh[kLocalWarps][0];
-  __shared__ uint32_t s_chunk;
-  __shared__ unsigned long long s_or[kLocalWarps], s_and[kLocalWarps];
+  uint16_t* si0 = reinterpret_cast<uint16_t*>(sk1 + kSortLocalMax);
+  uint16_t* si1 = si0 + kSortLocalMax;
+  uint16_t (*wh)[256] = reinterpret_cast<uint16_t (*)[256]>(si1 + kSortLocalMax);
+  uint32_t* doff = reinterpret_cast<uint32_t*>(&wh[kLocalWarps][0]);
+  __shared__ uint32_t s_min[kLocalWarps][2], s_max[kLocalWarps][2];
+  __shared__ uint32_t s_bmin[8], s_width[8], s_off[8];
+  __shared__ uint8_t s_field[64];          // bit position -> hash value it belongs to
+  __shared__ int s_bits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t nc = min(a.cnt[kCntChunks], a.chunk_cap);
-  for (;;) {
-    if (threadIdx.x == 0) s_chunk = atomicAdd(&a.cnt[kCntWork], 1u);
-    __syncthreads();
-    const uint32_t c = s_chunk;
-    __syncthreads();
-    if (c >= nc) break;
+  for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
     const SortChunk ch = a.chunks[c];
     if (ch.seg >= uint32_t(a.segs) || int64_t(ch.start) + ch.size > a.M) continue;   // only after an overflow
     const int64_t ib = int64_t(ch.seg) * a.M + ch.start;
@@ -482,48 +521,88 @@ __global__ void __launch_bounds__(kLocalThreads, 2) k_sort_local(LocalArgs a) {
       }
       continue;
     }
-    uint64_t o = 0, nd = ~0ull;
+    // per-byte minimum and maximum over the chunk (four bytes per word)
+    uint32_t mn[2] = {~0u, ~0u}, mx[2] = {0u, 0u};
     for (int q = threadIdx.x; q < n; q += kLocalThreads) {
       const uint64_t k = kin[q] & a.kmask;
-      sk0[q] = k;
-      sv0[q] = vin[q];
-      o |= k;
-      nd &= k;
+      sk1[q] = k;                                  // the keys as loaded, for the compression
+      const uint32_t w0 = uint32_t(k >> 32), w1 = uint32_t(k);
+      mn[0] = __vminu4(mn[0], w0); mn[1] = __vminu4(mn[1], w1);
+      mx[0] = __vmaxu4(mx[0], w0); mx[1] = __vmaxu4(mx[1], w1);
     }
     for (int off = 16; off; off >>= 1) {
-      o |= __shfl_xor_sync(0xffffffffu, o, off);
-      nd &= __shfl_xor_sync(0xffffffffu, nd, off);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        mn[h] = __vminu4(mn[h], __shfl_xor_sync(0xffffffffu, mn[h], off));
+        mx[h] = __vmaxu4(mx[h], __shfl_xor_sync(0xffffffffu, mx[h], off));
+      }
     }
     if (lane == 0) {
-      s_or[warp] = o;
-      s_and[warp] = nd;
+      s_min[warp][0] = mn[0]; s_min[warp][1] = mn[1];
+      s_max[warp][0] = mx[0]; s_max[warp][1] = mx[1];
     }
     __syncthreads();
-    uint64_t vary = 0;
-    {
-      uint64_t oo = 0, aa = ~0ull;
+    if (threadIdx.x < 8) {
+      const int b = threadIdx.x, h = b >> 2, sh = 24 - 8 * (b & 3);   // byte b of the key, 0 = most significant
+      uint32_t lo = 255u, hi = 0u;
       for (int w = 0; w < kLocalWarps; ++w) {
-        oo |= s_or[w];
-        aa &= s_and[w];
+        lo = min(lo, (s_min[w][h] >> sh) & 255u);
+        hi = max(hi, (s_max[w][h] >> sh) & 255u);
       }
-      vary = oo ^ aa;                     // bits that differ somewhere in the chunk
+      s_bmin[b] = lo;
+      s_width[b] = hi > lo ? 32u - __clz(hi - lo) : 0u;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int off = 0;                                  // bit offset of each field from the bottom
+      for (int b = 7; b >= 0; --b) {
+        s_off[b] = uint32_t(off);
+        off += int(s_width[b]);
+      }
+      s_bits = off;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      uint8_t f = 8;
+      for (int b = 0; b < 8; ++b)
+        if (uint32_t(threadIdx.x) >= s_off[b] && uint32_t(threadIdx.x) < s_off[b] + s_width[b]) f = uint8_t(b);
+      s_field[threadIdx.x] = f;
+    }
+    const uint32_t bmin_hi = (s_bmin[0] << 24) | (s_bmin[1] << 16) | (s_bmin[2] << 8) | s_bmin[3];
+    const uint32_t bmin_lo = (s_bmin[4] << 24) | (s_bmin[5] << 16) | (s_bmin[6] << 8) | s_bmin[7];
+    uint32_t foff[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) foff[b] = s_off[b];
+    for (int q = threadIdx.x; q < n; q += kLocalThreads) {
+      const uint64_t k = sk1[q];
+      // byte-wise offsets from the minima (no borrow: every byte is >= its minimum)
+      const uint32_t d0 = __vsub4(uint32_t(k >> 32), bmin_hi), d1 = __vsub4(uint32_t(k), bmin_lo);
+      uint64_t z = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const uint32_t v = ((b < 4 ? d0 : d1) >> (24 - 8 * (b & 3))) & 255u;
+        z |= uint64_t(v) << foff[b];                 // width 0: the offset is 0
+      }
+      sk0[q] = z;
+      si0[q] = uint16_t(q);
+    }
+    __syncthreads();
     uint64_t* ck = sk0;
-    uint32_t* cv = sv0;
+    uint16_t* ci = si0;
     uint64_t* ok = sk1;
-    uint32_t* ov = sv1;
-    for (int shift = 0; shift < 64; shift += 8) {
-      if (!((vary >> shift) & 255u)) continue;
-      local_pass(ck, cv, ok, ov, n, shift, wh, doff);
+    uint16_t* oi = si1;
+    const int bits = s_bits;
+    for (int shift = 0; shift < bits; shift += 8) {
+      local_pass(ck, ci, ok, oi, n, shift, wh, doff);
       uint64_t* tk = ck; ck = ok; ok = tk;
-      uint32_t* tv = cv; cv = ov; ov = tv;
+      uint16_t* ti = ci; ci = oi; oi = ti;
     }
     for (int q = threadIdx.x; q < n; q += kLocalThreads) {
-      a.order[ob + q] = cv[q];
+      a.order[ob + q] = vin[ci[q]];
       uint32_t l = ch.lcp0;
       if (q > 0) {
         const uint64_t x = ck[q] ^ ck[q - 1];
-        l = x == 0 ? 8u : uint32_t(__clzll(x)) / 8u;
+        l = x == 0 ? 8u : uint32_t(s_field[63 - __clzll(x)]);
         if (l > uint32_t(a.K)) l = uint32_t(a.K);
       }
       a.lcp[ob + q] = uint8_t(l);
@@ -532,8 +611,8 @@ __global__ void __launch_bounds__(kLocalThreads, 2) k_sort_local(LocalArgs a) {
   }
 }
 
-constexpr size_t kLocalSmem = size_t(kSortLocalMax) * (8 + 8 + 4 + 4) +
-                              size_t(kLocalWarps + 1) * 256 * 4;
+constexpr size_t kLocalSmem = size_t(kSortLocalMax) * (8 + 8 + 2 + 2) +
+                              size_t(kLocalWarps) * 256 * 2 + 256 * 4;
 
 }  // namespace
 
@@ -635,7 +714,9 @@ cudaError_t launch_sort_reps(const Index& ix, int j0, int j1, const SortScratch&
   la.kmask = ix.K >= 8 ? ~0ull : ~((~0ull) >> (8 * ix.K));
   la.order = ix.order;
   la.lcp = ix.lcp;
-  MOMENTI_LAUNCH("sort_local", s, k_sort_local<<<sm * 2, kLocalThreads, kLocalSmem, s>>>(la));
+  // five CTAs of 4 warps per SM (shared memory bound); chunks statically
+  // interleaved over them
+  MOMENTI_LAUNCH("sort_local", s, k_sort_local<<<sm * 5, kLocalThreads, kLocalSmem, s>>>(la));
   return cudaGetLastError();
 }
 
