@@ -370,9 +370,10 @@ def run_momenti(args):
                      "value": units_step / (statistics.mean(ts) / 1e3),
                      "t_hash_ms": st32["t_hash_ms"]}
             h32.close()
-        rsweep = None
+        rsweep = tens = None
         if wl.name == "plain_fp32" and not args.no_rsweep:
             rsweep = r_sweep_leg(mom, wl, series, stream, flush, prec)
+            tens = tensoring_leg(mom, wl, series, stream, flush, prec)
         batch = batch_leg(mom, args.batch_series, dev) if args.batch_series > 0 else None
         base = None if args.no_baseline else cpu_baseline(wl)
         # float64 error of each result: the float32 traversal distance
@@ -402,6 +403,7 @@ def run_momenti(args):
             "motifs": [[m["a"], m["b"], round(m["dist_d"], 6), list(m["dims"])] for m in motifs],
             "plain_fp32": plain,
             "r_sweep": rsweep,
+            "tensoring": tens,
             "batch_form": batch,
             "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
                     "time_to_topk_s": e2e_s, "h2d_bytes_per_step": h_bytes,
@@ -417,6 +419,45 @@ def run_momenti(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def tensoring_leg(mom, wl, series, stream, flush, prec, m=14):
+    """Tensoring (Section 6.1) against plain repetitions on this workload at
+    the same L = m^2 (K = 8, r by the heuristic, library defaults
+    otherwise): hash_all time (projections of K m instead of K L values per
+    window and dim, then the key interleave), device memory held by the
+    handle, time to top-k (mean of two steps after one warm-up, L2 flushed
+    before each) and the motifs found."""
+    import torch
+    out = {"L": m * m}
+    motifs = {}
+    for name, flags in (("plain", 0), ("tensored", mom.FLAG_TENSORING)):
+        p = params_for(mom, wl, prec)
+        p.L = m * m
+        p.flags = flags
+        hh = mom.Momenti(p)
+        hh.hash_all(series, stream=stream.cuda_stream)
+        hh.topk()
+        ts, th = [], []
+        for _ in range(2):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hh.hash_all(series, stream=stream.cuda_stream)
+            mm, st = hh.topk()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            th.append(st["t_hash_ms"])
+        hh.close()
+        motifs[name] = [(x["a"], x["b"]) for x in mm]
+        out[name] = {"t_hash_ms": statistics.mean(th), "t_sort_ms": st["t_sort_ms"],
+                     "time_to_topk_ms": statistics.mean(ts), "device_bytes": st["device_bytes"],
+                     "stop": [st["stop_i"], st["stop_j"]], "fallback": st["fallback"],
+                     "n_verified": st["n_verified"], "r": st["r"]}
+    out["same_motifs"] = motifs["plain"] == motifs["tensored"]
     return out
 
 

@@ -94,6 +94,19 @@ typedef struct momenti_params {
  * stops there and the exact path runs (its result is the exact top-k, the
  * probability-1 branch of Lemma topk). */
 #define MOMENTI_FLAG_NO_COST_SWITCH 2u
+/* flags: tensoring (Section 6.1).  The L = m^2 repetitions are built from m
+ * left and m right hash functions of K/2 values each (K even): repetition
+ * j' (0-based) interleaves the values of left function j' div m and right
+ * function j' mod m, a left value first.  The projections cover K m hash
+ * values per window and dimension instead of K L.  The memory planner
+ * keeps L a square (the largest that fits, at most params.L, 4096 when 0).
+ * The r heuristic projects the sample windows onto the K/2 vectors of
+ * left function 0.  STOP compares the re-derived tensoring bound
+ * (momenti_tensoring_failure_bound of P(dist_max)^d) with delta.  Explicit
+ * hash functions (momenti_set_hash_params) are then 2 m' half functions of
+ * K/2 values, left function l at index 2 l and right function r at
+ * 2 r + 1 (m' >= the m the planner uses). */
+#define MOMENTI_FLAG_TENSORING 4u
 
 /* One motif: windows a < b (0-based), dist_d (Definition distdims),
  * dist_d^max (Eq. distdmax), the dims_d set as a bit mask (bit f = dim f),
@@ -146,7 +159,8 @@ int momenti_default_params(momenti_params* p);
 
 /* Validates *p and creates a handle (no device memory yet).
  * MOMENTI_ERR_ARG: out or p NULL, w < 2, d < 1, k < 1, delta not in (0,1),
- * K not in 1..8, L < 0, unknown precision or delta_mode. */
+ * K not in 1..8, L < 0, unknown precision or delta_mode, or
+ * MOMENTI_FLAG_TENSORING with an odd K. */
 int momenti_create(momenti_handle** out, const momenti_params* p);
 
 /* Releases the handle and every device buffer it holds.  NULL is a no-op. */
@@ -161,9 +175,11 @@ const char* momenti_last_error(const momenti_handle* h);
  * rounded to IEEE half precision (pass half-representable values to make
  * the rounding exact).  u: D*L*K floats in [0, 1), layout [f][j][k];
  * b = u * r.  L here is the number of repetitions supplied; the memory
- * planner uses the first L_used <= L of them.  Copied by the call.
+ * planner uses the first L_used <= L of them.  With MOMENTI_FLAG_TENSORING,
+ * L counts half functions (even; left l at 2 l, right r at 2 r + 1) and K
+ * is their K/2 values.  Copied by the call.
  * MOMENTI_ERR_ARG on NULL pointers, w / K mismatch with the parameters,
- * D not in 1..64, or u outside [0, 1). */
+ * D not in 1..64, an odd L under tensoring, or u outside [0, 1). */
 int momenti_set_hash_params(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
                             const float* a, const float* u);
 
@@ -258,7 +274,9 @@ int momenti_get_keys(momenti_handle* h, int32_t j, uint64_t* keys);
 
 /* The random numbers of the hash functions the index was built with
  * (Eq. drp: a ~ N(0,1)^w, b = u r with u ~ U[0,1)), for the first L_used
- * repetitions (momenti_get_info's L): a D*L*K*w floats, layout [f][j][k][t],
+ * repetitions (momenti_get_info's L; under MOMENTI_FLAG_TENSORING the 2 m
+ * half functions of K/2 values, m^2 = L, laid out as for
+ * momenti_set_hash_params): a D*L*K*w floats, layout [f][j][k][t],
  * as the projections use them (rounded to half precision); u D*L*K floats,
  * layout [f][j][k].  Drawn on the device from seed (Philox4x32-10, Salmon
  * et al. SC'11: counter {q, q >> 32, stream, 0}, key {seed, seed >> 32};
@@ -378,7 +396,7 @@ uint64_t momenti_launch_count(void);
  * Kernel names: split_f32, split_f64, point_major, window_stats,
  * stats_pm, mean16, r_sample, draw, layout_hash, layout_boff,
  * proj_hash_fp32, proj_hash_tc, rehash, sort_init, sort_hist, sort_scan,
- * sort_scatter, sort_local, chunk_agg, chunk_scan, scan_local, scan_top,
+ * sort_scatter, sort_local, tensor_keys, chunk_agg, chunk_scan, scan_local, scan_top,
  * scan_add, collide, bucket_jobs, subbucket, subwarp, hs_clear,
  * verify_events, verify_pairs, allpairs, select_pairs. */
 int momenti_time_kernel(const char* name);

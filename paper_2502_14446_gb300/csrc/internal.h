@@ -108,6 +108,12 @@ cudaError_t launch_proj_hash_tc(const Index& ix, int j0, int j1, uint64_t* flags
 cudaError_t launch_rehash_fp32(const Index& ix, const uint64_t* flags, const uint32_t* flag_count,
                                uint32_t flag_cap, cudaStream_t s);
 
+// ---- k_tensor.cu --------------------------------------------------------
+// Tensoring: keys [j][M][D] of repetitions [j0, j1) of L = m^2 from the keys
+// half [2m][M][D] of the half functions (left l at 2 l, right r at 2 r + 1).
+cudaError_t launch_tensor_keys(const Index& ix, const uint64_t* half, int m, int j0, int j1,
+                               cudaStream_t s);
+
 // ---- k_sort.cu ----------------------------------------------------------
 // Largest chunk one CTA sorts in shared memory (the most-significant-digit
 // partition goes one hash value deeper for larger buckets).

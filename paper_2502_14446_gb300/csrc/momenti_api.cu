@@ -379,6 +379,12 @@ uint64_t job_cap_for(int64_t M, int D) {
   return c;
 }
 
+int isqrt(int x) {
+  int m = 0;
+  while ((m + 1) * (m + 1) <= x) ++m;
+  return m;
+}
+
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
@@ -691,7 +697,8 @@ static int create_impl(momenti_handle** out, const momenti_params* p) {
   if (p->w < 2 || p->d < 1 || p->k < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->K < 1 ||
       p->K > MOMENTI_MAX_K || p->L < 0 ||
       (p->precision != MOMENTI_PREC_FP32 && p->precision != MOMENTI_PREC_F16X2) ||
-      (p->delta_mode != MOMENTI_DELTA_PER_MOTIF && p->delta_mode != MOMENTI_DELTA_ALL_K))
+      (p->delta_mode != MOMENTI_DELTA_PER_MOTIF && p->delta_mode != MOMENTI_DELTA_ALL_K) ||
+      ((p->flags & MOMENTI_FLAG_TENSORING) && (p->K % 2 != 0)))
     return MOMENTI_ERR_ARG;
   auto* h = new momenti_handle();
   h->p = *p;
@@ -715,7 +722,10 @@ const char* momenti_last_error(const momenti_handle* h) {
 static int set_hash_params_impl(momenti_handle* h, int32_t D, int32_t L, int32_t K, int32_t w,
                             const float* a, const float* u) {
   if (!h) return MOMENTI_ERR_ARG;
-  if (!a || !u || D < 1 || D > MOMENTI_MAX_D || L < 1 || K != h->p.K || w != h->p.w)
+  const bool tens = (h->p.flags & MOMENTI_FLAG_TENSORING) != 0;
+  const int K_fn = tens ? h->p.K / 2 : h->p.K;      // values per hash function
+  if (!a || !u || D < 1 || D > MOMENTI_MAX_D || L < 1 || K != K_fn || w != h->p.w ||
+      (tens && L % 2 != 0))
     return fail(h, MOMENTI_ERR_ARG, "set_hash_params: bad sizes");
   const size_t na = size_t(D) * L * K * w, nu = size_t(D) * L * K;
   for (size_t q = 0; q < nu; ++q)
@@ -733,6 +743,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                      int64_t ld, int32_t on_device, void* stream) {
   if (!h) return MOMENTI_ERR_ARG;
   const auto& p = h->p;
+  const bool tens = (p.flags & MOMENTI_FLAG_TENSORING) != 0;
   if (!series || D < 1 || D > MOMENTI_MAX_D || p.d > D || n < p.w || ld < n ||
       (dtype != MOMENTI_F32 && dtype != MOMENTI_F64))
     return fail(h, MOMENTI_ERR_ARG, "hash_all: bad arguments");
@@ -773,7 +784,8 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                              + uint64_t(D) * K * (w + 1) * 4                 // draws
                              + uint64_t(D) * M * kRepStride * 8 / 100;       // rehash flags
     const int L_cap = p.L > 0 ? p.L : 4096;
-    const int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
+    int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
+    if (tens && !h->user_a.empty()) L_user = std::min(L_cap, (h->user_L / 2) * (h->user_L / 2));
     // sort scratch: a batch of repetitions whose ping-pong buffers hold about 640 MB
     // (fewer, fuller launches; measured faster than batches that stay in L2)
     const uint64_t seg_bytes = uint64_t(M) * (8 + 8 + 4 + 4);
@@ -805,6 +817,11 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
       }
       L = lo;
     }
+    if (tens) {                            // tensoring: a square number of repetitions
+      int m = 1;
+      while ((m + 1) * (m + 1) <= L) ++m;
+      L = m * m;
+    }
     sort_reps = std::max(1, std::min(sort_reps, L));
     chunk = std::max(1, std::min(chunk, L));
     h->chunk_reps = chunk;
@@ -819,7 +836,8 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     ix.Wp = Wp;
     ix.excl = p.excl < 0 ? w / 2 : p.excl;
     ix.has_lo = dtype == MOMENTI_F64;
-    const int N = L * kRepStride;
+    // projections per dim: K per repetition, or K/2 per half function
+    const int N = (tens ? 2 * isqrt(L) : L) * kRepStride;
     CK(dalloc(h, &ix.xs_hi, size_t(D) * n));
     if (ix.has_lo) CK(dalloc(h, &ix.xs_lo, size_t(D) * n));
     if (D <= 16) {
@@ -846,8 +864,10 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     CK(dalloc(h, &ix.lcp, size_t(L) * M * D));
     h->draw_a = nullptr;
     h->draw_u = nullptr;
-    const size_t na = h->user_a.empty() ? size_t(D) * L * K * w : h->user_a.size();
-    const size_t nu = h->user_a.empty() ? size_t(D) * L * K : h->user_u.size();
+    const int n_fn = tens ? 2 * isqrt(L) : L;          // hash functions per dim
+    const int K_fn = tens ? K / 2 : K;                 // values per hash function
+    const size_t na = h->user_a.empty() ? size_t(D) * n_fn * K_fn * w : h->user_a.size();
+    const size_t nu = h->user_a.empty() ? size_t(D) * n_fn * K_fn : h->user_u.size();
     CK(dalloc(h, &h->draw_a, na));
     CK(dalloc(h, &h->draw_u, nu));
     h->flag_cap = uint32_t(std::min<uint64_t>(uint64_t(1) << 24,
@@ -897,8 +917,19 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     h->built_gen = h->hp_gen;
     h->built_p = h->p;
   }
-  const int L = ix.L, Wp = ix.Wp, N = L * kRepStride;
-  (void)Wp;
+  const int L = ix.L;
+  // the functions that are projected: the repetitions themselves, or under
+  // tensoring the 2m half functions of K/2 values, whose keys are then
+  // interleaved into the m^2 repetitions' keys
+  const int m_t = tens ? isqrt(L) : 0;
+  Index hx = ix;
+  uint64_t* half = nullptr;
+  if (tens) {
+    hx.L = 2 * m_t;
+    hx.K = K / 2;
+    CK(pool_malloc(&half, size_t(hx.L) * M * D * 8, s));
+    hx.keys = half;
+  }
 
   Timer t_all(s);
   // ---- series: device split into float32 hi (+ lo for float64 input) ----
@@ -917,15 +948,15 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
   CK(launch_stats_point_major(ix, s));
 
   // ---- hash functions ----
-  int L_src = L;
+  int L_src = hx.L;
   if (!h->user_a.empty()) {
     L_src = h->user_L;
     CK(cudaMemcpyAsync(h->draw_a, h->user_a.data(), h->user_a.size() * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->draw_u, h->user_u.data(), h->user_u.size() * 4, cudaMemcpyHostToDevice, s));
   } else {
-    CK(launch_draw_hash(p.seed, D, L, K, w, h->draw_a, h->draw_u, s));
+    CK(launch_draw_hash(p.seed, D, hx.L, hx.K, w, h->draw_a, h->draw_u, s));
   }
-  CK(launch_layout_hash(ix, h->draw_a, L_src, s));
+  CK(launch_layout_hash(hx, h->draw_a, L_src, s));
 
   // ---- r: fixed, or Section 6.1's heuristic ----
   if (p.r > 0) {
@@ -935,7 +966,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     const float init[2] = {INFINITY, -INFINITY};
     CK(cudaMemcpyAsync(mm, init, 8, cudaMemcpyHostToDevice, s));
     const int S = int(std::min<int64_t>(M, 4096));
-    CK(launch_r_sample(ix, S, mm, s));
+    CK(launch_r_sample(hx, S, mm, s));
     float res[2];
     CK(cudaMemcpyAsync(res, mm, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -943,7 +974,9 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     ix.r = (rr > 0 && std::isfinite(rr)) ? rr : 1.0;
   }
   ix.inv_r = float(1.0 / ix.r);
-  CK(launch_layout_boff(ix, h->draw_u, L_src, s));
+  hx.r = ix.r;
+  hx.inv_r = ix.inv_r;
+  CK(launch_layout_boff(hx, h->draw_u, L_src, s));
 
   // ---- projections and hashes of all repetitions ----
   h->used_tc = false;
@@ -953,19 +986,22 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     uint32_t* fcount = reinterpret_cast<uint32_t*>(h->small) + 2;
     int* err = reinterpret_cast<int*>(h->small) + 3;
     CK(cudaMemsetAsync(fcount, 0, 8, s));
-    CK(launch_proj_hash_tc(ix, 0, L, h->flags, h->flag_cap, fcount, err, s));
-    CK(launch_rehash_fp32(ix, h->flags, fcount, h->flag_cap, s));
+    CK(launch_proj_hash_tc(hx, 0, hx.L, h->flags, h->flag_cap, fcount, err, s));
+    CK(launch_rehash_fp32(hx, h->flags, fcount, h->flag_cap, s));
     uint32_t hc[2] = {0, 0};
     CK(cudaMemcpyAsync(hc, fcount, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hc[1]) return fail(h, MOMENTI_ERR_TIMEOUT, "hash_all: tensor-core projection wait timed out");
     h->n_flagged = hc[0];
-    if (hc[0] > h->flag_cap) CK(launch_proj_hash_fp32(ix, 0, L, s));   // flag list overflowed
+    if (hc[0] > h->flag_cap) CK(launch_proj_hash_fp32(hx, 0, hx.L, s));   // flag list overflowed
     else h->used_tc = true;
   } else {
-    CK(launch_proj_hash_fp32(ix, 0, L, s));
+    CK(launch_proj_hash_fp32(hx, 0, hx.L, s));
   }
-  (void)N;
+  if (tens) {
+    CK(launch_tensor_keys(ix, half, m_t, 0, L, s));
+    CK(cudaFreeAsync(half, s));
+  }
 
   // ---- index: sort every (j, f) ----
   Timer t_sort(s);
@@ -986,6 +1022,7 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
   const auto& p = h->p;
   cudaStream_t s = h->stream;
   const int K = ix.K, L = ix.L, d = p.d, k = p.k;
+  const bool tens = (p.flags & MOMENTI_FLAG_TENSORING) != 0;
   const double delta = p.delta_mode == MOMENTI_DELTA_ALL_K ? p.delta / k : p.delta;
   momenti_stats st{};
   st.K = K;
@@ -1112,7 +1149,9 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
         auto& v = by_rep[j - j0];
         if (!v.empty()) pool.add(v.data(), v.size());
         if (pool.valid()) {
-          fb = failure_bound(pool.top.back().dmax, i, j + 1, K, L, d, ix.r);
+          fb = tens ? momenti_tensoring_failure_bound(
+                          std::pow(collision_probability(pool.top.back().dmax, ix.r), d), i, j + 1, K, L)
+                    : failure_bound(pool.top.back().dmax, i, j + 1, K, L, d, ix.r);
           if (fb <= delta) {
             stop_i = i;
             stop_j = j + 1;
@@ -1355,9 +1394,11 @@ int momenti_get_hash_draws(momenti_handle* h, float* a, float* u) {
   const Index& ix = h->ix;
   // the device copies hold L_src repetitions per dim (L_src = L_used for
   // device draws, the supplied count for set_hash_params): copy the first L_used
-  const int L_src = h->user_a.empty() ? ix.L : h->user_L;
-  const size_t ra = size_t(ix.L) * ix.K * ix.w, rs = size_t(L_src) * ix.K * ix.w;
-  const size_t ua = size_t(ix.L) * ix.K, us = size_t(L_src) * ix.K;
+  const bool tens = (h->p.flags & MOMENTI_FLAG_TENSORING) != 0;
+  const int n_fn = tens ? 2 * isqrt(ix.L) : ix.L, K_fn = tens ? ix.K / 2 : ix.K;
+  const int L_src = h->user_a.empty() ? n_fn : h->user_L;
+  const size_t ra = size_t(n_fn) * K_fn * ix.w, rs = size_t(L_src) * K_fn * ix.w;
+  const size_t ua = size_t(n_fn) * K_fn, us = size_t(L_src) * K_fn;
   if (a) CK(cudaMemcpy2DAsync(a, ra * 4, h->draw_a, rs * 4, ra * 4, ix.D, cudaMemcpyDeviceToHost, h->stream));
   if (u) CK(cudaMemcpy2DAsync(u, ua * 4, h->draw_u, us * 4, ua * 4, ix.D, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

@@ -22,6 +22,7 @@ F32, F64 = 0, 1
 PREC_FP32, PREC_F16X2 = 0, 1
 FLAG_TILES_ONLY = 1
 FLAG_NO_COST_SWITCH = 2
+FLAG_TENSORING = 4
 DELTA_PER_MOTIF, DELTA_ALL_K = 0, 1
 MAX_D, MAX_K = 64, 8
 NOALLOC_MAX_KEYS = 262144
@@ -361,10 +362,14 @@ class Momenti:
 
     def hash_draws(self):
         """(a (D, L, K, w), u (D, L, K)) float32: the hash functions' random
-        numbers of the current index."""
+        numbers of the current index (under tensoring the 2m half functions
+        of K/2 values: a (D, 2m, K/2, w))."""
         inf = self.info()
-        a = np.zeros((inf["D"], inf["L"], inf["K"], self.params.w), dtype=np.float32)
-        u = np.zeros((inf["D"], inf["L"], inf["K"]), dtype=np.float32)
+        nf, kf = inf["L"], inf["K"]
+        if self.params.flags & FLAG_TENSORING:            # 2m half functions of K/2 values
+            nf, kf = 2 * int(round(inf["L"] ** 0.5)), inf["K"] // 2
+        a = np.zeros((inf["D"], nf, kf, self.params.w), dtype=np.float32)
+        u = np.zeros((inf["D"], nf, kf), dtype=np.float32)
         self._check(lib.momenti_get_hash_draws(self.h, _ptr(a), _ptr(u)), "momenti_get_hash_draws")
         return a, u
 

@@ -48,7 +48,8 @@ def test_default_params_are_the_papers(mom):
 
 @pytest.mark.parametrize("bad", [dict(w=1), dict(d=0), dict(k=0), dict(delta=0.0),
                                  dict(delta=1.0), dict(K=9), dict(K=0), dict(L=-1),
-                                 dict(precision=7), dict(delta_mode=3)])
+                                 dict(precision=7), dict(delta_mode=3),
+                                 dict(K=7, flags=4)])           # tensoring needs an even K
 def test_create_rejects_bad_parameters(mom, bad):
     p = mom.default_params(**bad)
     h = C.c_void_p()
