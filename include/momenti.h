@@ -215,6 +215,28 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
  * MOMENTI_ERR_STATE before momenti_hash_all. */
 int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats);
 
+/* Section 6.3, motifs of several dimensionalities: the top-k motifs of
+ * every d in [d_low, d_high] from one traversal.  One TOP per d; the
+ * collision condition W >= d uses the smallest d not yet confirmed; every
+ * verified pair is offered to the TOP of every unconfirmed d (its
+ * per-dimension distances give dist_d for all d); after each repetition
+ * every unconfirmed d whose TOP passes STOP (Algorithm 2 with its own d) is
+ * confirmed at that (i, j); each d still unconfirmed when the loop ends
+ * (or when the cost switch chooses it) gets the exact top-k.  Each d's
+ * result carries the guarantee of Lemma topk for that d.  params.d of the
+ * handle is not used.
+ *   out   : (d_high - d_low + 1) * k motifs, row q for d = d_low + q, each
+ *           sorted by (dist_d, a, b) and float64 re-verified;
+ *   n_out : d_high - d_low + 1 counts;
+ *   stops : optional, 2 per d: the (i, j) at which d was confirmed, 0 0 for
+ *           the exact path;
+ *   stats : optional counters (stop_i, stop_j of d_low; fallback = 1 if
+ *           any d took the exact path).
+ * MOMENTI_ERR_ARG unless 1 <= d_low <= d_high <= D; MOMENTI_ERR_STATE
+ * before momenti_hash_all. */
+int momenti_topk_multi(momenti_handle* h, int32_t d_low, int32_t d_high, momenti_motif* out,
+                       int32_t* n_out, int32_t* stops, momenti_stats* stats);
+
 /* The final fallback of Algorithm 1 alone: the exact top-k over all pairs (the quantity
  * of Definition top-k), on the GPU, float64 re-verified.  Same outputs and
  * errors as momenti_topk. */

@@ -624,7 +624,8 @@ def momenti(T: np.ndarray, w: int, d: int, k: int, delta: float, A: np.ndarray,
 
 
 def momenti_multi(T: np.ndarray, w: int, d_low: int, d_high: int, k: int, delta: float,
-                  A: np.ndarray, U: np.ndarray, r: float, excl: int | None = None):
+                  A: np.ndarray, U: np.ndarray, r: float, excl: int | None = None,
+                  keys: np.ndarray | None = None):
     """Section 6.3, motifs of every dimensionality d in [d_low, d_high] in
     one traversal: one TOP per d; a verified pair's per-dimension distances
     give dist_d for every d at once, and the pair is offered to the TOP of
@@ -635,6 +636,9 @@ def momenti_multi(T: np.ndarray, w: int, d_low: int, d_high: int, k: int, delta:
     the loop ends, each d still unconfirmed gets the exact top-k (the final
     fallback of Algorithm 1).
 
+    ``keys`` (uint64 (L, M, D)), when given, replaces the keys hashed from
+    A, U and r (the traversal then runs on those keys).
+
     Returns {d: {"motifs", "stop", "fail_bound"}} and the number of
     distance computations under the key "n_dist"."""
     T = np.asarray(T, dtype=np.float64)
@@ -643,7 +647,8 @@ def momenti_multi(T: np.ndarray, w: int, d_low: int, d_high: int, k: int, delta:
     if not 1 <= d_low <= d_high <= D:
         raise ValueError("need 1 <= d_low <= d_high <= D")
     eps = exclusion_zone(w, excl)
-    keys, _ = hash_all(T, w, A, U, r)
+    if keys is None:
+        keys, _ = hash_all(T, w, A, U, r)
     M = keys.shape[1]
     Z = [znorm_windows(T[f], w) for f in range(D)]
     pools = {d: _Pool(k, eps) for d in range(d_low, d_high + 1)}

@@ -416,8 +416,8 @@ struct Timer {
 // tolerance of the k-th selected one, and selects the top-k again on the
 // float64 distances.  fills out/n_out; returns the max relative float32
 // error over the result.
-int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out, int32_t* n_out,
-             double fail_bound, double* max_err) {
+int finalize(momenti_handle* h, int d, std::vector<PoolEntry> cand, momenti_motif* out,
+             int32_t* n_out, double fail_bound, double* max_err) {
   const Index& ix = h->ix;
   const int k = h->p.k;
   std::sort(cand.begin(), cand.end(), pair_less);
@@ -440,7 +440,7 @@ int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out,
     CK(pool_malloc(&ddd, m * 8, h->stream));
     CK(pool_malloc(&dmask, m * 8, h->stream));
     CK(cudaMemcpyAsync(dp, pk.data(), m * 8, cudaMemcpyHostToDevice, h->stream));
-    CK(launch_verify_pairs(ix, h->p.d, dp, m, 1, dpd, ddd, dmask, h->stream));
+    CK(launch_verify_pairs(ix, d, dp, m, 1, dpd, ddd, dmask, h->stream));
     std::vector<double> per(m * ix.D), dd(m);
     std::vector<uint64_t> mk(m);
     CK(cudaMemcpyAsync(per.data(), dpd, m * ix.D * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -480,7 +480,8 @@ int finalize(momenti_handle* h, std::vector<PoolEntry> cand, momenti_motif* out,
 
 // Exact all-pairs top-k (the final fallback of Algorithm 1).  tau0 <= 0: derive the
 // first threshold from per-window nearest distances.
-int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_out, double* max_err) {
+int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_t* n_out,
+               double* max_err) {
   Index& ix = h->ix;
   const int k = h->p.k;
   double tau = tau0;
@@ -488,7 +489,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     float* rowmin = nullptr;
     CK(pool_malloc(&rowmin, ix.M * 4, h->stream));
     CK(cudaMemsetAsync(rowmin, 0x7f, ix.M * 4, h->stream));
-    CK(launch_allpairs_rowmin(ix, h->p.d, rowmin, h->stream));
+    CK(launch_allpairs_rowmin(ix, d, rowmin, h->stream));
     std::vector<float> rm(ix.M);
     CK(cudaMemcpyAsync(rm.data(), rowmin, ix.M * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaFreeAsync(rowmin, h->stream));
@@ -535,7 +536,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     CK(pool_malloc(&dpd, m * ix.D * 8, h->stream));
     CK(pool_malloc(&ddd, m * 8, h->stream));
     CK(pool_malloc(&dmask, m * 8, h->stream));
-    CK(launch_verify_pairs(ix, h->p.d, dpairs, m, 0, dpd, ddd, dmask, h->stream));
+    CK(launch_verify_pairs(ix, d, dpairs, m, 0, dpd, ddd, dmask, h->stream));
     std::vector<uint64_t> pk(m), mk(m);
     std::vector<double> per(m * ix.D), dd(m);
     CK(cudaMemcpyAsync(pk.data(), dpairs, m * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -564,7 +565,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     return int(acc.size()) == k && got[acc.back()].dd * (1.0 + 1e-4) + 1e-6 <= e;
   };
   // no pair has an approximate distance above this
-  const float all_edge = float(2.0 * std::sqrt(double(ix.w)) * h->p.d * 1.01 + 0.02);
+  const float all_edge = float(2.0 * std::sqrt(double(ix.w)) * d * 1.01 + 0.02);
   constexpr int64_t kBatch = int64_t(1) << 13;   // pairs verified per batch (smallest first)
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
@@ -605,7 +606,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     ar.hist = dhist;
     ar.lo = lo;
     ar.hscale = float(kApBins) / (hi - lo);
-    CK(launch_allpairs(ix, h->p.d, hi, ar, h->stream));
+    CK(launch_allpairs(ix, d, hi, ar, h->stream));
     unsigned long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(hist.data(), dhist, kApBins * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -657,7 +658,7 @@ int exact_path(momenti_handle* h, double tau0, momenti_motif* out, int32_t* n_ou
     release();
     if (done || hi >= all_edge) {
       // done, or every pair is held: fewer than k non-trivial motifs exist
-      rc = finalize(h, got, out, n_out, 0.0, max_err);
+      rc = finalize(h, d, got, out, n_out, 0.0, max_err);
       break;
     }
     lo = hi;
@@ -1014,14 +1015,30 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
   return MOMENTI_OK;
 }
 
-static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
+// Algorithm 1 for the dimensionalities d_low..d_high (Section 6.3; one d
+// is Algorithm 1 as printed).  One TOP per d; collisions use W >= d_cur,
+// the smallest d not yet confirmed; every verified pair is offered to the
+// TOP of every unconfirmed d (its per-dimension distances give dist_d for
+// all d); after each repetition every unconfirmed d whose TOP passes STOP
+// with its own d is confirmed at that (i, j).  A confirmation that raises
+// d_cur in the middle of a chunk of repetitions discards the rest of the
+// chunk, clears the device set of verified pairs (its entries were found
+// under the old condition) and runs the rest again under the new one, so
+// the device follows the printed loop repetition by repetition.  Each d
+// left unconfirmed gets the exact top-k.  out holds k motifs per d,
+// n_out and stops (i, j per d, 0 0 for the exact path) one entry per d.
+static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* out, int32_t* n_out,
+                     int32_t* stops, momenti_stats* stats) {
   if (!h) return MOMENTI_ERR_ARG;
   if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
   if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk before hash_all");
   Index& ix = h->ix;
   const auto& p = h->p;
+  if (d_low < 1 || d_high < d_low || d_high > ix.D)
+    return fail(h, MOMENTI_ERR_ARG, "topk: need 1 <= d_low <= d_high <= D");
   cudaStream_t s = h->stream;
-  const int K = ix.K, L = ix.L, d = p.d, k = p.k;
+  const int K = ix.K, L = ix.L, k = p.k;
+  const int nd = d_high - d_low + 1;
   const bool tens = (p.flags & MOMENTI_FLAG_TENSORING) != 0;
   const double delta = p.delta_mode == MOMENTI_DELTA_ALL_K ? p.delta / k : p.delta;
   momenti_stats st{};
@@ -1030,19 +1047,31 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
   st.r = ix.r;
   st.n_windows = ix.M;
 
-  Pool pool;
-  pool.k = k;
-  pool.eps = ix.excl;
+  struct DState {
+    int d = 0;
+    Pool pool;
+    bool done = false;
+    int stop_i = 0, stop_j = 0;
+    double fb = 1.0;
+    float tau = INFINITY;       // verified pairs at or above it cannot enter this TOP
+  };
+  std::vector<DState> ds(static_cast<size_t>(nd));
+  for (int q = 0; q < nd; ++q) {
+    ds[size_t(q)].d = d_low + q;
+    ds[size_t(q)].pool.k = k;
+    ds[size_t(q)].pool.eps = ix.excl;
+  }
+  auto open_min = [&]() {
+    for (auto& x : ds)
+      if (!x.done) return x.d;
+    return 0;
+  };
   CK(launch_hashset_clear(h->hs, s));
   h->set_fill = 0;
   Timer t_trav(s);
-  int stop_i = 0, stop_j = 0;
-  double fb = 1.0;
-  // Verified pairs at or above tau are dropped on the device; tau only
-  // decreases and TOP is valid while its k-th pair is below it (every pair
-  // below the k-th is then held).
-  float tau = INFINITY;
   std::vector<std::vector<PairRec>> by_rep(h->chunk_reps);
+  std::vector<PairRec> recd;                 // one record per dimensionality (several d)
+  std::vector<double> per_dim, srt;
   unsigned long long* cnt = h->cnt_host;
   // MOMENTI_TRACE=1 prints one line per chunk (level, repetitions, work counts, TOP state)
   const char* tr = std::getenv("MOMENTI_TRACE");
@@ -1050,11 +1079,18 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
   // cost switch: each level opens with a one-repetition probe
   const bool cost_switch = !(p.flags & MOMENTI_FLAG_NO_COST_SWITCH) && L > 1;
   int switch_level = 0;
-  for (int i = K; i >= 1 && !stop_i && !switch_level; --i) {
+  int d_cur = d_low;
+  for (int i = K; i >= 1 && d_cur && !switch_level; --i) {
     int j1 = 0;
-    for (int j0 = 0; j0 < L && !stop_i && !switch_level; j0 = j1) {
+    for (int j0 = 0; j0 < L && d_cur && !switch_level; j0 = j1) {
       const bool probe = cost_switch && j0 == 0;
       j1 = probe ? 1 : std::min(L, j0 + h->chunk_reps);
+      const int d = d_cur;
+      // device threshold: a pair is kept if it may enter the TOP of some
+      // unconfirmed d (dist_d >= dist_{d_cur})
+      float tau = 0.f;
+      for (auto& x : ds)
+        if (!x.done) tau = std::max(tau, x.tau);
       const auto tc0 = std::chrono::steady_clock::now();
       bool used_sub = false;
       unsigned long long tiles = 0;
@@ -1132,6 +1168,25 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
           CK(cudaStreamSynchronize(s));
         }
       }
+      // several dimensionalities: the per-dimension distances of every
+      // record (the float32 form of the verification), and from them
+      // dist_d, dist_d^max and dims_d for each d of the range
+      if (nd > 1 && nrec) {
+        std::vector<uint64_t> pk(nrec);
+        for (uint64_t q = 0; q < nrec; ++q)
+          pk[q] = (uint64_t(h->rec_host[q].a) << 32) | h->rec_host[q].b;
+        uint64_t* dp = nullptr;
+        double* dpd = nullptr;
+        CK(pool_malloc(&dp, nrec * 8, s));
+        CK(pool_malloc(&dpd, nrec * ix.D * 8, s));
+        CK(cudaMemcpyAsync(dp, pk.data(), nrec * 8, cudaMemcpyHostToDevice, s));
+        CK(launch_verify_pairs(ix, d, dp, int64_t(nrec), 0, dpd, nullptr, nullptr, s));
+        per_dim.resize(nrec * ix.D);
+        CK(cudaMemcpyAsync(per_dim.data(), dpd, nrec * ix.D * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaFreeAsync(dp, s));
+        CK(cudaFreeAsync(dpd, s));
+        CK(cudaStreamSynchronize(s));
+      }
       if (h->set_fill * 2 > h->hs.cap) {
         CK(launch_hashset_clear(h->hs, s));
         h->set_fill = 0;
@@ -1143,18 +1198,64 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
       for (uint64_t q = 0; q < nrec; ++q) {
         int jj = h->rec_host[q].j - j0;
         if (jj < 0 || jj >= j1 - j0) return fail(h, MOMENTI_ERR_CUDA, "topk: bad repetition tag");
-        by_rep[jj].push_back(h->rec_host[q]);
+        PairRec rr = h->rec_host[q];
+        rr.pad = uint32_t(q);                // row of the record's per-dimension distances
+        by_rep[jj].push_back(rr);
       }
       for (int j = j0; j < j1; ++j) {
         auto& v = by_rep[j - j0];
-        if (!v.empty()) pool.add(v.data(), v.size());
-        if (pool.valid()) {
-          fb = tens ? momenti_tensoring_failure_bound(
-                          std::pow(collision_probability(pool.top.back().dmax, ix.r), d), i, j + 1, K, L)
-                    : failure_bound(pool.top.back().dmax, i, j + 1, K, L, d, ix.r);
-          if (fb <= delta) {
-            stop_i = i;
-            stop_j = j + 1;
+        for (auto& x : ds) {
+          if (x.done || v.empty()) continue;
+          if (nd == 1) {
+            x.pool.add(v.data(), v.size());
+            continue;
+          }
+          // this d's distances: the sum of the d smallest per-dimension ones
+          recd.assign(v.begin(), v.end());
+          for (auto& rc : recd) {
+            const double* pd = per_dim.data() + size_t(rc.pad) * ix.D;
+            srt.assign(pd, pd + ix.D);
+            std::vector<int> ord(static_cast<size_t>(ix.D));
+            for (int f = 0; f < ix.D; ++f) ord[size_t(f)] = f;
+            std::stable_sort(ord.begin(), ord.end(), [&](int u, int w2) { return srt[size_t(u)] < srt[size_t(w2)]; });
+            double sum = 0.0, mx = 0.0;
+            uint64_t mask = 0;
+            for (int q = 0; q < x.d; ++q) {
+              const double val = srt[size_t(ord[size_t(q)])];
+              sum += val;
+              mx = std::max(mx, val);
+              mask |= uint64_t(1) << ord[size_t(q)];
+            }
+            rc.dist_d = float(sum);
+            rc.dist_max = float(mx);
+            rc.dims = mask;
+          }
+          x.pool.add(recd.data(), recd.size());
+        }
+        bool confirmed = false;
+        for (auto& x : ds) {
+          if (x.done || !x.pool.valid()) continue;
+          const double pr = std::pow(collision_probability(x.pool.top.back().dmax, ix.r), x.d);
+          const double fbx = tens ? momenti_tensoring_failure_bound(pr, i, j + 1, K, L)
+                                  : failure_bound(x.pool.top.back().dmax, i, j + 1, K, L, x.d, ix.r);
+          if (fbx <= delta) {
+            x.done = true;
+            x.stop_i = i;
+            x.stop_j = j + 1;
+            x.fb = fbx;
+            confirmed = true;
+          }
+        }
+        if (confirmed) {
+          const int nc = open_min();
+          if (nc != d_cur) {
+            d_cur = nc;
+            if (nc && j + 1 < j1) {
+              // the rest of the chunk ran under the old condition: again
+              CK(launch_hashset_clear(h->hs, s));
+              h->set_fill = 0;
+              j1 = j + 1;
+            }
             break;
           }
         }
@@ -1163,24 +1264,28 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
       st.t_host_ms += std::chrono::duration<double, std::milli>(tc1 - th0).count();
       if (trace)
         std::fprintf(stderr,
-                     "momenti trace: i=%d j=[%d,%d) sub=%d events=%llu tiles=%llu lb_pruned=%llu "
+                     "momenti trace: i=%d j=[%d,%d) d=%d sub=%d events=%llu tiles=%llu lb_pruned=%llu "
                      "records=%llu top=%d kth=%.5g ms=%.3f\n",
-                     i, j0, j1, int(used_sub), cnt[0], tiles, cnt[3], (unsigned long long)nrec,
-                     int(pool.top.size()), pool.top.empty() ? -1.0 : pool.kth(),
+                     i, j0, j1, d, int(used_sub), cnt[0], tiles, cnt[3], (unsigned long long)nrec,
+                     int(ds[0].pool.top.size()), ds[0].pool.top.empty() ? -1.0 : ds[0].pool.kth(),
                      std::chrono::duration<double, std::milli>(tc1 - tc0).count());
-      if (int(pool.top.size()) == k) {
-        const float t2 = float(1.1 * pool.kth() + 1e-6);
-        if (t2 < tau) tau = t2;
-        pool.tau_trunc = std::min(pool.tau_trunc, double(tau));
+      for (auto& x : ds) {
+        if (x.done || int(x.pool.top.size()) != k) continue;
+        const float t2 = float(1.1 * x.pool.kth() + 1e-6);
+        if (t2 < x.tau) x.tau = t2;
+        x.pool.tau_trunc = std::min(x.pool.tau_trunc, double(x.tau));
       }
-      if (probe && !stop_i) {
+      if (probe && d_cur) {
         // the rest of this level, and the lower levels (shorter prefixes
-        // collide more: each costs at least as much as this one)
+        // collide more: each costs at least as much as this one), against
+        // the exact path of every open d
         const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
         const double rep = predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events,
                                           verified, nrec);
         const double rest = double(L - 1) * rep + double(i - 1) * double(L) * rep;
-        const double exact = predict_exact_ms(ix, int(pool.top.size()) == k ? 1 : 2);
+        double exact = 0.0;
+        for (auto& x : ds)
+          if (!x.done) exact += predict_exact_ms(ix, int(x.pool.top.size()) == k ? 1 : 2);
         if (rest > exact) {
           switch_level = i;
           st.predicted_rest_ms = rest;
@@ -1191,34 +1296,47 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
   }
   st.switch_level = switch_level;
   st.t_traverse_ms = t_trav.stop();
-  st.n_pool = int64_t(pool.items.size());
-  pool.sort_all();
   double max_err = 0;
-  int rc;
-  if (stop_i) {
-    st.stop_i = stop_i;
-    st.stop_j = stop_j;
-    // every pool pair at or below the k-th, for the float64 re-check
-    std::vector<PoolEntry> cand;
-    const double lim = pool.kth() * (1.0 + 1e-3) + 1e-5;
-    for (auto& c : pool.items)
-      if (c.dd <= lim) cand.push_back(c);
-    rc = finalize(h, cand, out, n_out, fb, &max_err);
-  } else {
-    st.fallback = 1;
-    Timer t_fb(s);
-    double tau0 = (int(pool.top.size()) == k) ? pool.kth() * 1.05 + 1e-6 : 0.0;
-    rc = exact_path(h, tau0, out, n_out, &max_err);
-    st.t_fallback_ms = t_fb.stop();
+  Timer t_fb(s);
+  bool any_exact = false;
+  for (int q = 0; q < nd; ++q) {
+    DState& x = ds[size_t(q)];
+    momenti_motif* o = out + size_t(q) * k;
+    int32_t* no = n_out + q;
+    st.n_pool += int64_t(x.pool.items.size());
+    x.pool.sort_all();
+    double err = 0;
+    int rc;
+    if (x.done) {
+      // every pool pair at or below the k-th, for the float64 re-check
+      std::vector<PoolEntry> cand;
+      const double lim = x.pool.kth() * (1.0 + 1e-3) + 1e-5;
+      for (auto& c : x.pool.items)
+        if (c.dd <= lim) cand.push_back(c);
+      rc = finalize(h, x.d, cand, o, no, x.fb, &err);
+    } else {
+      any_exact = true;
+      double tau0 = (int(x.pool.top.size()) == k) ? x.pool.kth() * 1.05 + 1e-6 : 0.0;
+      rc = exact_path(h, x.d, tau0, o, no, &err);
+    }
+    if (rc != MOMENTI_OK) return rc;
+    // float32 traversal distances vs the float64 result
+    for (int t = 0; t < *no; ++t) {
+      uint64_t key = (uint64_t(o[t].a) << 32) | uint64_t(o[t].b);
+      for (auto& c : x.pool.items)
+        if (((uint64_t(c.a) << 32) | c.b) == key && o[t].dist_d > 0)
+          err = std::max(err, std::fabs(c.dd - o[t].dist_d) / o[t].dist_d);
+    }
+    max_err = std::max(max_err, err);
+    if (stops) {
+      stops[2 * q] = x.stop_i;
+      stops[2 * q + 1] = x.stop_j;
+    }
   }
-  if (rc != MOMENTI_OK) return rc;
-  // float32 traversal distances vs the float64 result
-  for (int q = 0; q < *n_out; ++q) {
-    uint64_t key = (uint64_t(out[q].a) << 32) | uint64_t(out[q].b);
-    for (auto& c : pool.items)
-      if (((uint64_t(c.a) << 32) | c.b) == key && out[q].dist_d > 0)
-        max_err = std::max(max_err, std::fabs(c.dd - out[q].dist_d) / out[q].dist_d);
-  }
+  st.t_fallback_ms = any_exact ? t_fb.stop() : 0.0;
+  st.fallback = any_exact ? 1 : 0;
+  st.stop_i = ds[0].stop_i;
+  st.stop_j = ds[0].stop_j;
   st.max_rel_err_fp32 = max_err;
   st.t_hash_ms = h->t_hash_ms;
   st.t_sort_ms = h->t_sort_ms;
@@ -1229,12 +1347,17 @@ static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, mome
   return MOMENTI_OK;
 }
 
+static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
+  if (!h) return MOMENTI_ERR_ARG;
+  return topk_core(h, h->p.d, h->p.d, out, n_out, nullptr, stats);
+}
+
 static int topk_exact_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out) {
   if (!h) return MOMENTI_ERR_ARG;
   if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk_exact: NULL output");
   if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk_exact before hash_all");
   double err = 0;
-  return exact_path(h, 0.0, out, n_out, &err);
+  return exact_path(h, h->p.d, 0.0, out, n_out, &err);
 }
 
 static int topk_batch_impl(int32_t B, const momenti_params* params, const void* const* series,
@@ -1482,6 +1605,17 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
 int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
   try {
     return topk_impl(h, out, n_out, stats);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_topk_multi(momenti_handle* h, int32_t d_low, int32_t d_high, momenti_motif* out,
+                       int32_t* n_out, int32_t* stops, momenti_stats* stats) {
+  try {
+    return topk_core(h, d_low, d_high, out, n_out, stops, stats);
   } catch (const std::bad_alloc&) {
     return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
   } catch (...) {

@@ -35,7 +35,7 @@ EXPORTS = (
     "momenti_get_index", "momenti_collide", "momenti_launch_count", "momenti_time_kernel",
     "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
     "momenti_collision_probability", "momenti_failure_bound", "momenti_top_select",
-    "momenti_tensoring_failure_bound", "momenti_get_hash_draws",
+    "momenti_tensoring_failure_bound", "momenti_get_hash_draws", "momenti_topk_multi",
 )
 
 
@@ -83,6 +83,8 @@ def _load():
                                        C.c_int32, vp]),
         "momenti_topk": (C.c_int, [vp, P(momenti_motif), P(C.c_int32), P(momenti_stats)]),
         "momenti_topk_exact": (C.c_int, [vp, P(momenti_motif), P(C.c_int32)]),
+        "momenti_topk_multi": (C.c_int, [vp, C.c_int32, C.c_int32, P(momenti_motif),
+                                         P(C.c_int32), P(C.c_int32), P(momenti_stats)]),
         "momenti_verify": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, C.c_int32]),
         "momenti_get_info": (C.c_int, [vp, P(C.c_int64), P(C.c_int32), P(C.c_int32),
                                        P(C.c_int32), P(C.c_double)]),
@@ -327,6 +329,23 @@ class Momenti:
         self._check(lib.momenti_topk(self.h, buf, C.byref(n), C.byref(st)), "momenti_topk")
         stats = {name: getattr(st, name) for name, _ in momenti_stats._fields_}
         return self._motifs(buf, n.value), stats
+
+    def topk_multi(self, d_low: int, d_high: int):
+        """Section 6.3: {d: (motifs, (stop_i, stop_j))} for d_low..d_high,
+        and the stats of the traversal."""
+        k = self.params.k
+        nd = d_high - d_low + 1
+        buf = (momenti_motif * (k * max(nd, 1)))()
+        n = (C.c_int32 * max(nd, 1))()
+        stops = (C.c_int32 * (2 * max(nd, 1)))()
+        st = momenti_stats()
+        self._check(lib.momenti_topk_multi(self.h, d_low, d_high, buf, n, stops, C.byref(st)),
+                    "momenti_topk_multi")
+        out = {}
+        for q in range(nd):
+            out[d_low + q] = (self._motifs(buf[q * k:(q + 1) * k], n[q]),
+                              (stops[2 * q], stops[2 * q + 1]))
+        return out, {name: getattr(st, name) for name, _ in momenti_stats._fields_}
 
     def topk_exact(self):
         k = self.params.k
