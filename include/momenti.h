@@ -237,6 +237,40 @@ int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_
 int momenti_topk_multi(momenti_handle* h, int32_t d_low, int32_t d_high, momenti_motif* out,
                        int32_t* n_out, int32_t* stops, momenti_stats* stats);
 
+/* ---- anytime search (Section 4, the remark after Algorithm 1) ---------
+ * The traversal of momenti_topk / momenti_topk_multi as a search that can
+ * be advanced, inspected and resumed: TOP only ever admits better pairs, so
+ * at any point it holds candidate motifs whose miss probability the bound
+ * of Lemma stop gives for the repetitions done so far.
+ *   momenti_search_begin   starts a search for d_low..d_high (one d for the
+ *                          plain problem) on the current index, replacing
+ *                          any search in progress;
+ *   momenti_search_step    advances it by at least one and at most max_reps
+ *                          repetitions (fewer at the end); *ended (may be
+ *                          NULL) becomes 1 once STOP held for every d, the
+ *                          cost switch chose the exact path, or the loop
+ *                          ran out; further steps are no-ops;
+ *   momenti_search_current the current TOP of every d: out (k per d, as
+ *                          momenti_topk_multi), n_out per d; each motif's
+ *                          fail_bound is the bound of Lemma stop for its own
+ *                          dist_d^max after the last repetition processed
+ *                          (1 before any; the confirming value for a d that
+ *                          STOP confirmed); distances are the traversal's
+ *                          float32 form; cursor (3 ints, may be NULL): the
+ *                          last (i, j) processed and the ended flag;
+ *   momenti_search_finish  completes it (the rest of the traversal, the
+ *                          float64 re-verification, the exact top-k of any d
+ *                          STOP did not confirm) with the outputs of
+ *                          momenti_topk_multi, and ends the search.
+ * momenti_hash_all ends a search in progress.  MOMENTI_ERR_STATE without a
+ * search (or before momenti_hash_all); MOMENTI_ERR_ARG for bad d bounds or
+ * max_reps < 1. */
+int momenti_search_begin(momenti_handle* h, int32_t d_low, int32_t d_high);
+int momenti_search_step(momenti_handle* h, int64_t max_reps, int32_t* ended);
+int momenti_search_current(momenti_handle* h, momenti_motif* out, int32_t* n_out, int32_t* cursor);
+int momenti_search_finish(momenti_handle* h, momenti_motif* out, int32_t* n_out, int32_t* stops,
+                          momenti_stats* stats);
+
 /* The final fallback of Algorithm 1 alone: the exact top-k over all pairs (the quantity
  * of Definition top-k), on the GPU, float64 re-verified.  Same outputs and
  * errors as momenti_topk. */

@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -192,6 +193,28 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// TOP and stopping state of one dimensionality d.
+struct DState {
+  int d = 0;
+  Pool pool;
+  bool done = false;
+  int stop_i = 0, stop_j = 0;
+  double fb = 1.0;
+  float tau = INFINITY;       // verified pairs at or above it cannot enter this TOP
+};
+
+// A traversal in progress (the anytime search): one state per d, and the
+// cursor (level i, next repetition j0) where the next chunk starts.
+struct SearchState {
+  int d_low = 0, d_high = 0;
+  std::vector<DState> ds;
+  int i = 0, j0 = 0, d_cur = 0;
+  int last_i = 0, last_j = 0;     // the last repetition processed (1-based j), 0 0 before any
+  int switch_level = 0;
+  bool ended = false;             // STOP for every d, the cost switch, or the loop's end
+  momenti_stats st{};
+};
+
 }  // namespace
 
 struct momenti_handle {
@@ -231,6 +254,7 @@ struct momenti_handle {
   cudaStream_t own_stream = nullptr;        // created for the batching form
   momenti_params built_p{};                 // parameters the index was built with
   size_t rec_host_cap = 0;                  // pinned record buffer (kept across rebuilds)
+  std::unique_ptr<SearchState> search;      // the traversal in progress, if any
 };
 
 namespace {
@@ -758,6 +782,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                      std::memcmp(&h->built_p, &h->p, sizeof(momenti_params)) == 0;
   if (!reuse) free_all(h);
   h->ready = false;
+  h->search.reset();                       // a search in progress ends with its index
   // buffers last used on another stream: let that work finish first
   if (h->stream != static_cast<cudaStream_t>(stream) && !h->bufs.empty())
     cudaStreamSynchronize(h->stream);
@@ -1016,59 +1041,64 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
 }
 
 // Algorithm 1 for the dimensionalities d_low..d_high (Section 6.3; one d
-// is Algorithm 1 as printed).  One TOP per d; collisions use W >= d_cur,
-// the smallest d not yet confirmed; every verified pair is offered to the
-// TOP of every unconfirmed d (its per-dimension distances give dist_d for
-// all d); after each repetition every unconfirmed d whose TOP passes STOP
-// with its own d is confirmed at that (i, j).  A confirmation that raises
-// d_cur in the middle of a chunk of repetitions discards the rest of the
-// chunk, clears the device set of verified pairs (its entries were found
-// under the old condition) and runs the rest again under the new one, so
-// the device follows the printed loop repetition by repetition.  Each d
-// left unconfirmed gets the exact top-k.  out holds k motifs per d,
-// n_out and stops (i, j per d, 0 0 for the exact path) one entry per d.
-static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* out, int32_t* n_out,
-                     int32_t* stops, momenti_stats* stats) {
+// is Algorithm 1 as printed), as a resumable search.  One TOP per d;
+// collisions use W >= d_cur, the smallest d not yet confirmed; every
+// verified pair is offered to the TOP of every unconfirmed d (its
+// per-dimension distances give dist_d for all d); after each repetition
+// every unconfirmed d whose TOP passes STOP with its own d is confirmed at
+// that (i, j).  A confirmation that raises d_cur in the middle of a chunk
+// of repetitions discards the rest of the chunk, clears the device set of
+// verified pairs (its entries were found under the old condition) and runs
+// the rest again under the new one, so the device follows the printed loop
+// repetition by repetition.  Each d left unconfirmed gets the exact top-k.
+static int search_begin_impl(momenti_handle* h, int d_low, int d_high) {
   if (!h) return MOMENTI_ERR_ARG;
-  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
-  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk before hash_all");
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "search before hash_all");
+  const Index& ix = h->ix;
+  if (d_low < 1 || d_high < d_low || d_high > ix.D)
+    return fail(h, MOMENTI_ERR_ARG, "search: need 1 <= d_low <= d_high <= D");
+  auto ss = std::make_unique<SearchState>();
+  ss->d_low = d_low;
+  ss->d_high = d_high;
+  ss->ds.resize(size_t(d_high - d_low + 1));
+  for (int q = 0; q <= d_high - d_low; ++q) {
+    ss->ds[size_t(q)].d = d_low + q;
+    ss->ds[size_t(q)].pool.k = h->p.k;
+    ss->ds[size_t(q)].pool.eps = ix.excl;
+  }
+  ss->i = ix.K;
+  ss->j0 = 0;
+  ss->d_cur = d_low;
+  ss->st.K = ix.K;
+  ss->st.L = ix.L;
+  ss->st.r = ix.r;
+  ss->st.n_windows = ix.M;
+  CK(launch_hashset_clear(h->hs, h->stream));
+  h->set_fill = 0;
+  h->search = std::move(ss);
+  return MOMENTI_OK;
+}
+
+// Runs chunks of repetitions until max_reps repetitions have been processed
+// (at least one chunk) or the traversal has ended.
+static int search_step_impl(momenti_handle* h, int64_t max_reps, int32_t* ended) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->search) return fail(h, MOMENTI_ERR_STATE, "search_step without search_begin");
+  SearchState& S = *h->search;
   Index& ix = h->ix;
   const auto& p = h->p;
-  if (d_low < 1 || d_high < d_low || d_high > ix.D)
-    return fail(h, MOMENTI_ERR_ARG, "topk: need 1 <= d_low <= d_high <= D");
   cudaStream_t s = h->stream;
   const int K = ix.K, L = ix.L, k = p.k;
-  const int nd = d_high - d_low + 1;
+  const int nd = S.d_high - S.d_low + 1;
   const bool tens = (p.flags & MOMENTI_FLAG_TENSORING) != 0;
   const double delta = p.delta_mode == MOMENTI_DELTA_ALL_K ? p.delta / k : p.delta;
-  momenti_stats st{};
-  st.K = K;
-  st.L = L;
-  st.r = ix.r;
-  st.n_windows = ix.M;
-
-  struct DState {
-    int d = 0;
-    Pool pool;
-    bool done = false;
-    int stop_i = 0, stop_j = 0;
-    double fb = 1.0;
-    float tau = INFINITY;       // verified pairs at or above it cannot enter this TOP
-  };
-  std::vector<DState> ds(static_cast<size_t>(nd));
-  for (int q = 0; q < nd; ++q) {
-    ds[size_t(q)].d = d_low + q;
-    ds[size_t(q)].pool.k = k;
-    ds[size_t(q)].pool.eps = ix.excl;
-  }
+  momenti_stats& st = S.st;
+  std::vector<DState>& ds = S.ds;
   auto open_min = [&]() {
     for (auto& x : ds)
       if (!x.done) return x.d;
     return 0;
   };
-  CK(launch_hashset_clear(h->hs, s));
-  h->set_fill = 0;
-  Timer t_trav(s);
   std::vector<std::vector<PairRec>> by_rep(h->chunk_reps);
   std::vector<PairRec> recd;                 // one record per dimensionality (several d)
   std::vector<double> per_dim, srt;
@@ -1078,230 +1108,308 @@ static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* ou
   const bool trace = tr && tr[0] == '1';
   // cost switch: each level opens with a one-repetition probe
   const bool cost_switch = !(p.flags & MOMENTI_FLAG_NO_COST_SWITCH) && L > 1;
-  int switch_level = 0;
-  int d_cur = d_low;
-  for (int i = K; i >= 1 && d_cur && !switch_level; --i) {
-    int j1 = 0;
-    for (int j0 = 0; j0 < L && d_cur && !switch_level; j0 = j1) {
-      const bool probe = cost_switch && j0 == 0;
-      j1 = probe ? 1 : std::min(L, j0 + h->chunk_reps);
-      const int d = d_cur;
-      // device threshold: a pair is kept if it may enter the TOP of some
-      // unconfirmed d (dist_d >= dist_{d_cur})
-      float tau = 0.f;
-      for (auto& x : ds)
-        if (!x.done) tau = std::max(tau, x.tau);
-      const auto tc0 = std::chrono::steady_clock::now();
-      bool used_sub = false;
-      unsigned long long tiles = 0;
-      // collision counting (prefix length 1: buckets split by a second
-      // dimension when every bucket fits a CTA); grow the event list, or
-      // halve the chunk beyond the event budget
-      for (;;) {
-        bool sub = false;
-        unsigned long long jc[5] = {0, 0, 0, 0, 0};
-        if (i <= 3 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
-          CK(cudaMemsetAsync(h->job_counts, 0, 5 * sizeof(unsigned long long), s));
-          CK(launch_bucket_jobs(ix, i, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
-          CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-          const uint64_t qcap = h->job_cap / 4;
-          sub = jc[0] <= qcap && jc[2] <= qcap && jc[3] <= qcap && jc[4] <= qcap &&
-                jc[1] <= uint64_t(subbucket_cap(ix.D, i));
-        }
-        CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
-        used_sub = sub;
-        if (sub) {
-          CK(launch_subbucket(ix, i, j0, j1, d, h->hs, h->cs, h->jobs, h->job_cap, h->job_counts,
-                              int(jc[1]), s));
-        } else {
-          CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
-          const int64_t E = int64_t(j1 - j0) * ix.D * ((ix.M + 31) / 32);
-          CK(cudaMemcpyAsync(&cnt[5], h->cs.ntile + E, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        }
-        CK(cudaMemcpyAsync(cnt, h->cs.counters, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        if (sub) CK(cudaMemcpyAsync(&cnt[5], h->cs.counters + 5, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  Timer t_trav(s);
+  int64_t reps_done = 0;
+  while (!S.ended && (reps_done == 0 || reps_done < max_reps)) {
+    if (S.j0 >= L) {                         // the level is complete
+      S.j0 = 0;
+      if (--S.i < 1) {
+        S.ended = true;
+        break;
+      }
+    }
+    const int i = S.i, j0 = S.j0;
+    const bool probe = cost_switch && j0 == 0;
+    int j1 = probe ? 1 : std::min(L, j0 + h->chunk_reps);
+    if (max_reps > 0 && j1 - j0 > max_reps - reps_done)          // the caller's step size
+      j1 = j0 + int(std::max<int64_t>(1, max_reps - reps_done));
+    const int d = S.d_cur;
+    // device threshold: a pair is kept if it may enter the TOP of some
+    // unconfirmed d (dist_d >= dist_{d_cur})
+    float tau = 0.f;
+    for (auto& x : ds)
+      if (!x.done) tau = std::max(tau, x.tau);
+    const auto tc0 = std::chrono::steady_clock::now();
+    bool used_sub = false;
+    unsigned long long tiles = 0;
+    // collision counting (prefix length 1: buckets split by a second
+    // dimension when every bucket fits a CTA); grow the event list, or
+    // halve the chunk beyond the event budget
+    for (;;) {
+      bool sub = false;
+      unsigned long long jc[5] = {0, 0, 0, 0, 0};
+      if (i <= 3 && d >= 2 && ix.D <= 16 && h->jobs && !(p.flags & MOMENTI_FLAG_TILES_ONLY)) {
+        CK(cudaMemsetAsync(h->job_counts, 0, 5 * sizeof(unsigned long long), s));
+        CK(launch_bucket_jobs(ix, i, j0, j1, d, h->jobs, h->job_cap, h->job_counts, s));
+        CK(cudaMemcpyAsync(jc, h->job_counts, sizeof(jc), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        tiles = cnt[5];
-        if (cnt[0] <= h->cs.ev_cap) break;
-        const uint64_t cap = next_pow2(cnt[0]);
-        if (cap * sizeof(Event) > h->ev_budget && j1 - j0 > 1) {
-          j1 = j0 + (j1 - j0) / 2;
+        const uint64_t qcap = h->job_cap / 4;
+        sub = jc[0] <= qcap && jc[2] <= qcap && jc[3] <= qcap && jc[4] <= qcap &&
+              jc[1] <= uint64_t(subbucket_cap(ix.D, i));
+      }
+      CK(cudaMemsetAsync(h->cs.counters, 0, 8 * sizeof(unsigned long long), s));
+      used_sub = sub;
+      if (sub) {
+        CK(launch_subbucket(ix, i, j0, j1, d, h->hs, h->cs, h->jobs, h->job_cap, h->job_counts,
+                            int(jc[1]), s));
+      } else {
+        CK(launch_collide(ix, i, j0, j1, d, h->hs, h->cs, 0, nullptr, 0, s));
+        const int64_t E = int64_t(j1 - j0) * ix.D * ((ix.M + 31) / 32);
+        CK(cudaMemcpyAsync(&cnt[5], h->cs.ntile + E, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      }
+      CK(cudaMemcpyAsync(cnt, h->cs.counters, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      if (sub) CK(cudaMemcpyAsync(&cnt[5], h->cs.counters + 5, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      tiles = cnt[5];
+      if (cnt[0] <= h->cs.ev_cap) break;
+      const uint64_t cap = next_pow2(cnt[0]);
+      if (cap * sizeof(Event) > h->ev_budget && j1 - j0 > 1) {
+        j1 = j0 + (j1 - j0) / 2;
+        continue;
+      }
+      Event* ev = nullptr;
+      CK(dalloc(h, &ev, size_t(cap)));
+      h->cs.events = ev;
+      h->cs.ev_cap = cap;
+    }
+    st.n_candidates += int64_t(cnt[0]);
+    st.n_verified += int64_t(cnt[0]);
+    const uint64_t checks = used_sub ? tiles : tiles * 1024;
+    st.n_pair_checks += int64_t(checks);
+    const uint64_t n_events = cnt[0];
+    uint64_t nrec = 0;
+    if (cnt[0]) {
+      for (;;) {
+        CK(launch_verify_events(ix, d, h->hs, h->cs, tau, h->rec_dev, h->rec_cap, s));
+        CK(cudaMemcpyAsync(cnt, h->cs.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (cnt[1] <= h->rec_cap) break;
+        // grow the record buffers and verify the chunk's events again
+        const uint64_t cap = next_pow2(cnt[1]);
+        PairRec* rec = nullptr;
+        CK(dalloc(h, &rec, size_t(cap)));
+        if (h->rec_host_cap < cap) {
+          PairRec* rh = nullptr;
+          CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
+          cudaFreeHost(h->rec_host);
+          h->rec_host = rh;
+          h->rec_host_cap = cap;
+        }
+        h->rec_dev = rec;
+        h->rec_cap = cap;
+        CK(cudaMemsetAsync(h->cs.counters + 1, 0, 7 * sizeof(unsigned long long), s));
+      }
+      nrec = cnt[1];
+      h->set_fill += cnt[2];
+      if (nrec) {
+        CK(cudaMemcpyAsync(h->rec_host, h->rec_dev, nrec * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
+    }
+    // several dimensionalities: the per-dimension distances of every
+    // record (the float32 form of the verification), and from them
+    // dist_d, dist_d^max and dims_d for each d of the range
+    if (nd > 1 && nrec) {
+      std::vector<uint64_t> pk(nrec);
+      for (uint64_t q = 0; q < nrec; ++q)
+        pk[q] = (uint64_t(h->rec_host[q].a) << 32) | h->rec_host[q].b;
+      uint64_t* dp = nullptr;
+      double* dpd = nullptr;
+      CK(pool_malloc(&dp, nrec * 8, s));
+      CK(pool_malloc(&dpd, nrec * ix.D * 8, s));
+      CK(cudaMemcpyAsync(dp, pk.data(), nrec * 8, cudaMemcpyHostToDevice, s));
+      CK(launch_verify_pairs(ix, d, dp, int64_t(nrec), 0, dpd, nullptr, nullptr, s));
+      per_dim.resize(nrec * ix.D);
+      CK(cudaMemcpyAsync(per_dim.data(), dpd, nrec * ix.D * 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaFreeAsync(dp, s));
+      CK(cudaFreeAsync(dpd, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    if (h->set_fill * 2 > h->hs.cap) {
+      CK(launch_hashset_clear(h->hs, s));
+      h->set_fill = 0;
+    }
+    ++st.n_chunks;
+    const auto th0 = std::chrono::steady_clock::now();
+    st.n_lb_pruned += int64_t(cnt[3]);
+    for (auto& v : by_rep) v.clear();
+    for (uint64_t q = 0; q < nrec; ++q) {
+      int jj = h->rec_host[q].j - j0;
+      if (jj < 0 || jj >= j1 - j0) return fail(h, MOMENTI_ERR_CUDA, "topk: bad repetition tag");
+      PairRec rr = h->rec_host[q];
+      rr.pad = uint32_t(q);                // row of the record's per-dimension distances
+      by_rep[jj].push_back(rr);
+    }
+    for (int j = j0; j < j1; ++j) {
+      auto& v = by_rep[j - j0];
+      for (auto& x : ds) {
+        if (x.done || v.empty()) continue;
+        if (nd == 1) {
+          x.pool.add(v.data(), v.size());
           continue;
         }
-        Event* ev = nullptr;
-        CK(dalloc(h, &ev, size_t(cap)));
-        h->cs.events = ev;
-        h->cs.ev_cap = cap;
-      }
-      st.n_candidates += int64_t(cnt[0]);
-      st.n_verified += int64_t(cnt[0]);
-      const uint64_t checks = used_sub ? tiles : tiles * 1024;
-      st.n_pair_checks += int64_t(checks);
-      const uint64_t n_events = cnt[0];
-      uint64_t nrec = 0;
-      if (cnt[0]) {
-        for (;;) {
-          CK(launch_verify_events(ix, d, h->hs, h->cs, tau, h->rec_dev, h->rec_cap, s));
-          CK(cudaMemcpyAsync(cnt, h->cs.counters, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-          if (cnt[1] <= h->rec_cap) break;
-          // grow the record buffers and verify the chunk's events again
-          const uint64_t cap = next_pow2(cnt[1]);
-          PairRec* rec = nullptr;
-          CK(dalloc(h, &rec, size_t(cap)));
-          if (h->rec_host_cap < cap) {
-            PairRec* rh = nullptr;
-            CK(cudaMallocHost(&rh, cap * sizeof(PairRec)));
-            cudaFreeHost(h->rec_host);
-            h->rec_host = rh;
-            h->rec_host_cap = cap;
+        // this d's distances: the sum of the d smallest per-dimension ones
+        recd.assign(v.begin(), v.end());
+        std::vector<int> ord(static_cast<size_t>(ix.D));
+        for (auto& rc : recd) {
+          const double* pd = per_dim.data() + size_t(rc.pad) * ix.D;
+          srt.assign(pd, pd + ix.D);
+          for (int f = 0; f < ix.D; ++f) ord[size_t(f)] = f;
+          std::stable_sort(ord.begin(), ord.end(),
+                           [&](int u, int w2) { return srt[size_t(u)] < srt[size_t(w2)]; });
+          double sum = 0.0, mx = 0.0;
+          uint64_t mask = 0;
+          for (int q = 0; q < x.d; ++q) {
+            const double val = srt[size_t(ord[size_t(q)])];
+            sum += val;
+            mx = std::max(mx, val);
+            mask |= uint64_t(1) << ord[size_t(q)];
           }
-          h->rec_dev = rec;
-          h->rec_cap = cap;
-          CK(cudaMemsetAsync(h->cs.counters + 1, 0, 7 * sizeof(unsigned long long), s));
+          rc.dist_d = float(sum);
+          rc.dist_max = float(mx);
+          rc.dims = mask;
         }
-        nrec = cnt[1];
-        h->set_fill += cnt[2];
-        if (nrec) {
-          CK(cudaMemcpyAsync(h->rec_host, h->rec_dev, nrec * sizeof(PairRec), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
-        }
+        x.pool.add(recd.data(), recd.size());
       }
-      // several dimensionalities: the per-dimension distances of every
-      // record (the float32 form of the verification), and from them
-      // dist_d, dist_d^max and dims_d for each d of the range
-      if (nd > 1 && nrec) {
-        std::vector<uint64_t> pk(nrec);
-        for (uint64_t q = 0; q < nrec; ++q)
-          pk[q] = (uint64_t(h->rec_host[q].a) << 32) | h->rec_host[q].b;
-        uint64_t* dp = nullptr;
-        double* dpd = nullptr;
-        CK(pool_malloc(&dp, nrec * 8, s));
-        CK(pool_malloc(&dpd, nrec * ix.D * 8, s));
-        CK(cudaMemcpyAsync(dp, pk.data(), nrec * 8, cudaMemcpyHostToDevice, s));
-        CK(launch_verify_pairs(ix, d, dp, int64_t(nrec), 0, dpd, nullptr, nullptr, s));
-        per_dim.resize(nrec * ix.D);
-        CK(cudaMemcpyAsync(per_dim.data(), dpd, nrec * ix.D * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaFreeAsync(dp, s));
-        CK(cudaFreeAsync(dpd, s));
-        CK(cudaStreamSynchronize(s));
-      }
-      if (h->set_fill * 2 > h->hs.cap) {
-        CK(launch_hashset_clear(h->hs, s));
-        h->set_fill = 0;
-      }
-      ++st.n_chunks;
-      const auto th0 = std::chrono::steady_clock::now();
-      st.n_lb_pruned += int64_t(cnt[3]);
-      for (auto& v : by_rep) v.clear();
-      for (uint64_t q = 0; q < nrec; ++q) {
-        int jj = h->rec_host[q].j - j0;
-        if (jj < 0 || jj >= j1 - j0) return fail(h, MOMENTI_ERR_CUDA, "topk: bad repetition tag");
-        PairRec rr = h->rec_host[q];
-        rr.pad = uint32_t(q);                // row of the record's per-dimension distances
-        by_rep[jj].push_back(rr);
-      }
-      for (int j = j0; j < j1; ++j) {
-        auto& v = by_rep[j - j0];
-        for (auto& x : ds) {
-          if (x.done || v.empty()) continue;
-          if (nd == 1) {
-            x.pool.add(v.data(), v.size());
-            continue;
-          }
-          // this d's distances: the sum of the d smallest per-dimension ones
-          recd.assign(v.begin(), v.end());
-          for (auto& rc : recd) {
-            const double* pd = per_dim.data() + size_t(rc.pad) * ix.D;
-            srt.assign(pd, pd + ix.D);
-            std::vector<int> ord(static_cast<size_t>(ix.D));
-            for (int f = 0; f < ix.D; ++f) ord[size_t(f)] = f;
-            std::stable_sort(ord.begin(), ord.end(), [&](int u, int w2) { return srt[size_t(u)] < srt[size_t(w2)]; });
-            double sum = 0.0, mx = 0.0;
-            uint64_t mask = 0;
-            for (int q = 0; q < x.d; ++q) {
-              const double val = srt[size_t(ord[size_t(q)])];
-              sum += val;
-              mx = std::max(mx, val);
-              mask |= uint64_t(1) << ord[size_t(q)];
-            }
-            rc.dist_d = float(sum);
-            rc.dist_max = float(mx);
-            rc.dims = mask;
-          }
-          x.pool.add(recd.data(), recd.size());
-        }
-        bool confirmed = false;
-        for (auto& x : ds) {
-          if (x.done || !x.pool.valid()) continue;
-          const double pr = std::pow(collision_probability(x.pool.top.back().dmax, ix.r), x.d);
-          const double fbx = tens ? momenti_tensoring_failure_bound(pr, i, j + 1, K, L)
-                                  : failure_bound(x.pool.top.back().dmax, i, j + 1, K, L, x.d, ix.r);
-          if (fbx <= delta) {
-            x.done = true;
-            x.stop_i = i;
-            x.stop_j = j + 1;
-            x.fb = fbx;
-            confirmed = true;
-          }
-        }
-        if (confirmed) {
-          const int nc = open_min();
-          if (nc != d_cur) {
-            d_cur = nc;
-            if (nc && j + 1 < j1) {
-              // the rest of the chunk ran under the old condition: again
-              CK(launch_hashset_clear(h->hs, s));
-              h->set_fill = 0;
-              j1 = j + 1;
-            }
-            break;
-          }
-        }
-      }
-      const auto tc1 = std::chrono::steady_clock::now();
-      st.t_host_ms += std::chrono::duration<double, std::milli>(tc1 - th0).count();
-      if (trace)
-        std::fprintf(stderr,
-                     "momenti trace: i=%d j=[%d,%d) d=%d sub=%d events=%llu tiles=%llu lb_pruned=%llu "
-                     "records=%llu top=%d kth=%.5g ms=%.3f\n",
-                     i, j0, j1, d, int(used_sub), cnt[0], tiles, cnt[3], (unsigned long long)nrec,
-                     int(ds[0].pool.top.size()), ds[0].pool.top.empty() ? -1.0 : ds[0].pool.kth(),
-                     std::chrono::duration<double, std::milli>(tc1 - tc0).count());
+      S.last_i = i;
+      S.last_j = j + 1;
+      ++reps_done;
+      bool confirmed = false;
       for (auto& x : ds) {
-        if (x.done || int(x.pool.top.size()) != k) continue;
-        const float t2 = float(1.1 * x.pool.kth() + 1e-6);
-        if (t2 < x.tau) x.tau = t2;
-        x.pool.tau_trunc = std::min(x.pool.tau_trunc, double(x.tau));
+        if (x.done || !x.pool.valid()) continue;
+        const double pr = std::pow(collision_probability(x.pool.top.back().dmax, ix.r), x.d);
+        const double fbx = tens ? momenti_tensoring_failure_bound(pr, i, j + 1, K, L)
+                                : failure_bound(x.pool.top.back().dmax, i, j + 1, K, L, x.d, ix.r);
+        if (fbx <= delta) {
+          x.done = true;
+          x.stop_i = i;
+          x.stop_j = j + 1;
+          x.fb = fbx;
+          confirmed = true;
+        }
       }
-      if (probe && d_cur) {
-        // the rest of this level, and the lower levels (shorter prefixes
-        // collide more: each costs at least as much as this one), against
-        // the exact path of every open d
-        const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
-        const double rep = predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events,
-                                          verified, nrec);
-        const double rest = double(L - 1) * rep + double(i - 1) * double(L) * rep;
-        double exact = 0.0;
-        for (auto& x : ds)
-          if (!x.done) exact += predict_exact_ms(ix, int(x.pool.top.size()) == k ? 1 : 2);
-        if (rest > exact) {
-          switch_level = i;
-          st.predicted_rest_ms = rest;
-          st.predicted_exact_ms = exact;
+      if (confirmed) {
+        const int nc = open_min();
+        if (nc != S.d_cur) {
+          S.d_cur = nc;
+          if (!nc) S.ended = true;
+          if (nc && j + 1 < j1) {
+            // the rest of the chunk ran under the old condition: again
+            CK(launch_hashset_clear(h->hs, s));
+            h->set_fill = 0;
+            j1 = j + 1;
+          }
+          break;
         }
       }
     }
+    S.j0 = j1;
+    const auto tc1 = std::chrono::steady_clock::now();
+    st.t_host_ms += std::chrono::duration<double, std::milli>(tc1 - th0).count();
+    if (trace)
+      std::fprintf(stderr,
+                   "momenti trace: i=%d j=[%d,%d) d=%d sub=%d events=%llu tiles=%llu lb_pruned=%llu "
+                   "records=%llu top=%d kth=%.5g ms=%.3f\n",
+                   i, j0, j1, d, int(used_sub), cnt[0], tiles, cnt[3], (unsigned long long)nrec,
+                   int(ds[0].pool.top.size()), ds[0].pool.top.empty() ? -1.0 : ds[0].pool.kth(),
+                   std::chrono::duration<double, std::milli>(tc1 - tc0).count());
+    for (auto& x : ds) {
+      if (x.done || int(x.pool.top.size()) != k) continue;
+      const float t2 = float(1.1 * x.pool.kth() + 1e-6);
+      if (t2 < x.tau) x.tau = t2;
+      x.pool.tau_trunc = std::min(x.pool.tau_trunc, double(x.tau));
+    }
+    if (probe && !S.ended) {
+      // the rest of this level, and the lower levels (shorter prefixes
+      // collide more: each costs at least as much as this one), against
+      // the exact path of every open d
+      const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
+      const double rep = predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events,
+                                        verified, nrec);
+      const double rest = double(L - 1) * rep + double(i - 1) * double(L) * rep;
+      double exact = 0.0;
+      for (auto& x : ds)
+        if (!x.done) exact += predict_exact_ms(ix, int(x.pool.top.size()) == k ? 1 : 2);
+      if (rest > exact) {
+        S.switch_level = i;
+        S.ended = true;
+        st.predicted_rest_ms = rest;
+        st.predicted_exact_ms = exact;
+      }
+    }
   }
-  st.switch_level = switch_level;
-  st.t_traverse_ms = t_trav.stop();
+  st.t_traverse_ms += t_trav.stop();
+  if (ended) *ended = S.ended ? 1 : 0;
+  return MOMENTI_OK;
+}
+
+// TOP of every d now (the anytime property: each candidate comes with the
+// miss-probability bound of its own dist_d^max after the repetitions done
+// so far).  Distances are those of the traversal (float32 form).
+static int search_current_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out,
+                               int32_t* cursor) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->search) return fail(h, MOMENTI_ERR_STATE, "search_current without search_begin");
+  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "search_current: NULL output");
+  const SearchState& S = *h->search;
+  const Index& ix = h->ix;
+  const int k = h->p.k;
+  const bool tens = (h->p.flags & MOMENTI_FLAG_TENSORING) != 0;
+  for (size_t q = 0; q < S.ds.size(); ++q) {
+    const DState& x = S.ds[q];
+    int c = 0;
+    for (const PoolEntry& e : x.pool.top) {
+      momenti_motif& m = out[q * size_t(k) + size_t(c)];
+      m.a = e.a;
+      m.b = e.b;
+      m.dist_d = e.dd;
+      m.dist_max = e.dmax;
+      m.dims_mask = e.dims;
+      double fb = 1.0;
+      if (x.done) {
+        fb = x.fb;
+      } else if (S.last_j > 0) {
+        const double pr = std::pow(collision_probability(e.dmax, ix.r), x.d);
+        fb = tens ? momenti_tensoring_failure_bound(pr, S.last_i, S.last_j, ix.K, ix.L)
+                  : failure_bound(e.dmax, S.last_i, S.last_j, ix.K, ix.L, x.d, ix.r);
+      }
+      m.fail_bound = fb;
+      if (++c == k) break;
+    }
+    n_out[q] = c;
+  }
+  if (cursor) {
+    cursor[0] = S.last_i;
+    cursor[1] = S.last_j;
+    cursor[2] = S.ended ? 1 : 0;
+  }
+  return MOMENTI_OK;
+}
+
+// Completes the search: the rest of the traversal, then each d's result
+// (float64 re-verified; the exact top-k for a d that STOP did not confirm).
+// out holds k motifs per d, n_out and stops (i, j per d, 0 0 for the exact
+// path) one entry per d.  The search ends with this call.
+static int search_finish_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out,
+                              int32_t* stops, momenti_stats* stats) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!h->search) return fail(h, MOMENTI_ERR_STATE, "search_finish without search_begin");
+  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
+  while (!h->search->ended) {
+    int r = search_step_impl(h, int64_t(1) << 40, nullptr);
+    if (r != MOMENTI_OK) return r;
+  }
+  SearchState& S = *h->search;
+  cudaStream_t s = h->stream;
+  const int k = h->p.k;
+  momenti_stats& st = S.st;
+  st.switch_level = S.switch_level;
   double max_err = 0;
   Timer t_fb(s);
   bool any_exact = false;
-  for (int q = 0; q < nd; ++q) {
-    DState& x = ds[size_t(q)];
-    momenti_motif* o = out + size_t(q) * k;
+  for (size_t q = 0; q < S.ds.size(); ++q) {
+    DState& x = S.ds[q];
+    momenti_motif* o = out + q * size_t(k);
     int32_t* no = n_out + q;
     st.n_pool += int64_t(x.pool.items.size());
     x.pool.sort_all();
@@ -1335,8 +1443,8 @@ static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* ou
   }
   st.t_fallback_ms = any_exact ? t_fb.stop() : 0.0;
   st.fallback = any_exact ? 1 : 0;
-  st.stop_i = ds[0].stop_i;
-  st.stop_j = ds[0].stop_j;
+  st.stop_i = S.ds[0].stop_i;
+  st.stop_j = S.ds[0].stop_j;
   st.max_rel_err_fp32 = max_err;
   st.t_hash_ms = h->t_hash_ms;
   st.t_sort_ms = h->t_sort_ms;
@@ -1344,7 +1452,20 @@ static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* ou
   st.precision_used = h->used_tc ? MOMENTI_PREC_F16X2 : MOMENTI_PREC_FP32;
   st.n_rehashed = h->n_flagged;
   if (stats) *stats = st;
+  h->search.reset();
   return MOMENTI_OK;
+}
+
+static int topk_core(momenti_handle* h, int d_low, int d_high, momenti_motif* out, int32_t* n_out,
+                     int32_t* stops, momenti_stats* stats) {
+  if (!h) return MOMENTI_ERR_ARG;
+  if (!out || !n_out) return fail(h, MOMENTI_ERR_ARG, "topk: NULL output");
+  if (!h->ready) return fail(h, MOMENTI_ERR_STATE, "topk before hash_all");
+  int r = search_begin_impl(h, d_low, d_high);
+  if (r != MOMENTI_OK) return r;
+  r = search_finish_impl(h, out, n_out, stops, stats);
+  h->search.reset();
+  return r;
 }
 
 static int topk_impl(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
@@ -1605,6 +1726,46 @@ int momenti_hash_all(momenti_handle* h, const void* series, int32_t dtype, int64
 int momenti_topk(momenti_handle* h, momenti_motif* out, int32_t* n_out, momenti_stats* stats) {
   try {
     return topk_impl(h, out, n_out, stats);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_search_begin(momenti_handle* h, int32_t d_low, int32_t d_high) {
+  try {
+    return search_begin_impl(h, d_low, d_high);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_search_step(momenti_handle* h, int64_t max_reps, int32_t* ended) {
+  try {
+    if (max_reps < 1) return fail(h, MOMENTI_ERR_ARG, "search_step: max_reps < 1");
+    return search_step_impl(h, max_reps, ended);
+  } catch (const std::bad_alloc&) {
+    return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_search_current(momenti_handle* h, momenti_motif* out, int32_t* n_out, int32_t* cursor) {
+  try {
+    return search_current_impl(h, out, n_out, cursor);
+  } catch (...) {
+    return fail(h, MOMENTI_ERR_CUDA, "unexpected internal error");
+  }
+}
+
+int momenti_search_finish(momenti_handle* h, momenti_motif* out, int32_t* n_out, int32_t* stops,
+                          momenti_stats* stats) {
+  try {
+    return search_finish_impl(h, out, n_out, stops, stats);
   } catch (const std::bad_alloc&) {
     return fail(h, MOMENTI_ERR_MEMORY, "host memory exhausted");
   } catch (...) {

@@ -36,6 +36,8 @@ EXPORTS = (
     "momenti_kernel_time", "momenti_index_sort_noalloc", "momenti_topk_batch",
     "momenti_collision_probability", "momenti_failure_bound", "momenti_top_select",
     "momenti_tensoring_failure_bound", "momenti_get_hash_draws", "momenti_topk_multi",
+    "momenti_search_begin", "momenti_search_step", "momenti_search_current",
+    "momenti_search_finish",
 )
 
 
@@ -85,6 +87,11 @@ def _load():
         "momenti_topk_exact": (C.c_int, [vp, P(momenti_motif), P(C.c_int32)]),
         "momenti_topk_multi": (C.c_int, [vp, C.c_int32, C.c_int32, P(momenti_motif),
                                          P(C.c_int32), P(C.c_int32), P(momenti_stats)]),
+        "momenti_search_begin": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "momenti_search_step": (C.c_int, [vp, C.c_int64, P(C.c_int32)]),
+        "momenti_search_current": (C.c_int, [vp, P(momenti_motif), P(C.c_int32), P(C.c_int32)]),
+        "momenti_search_finish": (C.c_int, [vp, P(momenti_motif), P(C.c_int32), P(C.c_int32),
+                                            P(momenti_stats)]),
         "momenti_verify": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, C.c_int32]),
         "momenti_get_info": (C.c_int, [vp, P(C.c_int64), P(C.c_int32), P(C.c_int32),
                                        P(C.c_int32), P(C.c_double)]),
@@ -345,6 +352,44 @@ class Momenti:
         for q in range(nd):
             out[d_low + q] = (self._motifs(buf[q * k:(q + 1) * k], n[q]),
                               (stops[2 * q], stops[2 * q + 1]))
+        return out, {name: getattr(st, name) for name, _ in momenti_stats._fields_}
+
+    # ---- anytime search ----
+    def search_begin(self, d_low: int | None = None, d_high: int | None = None):
+        d_low = self.params.d if d_low is None else d_low
+        d_high = d_low if d_high is None else d_high
+        self._search = (d_low, d_high)
+        self._check(lib.momenti_search_begin(self.h, d_low, d_high), "momenti_search_begin")
+
+    def search_step(self, max_reps: int = 1) -> bool:
+        """Advances the search; True once the traversal has ended."""
+        ended = C.c_int32()
+        self._check(lib.momenti_search_step(self.h, max_reps, C.byref(ended)), "momenti_search_step")
+        return bool(ended.value)
+
+    def search_current(self):
+        """({d: motifs with their current miss bounds}, (i, j, ended))."""
+        d_low, d_high = self._search
+        k, nd = self.params.k, d_high - d_low + 1
+        buf = (momenti_motif * (k * nd))()
+        n = (C.c_int32 * nd)()
+        cur = (C.c_int32 * 3)()
+        self._check(lib.momenti_search_current(self.h, buf, n, cur), "momenti_search_current")
+        return ({d_low + q: self._motifs(buf[q * k:(q + 1) * k], n[q]) for q in range(nd)},
+                (cur[0], cur[1], bool(cur[2])))
+
+    def search_finish(self):
+        """The final results, as topk_multi returns them."""
+        d_low, d_high = self._search
+        k, nd = self.params.k, d_high - d_low + 1
+        buf = (momenti_motif * (k * nd))()
+        n = (C.c_int32 * nd)()
+        stops = (C.c_int32 * (2 * nd))()
+        st = momenti_stats()
+        self._check(lib.momenti_search_finish(self.h, buf, n, stops, C.byref(st)),
+                    "momenti_search_finish")
+        out = {d_low + q: (self._motifs(buf[q * k:(q + 1) * k], n[q]),
+                           (stops[2 * q], stops[2 * q + 1])) for q in range(nd)}
         return out, {name: getattr(st, name) for name, _ in momenti_stats._fields_}
 
     def topk_exact(self):

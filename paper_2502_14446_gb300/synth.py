@@ -210,6 +210,17 @@ def tiny(seed: int, n: int, D: int, w: int, d: int, k: int = 2, n_motifs: int = 
                     planted=planted, seed=seed)
 
 
+def with_noise_dims(wl: Workload, extra: int, seed: int = 0) -> Workload:
+    """The robustness workload of Section 7 (impact of noise): ``wl`` with
+    ``extra`` more dimensions appended, each an independent Gaussian random
+    walk that holds no planted motif."""
+    rng = _rng(9000 + seed)
+    noise = random_walk(rng, extra, wl.n).astype(wl.series.dtype)
+    T = np.ascontiguousarray(np.concatenate([wl.series, noise], axis=0))
+    return Workload(f"{wl.name}+{extra}noise", T, wl.w, wl.d, wl.k, wl.delta, wl.mem_limit,
+                    planted=list(wl.planted), seed=wl.seed)
+
+
 # --------------------------------------------------------------------------
 # random numbers of the hash family, Eq. (drp)
 # --------------------------------------------------------------------------
