@@ -1,0 +1,150 @@
+/*
+ * exact_pairs.c - TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
+ *
+ * Every non-trivial pair of length-w windows of a D-dimensional series
+ * whose d-dimensional distance dist_d is at most tau, in float64, by the
+ * textbook matrix-profile recurrence along diagonals.  It shares no code
+ * with the CUDA library and nothing on the product path may call it; the
+ * tests, the golden-value script and the benchmark's CPU baseline do.
+ *
+ * What it computes (Section 3.1 of the paper; readings stated in the
+ * oracle's Python header):
+ *   - each dimension less its overall mean (a shift: z-normalised windows
+ *     are unchanged), then per dimension f and window a: mean mu and
+ *     population sigma (two passes over the window);
+ *   - for every pair a < b with b - a > excl, per dimension, the raw dot
+ *     product QT of the two windows, slid along the diagonal
+ *     (QT(a+1, b+1) = QT(a, b) - x_a x_b + x_{a+w} x_{b+w}) and recomputed
+ *     directly every 1024 steps;
+ *   - the z-normalised Euclidean distance (Eq. zned) in its Pearson form,
+ *     dist^2 = 2 w (1 - (QT - w mu_a mu_b) / (w sigma_a sigma_b)), clamped
+ *     at 0; a flat window (sigma <= flat_rel (1 + |mu|)) z-normalises to the
+ *     zero vector: distance 0 to another flat window, sqrt(w) to any other;
+ *   - dist_d = the sum of the d smallest per-dimension distances
+ *     (Definition distdims), dims_d those d dimensions (ties to the lower
+ *     index), dist_d^max the largest of them (Eq. distdmax).
+ * Diagonals are shared among threads (OpenMP); the output order is not
+ * specified (the caller sorts).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+typedef struct {
+  int64_t a, b;
+  double dist_d, dist_max;
+  uint64_t dims;
+} oracle_pair;
+
+static void window_stats(const double* x, int64_t M, int w, double* mu, double* sg) {
+  for (int64_t a = 0; a < M; ++a) {
+    double s = 0.0;
+    for (int t = 0; t < w; ++t) s += x[a + t];
+    const double m = s / w;
+    double v = 0.0;
+    for (int t = 0; t < w; ++t) v += (x[a + t] - m) * (x[a + t] - m);
+    mu[a] = m;
+    sg[a] = sqrt(v / w);
+  }
+}
+
+static double dot(const double* x, int64_t a, int64_t b, int w) {
+  double s = 0.0;
+  for (int t = 0; t < w; ++t) s += x[a + t] * x[b + t];
+  return s;
+}
+
+/* Pairs with dist_d <= tau into out (at most cap of them); returns how many
+ * there are in all (may exceed cap), or -1 if memory runs out. */
+int64_t oracle_pairs_below(const double* T, int D, int64_t n, int w, int d, int64_t excl,
+                           double tau, double flat_rel, oracle_pair* out, int64_t cap) {
+  const int64_t M = n - w + 1;
+  if (M < 1 || D < 1 || D > 64 || d < 1 || d > D) return 0;
+  double* mu = malloc(sizeof(double) * (size_t)(D * M));
+  double* sg = malloc(sizeof(double) * (size_t)(D * M));
+  unsigned char* flat = malloc((size_t)(D * M));
+  /* each dimension less its overall mean: z-normalised windows do not
+     change, and the raw dot products of the Pearson form lose less to
+     cancellation */
+  double* X = malloc(sizeof(double) * (size_t)(D * n));
+  if (!mu || !sg || !flat || !X) {
+    free(mu); free(sg); free(flat); free(X);
+    return -1;
+  }
+  for (int f = 0; f < D; ++f) {
+    double s = 0.0;
+    for (int64_t t = 0; t < n; ++t) s += T[(int64_t)f * n + t];
+    const double c = s / (double)n;
+    for (int64_t t = 0; t < n; ++t) X[(int64_t)f * n + t] = T[(int64_t)f * n + t] - c;
+    window_stats(X + (int64_t)f * n, M, w, mu + (int64_t)f * M, sg + (int64_t)f * M);
+    /* flat relative to the window's own level (before the shift) */
+    for (int64_t a = 0; a < M; ++a)
+      flat[(int64_t)f * M + a] = sg[(int64_t)f * M + a] <= flat_rel * (1.0 + fabs(mu[(int64_t)f * M + a] + c));
+  }
+  T = X;
+  int64_t found = 0;
+#pragma omp parallel
+  {
+    double qt[64], dist[64];
+    int ord[64];
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t delta = excl + 1; delta < M; ++delta) {
+      for (int64_t a = 0; a + delta < M; ++a) {
+        const int64_t b = a + delta;
+        for (int f = 0; f < D; ++f) {
+          const double* x = T + (int64_t)f * n;
+          if (a % 1024 == 0)
+            qt[f] = dot(x, a, b, w);
+          else
+            qt[f] = qt[f] - x[a - 1] * x[b - 1] + x[a + w - 1] * x[b + w - 1];
+          const int64_t ia = (int64_t)f * M + a, ib = (int64_t)f * M + b;
+          double df;
+          if (flat[ia] || flat[ib]) {
+            df = (flat[ia] && flat[ib]) ? 0.0 : sqrt((double)w);
+          } else {
+            const double corr = (qt[f] - w * mu[ia] * mu[ib]) / (w * sg[ia] * sg[ib]);
+            const double sq = 2.0 * w * (1.0 - corr);
+            df = sqrt(sq > 0.0 ? sq : 0.0);
+          }
+          dist[f] = df;
+        }
+        /* the d smallest, ties to the lower dimension: insertion into an
+           ordered list of dimension indices */
+        int m = 0;
+        for (int f = 0; f < D; ++f) {
+          int p = m < d ? m : d;
+          while (p > 0 && dist[ord[p - 1]] > dist[f]) --p;
+          if (p >= d) continue;
+          const int last = m < d ? m : d - 1;
+          for (int q = last; q > p; --q) ord[q] = ord[q - 1];
+          ord[p] = f;
+          if (m < d) ++m;
+        }
+        double sum = 0.0, mx = 0.0;
+        uint64_t dims = 0;
+        for (int q = 0; q < d; ++q) {
+          sum += dist[ord[q]];
+          if (dist[ord[q]] > mx) mx = dist[ord[q]];
+          dims |= (uint64_t)1 << ord[q];
+        }
+        if (sum <= tau) {
+          int64_t slot;
+#pragma omp atomic capture
+          slot = found++;
+          if (slot < cap) {
+            out[slot].a = a;
+            out[slot].b = b;
+            out[slot].dist_d = sum;
+            out[slot].dist_max = mx;
+            out[slot].dims = dims;
+          }
+        }
+      }
+    }
+  }
+  free(mu);
+  free(sg);
+  free(flat);
+  free(X);
+  return found;
+}

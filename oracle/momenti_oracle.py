@@ -271,6 +271,77 @@ def exact_topk(T: np.ndarray, w: int, d: int, k: int, excl: int | None = None,
     return acc
 
 
+_PAIR = np.dtype([("a", np.int64), ("b", np.int64), ("dist_d", np.float64),
+                  ("dist_max", np.float64), ("dims", np.uint64)])
+_CLIB = None
+
+
+def _pairs_lib():
+    """The oracle's C pair enumeration (exact_pairs.c), built on first use."""
+    global _CLIB
+    if _CLIB is None:
+        import ctypes as C
+        from oracle import build_c
+        lib = C.CDLL(build_c.build())
+        fn = lib.oracle_pairs_below
+        fn.restype = C.c_int64
+        fn.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int64, C.c_double,
+                       C.c_double, C.c_void_p, C.c_int64]
+        _CLIB = fn
+    return _CLIB
+
+
+def pairs_below(T: np.ndarray, w: int, d: int, tau: float, excl: int | None = None) -> np.ndarray:
+    """Every non-trivial pair (b - a > eps) with dist_d <= tau, as a record
+    array (a, b, dist_d, dist_max, dims mask), sorted by (dist_d, a, b).
+    Computed by exact_pairs.c: float64 sliding dot products along the
+    diagonals (recomputed directly every 1024 steps) in the Pearson form of
+    Eq. zned, the d smallest per-dimension distances (ties to the lower
+    dimension), flat windows as in znorm_windows."""
+    import ctypes as C
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    D, n = T.shape
+    eps = exclusion_zone(w, excl)
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, dtype=_PAIR)
+        cnt = _pairs_lib()(T.ctypes.data_as(C.c_void_p), D, n, w, d, eps, float(tau), FLAT_REL,
+                           out.ctypes.data_as(C.c_void_p), cap)
+        if cnt < 0:
+            raise MemoryError("exact_pairs: out of memory")
+        if cnt <= cap:
+            out = out[:cnt]
+            return out[np.lexsort((out["b"], out["a"], out["dist_d"]))]
+        cap = 1 << int(cnt - 1).bit_length()
+
+
+def exact_topk_diag(T, w, d, k, excl=None, tau0: float = 1.0):
+    """The exact top-k (same quantity and record format as exact_topk) from
+    pairs_below: collect every pair with dist_d <= tau, select greedily in
+    (dist_d, a, b) order, and double tau until k pairs are selected with
+    the k-th at or below tau (then no unseen pair can change the
+    selection).  Fewer than k are returned only when tau covers every pair
+    (2 d sqrt(w), the largest possible dist_d)."""
+    eps = exclusion_zone(w, excl)
+    tau = float(tau0)
+    top = 2.0 * d * math.sqrt(w)
+    while True:
+        cands = pairs_below(T, w, d, tau, excl)
+        acc = []
+        for c in cands:
+            a, b = int(c["a"]), int(c["b"])
+            if any(abs(a - q[1]) <= eps or abs(a - q[2]) <= eps or abs(b - q[1]) <= eps
+                   or abs(b - q[2]) <= eps for q in acc):
+                continue
+            dims = tuple(f for f in range(64) if int(c["dims"]) >> f & 1)
+            acc.append((float(c["dist_d"]), a, b, dims, float(c["dist_max"])))
+            if len(acc) == k:
+                break
+        if (len(acc) == k and acc[-1][0] <= tau) or tau >= top:
+            return acc
+        tau *= 2.0
+
+
 def exact_topk_auto(T, w, d, k, excl=None, tau0: float | None = None, block: int = 512):
     """exact_topk with tau doubled until k pairs are selected (tau0 = None
     means no threshold)."""

@@ -877,32 +877,55 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   }
 }
 
-// Wide series (D > 16): per-window means and 1/sigma are read per step.
+// Wide series (D > 16): per-window means and 1/sigma are read per step;
+// every thread of a block walks the same row windows a (their values are
+// broadcast loads) against its own diagonal.  Only the D centred cross
+// products live in registers: the row centring (the block's first row
+// window mean) and each thread's column centring sit in shared memory, and
+// a pair's squared distances are computed twice, the second time only for
+// a pair that has at least d dims within the threshold (the square roots
+// and the sum of the d smallest).
 template <int DM, bool ROWMIN>
-__global__ void __launch_bounds__(kDiagBlock)
+__global__ void __launch_bounds__(kDiagBlock, DM <= 32 ? 3 : 2)
 k_allpairs_wide(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin, int64_t ybase) {
+  extern __shared__ float wd_smem[];
+  float* s_ca = wd_smem;                         // [DM]
+  float* s_cb = wd_smem + DM;                    // [DM][kDiagBlock]
   const int64_t delta = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * kDiagBlock + threadIdx.x;
   const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  const int D = ix.D, w = ix.w;
+  if (threadIdx.x < DM) s_ca[threadIdx.x] = int(threadIdx.x) < D ? ix.mu_hi[int64_t(threadIdx.x) * ix.M + a0] : 0.f;
+  __syncthreads();
   if (delta >= ix.M || a0 >= ix.M - delta) return;
   const int64_t a1 = min(a0 + kSeg, ix.M - delta);
-  const int D = ix.D, w = ix.w;
   const float wf = float(w);
-  float qt[DM], ca[DM], cb[DM];
+  const float thr2 = thr * thr * (1.f + 1e-6f);      // a rounding of slack on the square
+  float* cb = s_cb + threadIdx.x;                    // cb[f * kDiagBlock]
+  float qt[DM];
   // direct start: centred dot products of windows a0 and a0 + delta
 #pragma unroll
   for (int f = 0; f < DM; ++f) {
-    qt[f] = 0.f; ca[f] = 0.f; cb[f] = 0.f;
+    qt[f] = 0.f;
     if (f < D) {
       const float* xh = ix.xs_hi + int64_t(f) * ix.n;
       const float* xl = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n : nullptr;
-      ca[f] = ix.mu_hi[int64_t(f) * ix.M + a0];
-      cb[f] = ix.mu_hi[int64_t(f) * ix.M + a0 + delta];
-      float s = 0.f;
+      const float ca = s_ca[f], cbf = ix.mu_hi[int64_t(f) * ix.M + a0 + delta];
+      cb[f * kDiagBlock] = cbf;
+      float acc = 0.f;
       for (int t = 0; t < w; ++t)
-        s = fmaf(xv(xh, xl, a0 + t) - ca[f], xv(xh, xl, a0 + delta + t) - cb[f], s);
-      qt[f] = s;
+        acc = fmaf(xv(xh, xl, a0 + t) - ca, xv(xh, xl, a0 + delta + t) - cbf, acc);
+      qt[f] = acc;
     }
   }
+  // squared z-normalised distance of dim f for the current (a, b)
+  auto sq_of = [&](int f, int64_t a, int64_t b) {
+    const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
+    const float isa = ix.inv_sig[oa], isb = ix.inv_sig[ob];
+    const float da = ix.mu_hi[oa] - s_ca[f], db = ix.mu_hi[ob] - cb[f * kDiagBlock];
+    const float cov = qt[f] / wf - da * db;
+    const float na = isa > 0.f ? wf : 0.f, nb = isb > 0.f ? wf : 0.f;
+    return fmaxf(na + nb - 2.f * wf * cov * isa * isb, 0.f);
+  };
   for (int64_t a = a0; a < a1; ++a) {
     const int64_t b = a + delta;
     if (a > a0) {
@@ -911,35 +934,28 @@ k_allpairs_wide(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
         if (f < D) {
           const float* xh = ix.xs_hi + int64_t(f) * ix.n;
           const float* xl = ix.has_lo ? ix.xs_lo + int64_t(f) * ix.n : nullptr;
-          float out_a = xv(xh, xl, a - 1) - ca[f], out_b = xv(xh, xl, b - 1) - cb[f];
-          float in_a = xv(xh, xl, a + w - 1) - ca[f], in_b = xv(xh, xl, b + w - 1) - cb[f];
+          const float ca = s_ca[f], cbf = cb[f * kDiagBlock];
+          const float out_a = xv(xh, xl, a - 1) - ca, out_b = xv(xh, xl, b - 1) - cbf;
+          const float in_a = xv(xh, xl, a + w - 1) - ca, in_b = xv(xh, xl, b + w - 1) - cbf;
           qt[f] = fmaf(in_a, in_b, fmaf(-out_a, out_b, qt[f]));
         }
       }
     }
-    float dist[DM];
     int near = 0;
 #pragma unroll
-    for (int f = 0; f < DM; ++f) {
-      dist[f] = INFINITY;
-      if (f < D) {
-        const int64_t oa = int64_t(f) * ix.M + a, ob = int64_t(f) * ix.M + b;
-        const float isa = ix.inv_sig[oa], isb = ix.inv_sig[ob];
-        const float da = ix.mu_hi[oa] - ca[f], db = ix.mu_hi[ob] - cb[f];
-        const float cov = qt[f] / wf - da * db;
-        const float na = isa > 0.f ? wf : 0.f, nb = isb > 0.f ? wf : 0.f;
-        const float sq = na + nb - 2.f * wf * cov * isa * isb;
-        dist[f] = sqrtf(fmaxf(sq, 0.f));
-        near += dist[f] <= thr;
+    for (int f = 0; f < DM; ++f)
+      if (f < D) near += sq_of(f, a, b) <= thr2;
+    if (ROWMIN || near >= d) {
+      float dist[DM];
+#pragma unroll
+      for (int f = 0; f < DM; ++f) dist[f] = f < D ? sqrtf(sq_of(f, a, b)) : INFINITY;
+      const float sm = sum_d_smallest<DM>(dist, D, d);
+      if (ROWMIN) {
+        atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+        atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+      } else if (sm <= thr && sm > rc.lo) {
+        record_pair(rc, a, b, sm);
       }
-    }
-    if (ROWMIN) {
-      float s = sum_d_smallest<DM>(dist, D, d);
-      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(s));
-      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(s));
-    } else if (near >= d) {
-      float s = sum_d_smallest<DM>(dist, D, d);
-      if (s <= thr && s > rc.lo) record_pair(rc, a, b, s);
     }
   }
 }
@@ -987,10 +1003,17 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
   }
   else if (ix.D <= 16)
     MOMENTI_LAUNCH("allpairs", s, k_allpairs<16, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
-  else if (ix.D <= 32)
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
-  else
-    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, 0, s>>>(ix, d, thr, rc, rowmin, y0));
+  else if (ix.D <= 32) {
+    const size_t smem = size_t(32) * (kDiagBlock + 1) * sizeof(float);
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_wide<32, ROWMIN>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<32, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
+  } else {
+    const size_t smem = size_t(64) * (kDiagBlock + 1) * sizeof(float);
+    cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_wide<64, ROWMIN>), smem);
+    if (e != cudaSuccess) return e;
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_wide<64, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, rowmin, y0));
+  }
   }
   return cudaGetLastError();
 }

@@ -7,6 +7,7 @@ Definition (top-k multidimensional motifs, Section 3.1) as
 [dist_d, a, b, dims, dist_max], and the oracle's wall time.
 
 Usage: python tests/golden/make_golden.py plain_small plain_fp32 batch_small guarantee
+       python tests/golden/make_golden.py precision_form large_form   (n = 2e5 prefixes)
 
 batch_small is the batching form at reduced lengths (6 series, n
 log-uniform in [1500, 5000]); its file holds one record per series.
@@ -83,11 +84,37 @@ def make_guarantee():
     print(path, f"{dt:.1f}s")
 
 
+# the larger forms at a length the oracle finishes in minutes (the same
+# generator, its motifs planted inside that length), through the oracle's C
+# pair enumeration (exact_topk_diag); first thresholds as above
+PREFIX = {"precision_form": (200_000, 16.0), "large_form": (200_000, 40.0)}
+
+
+def make_prefix(name: str, seed: int = 0):
+    n, tau0 = PREFIX[name]
+    wl = getattr(synth, name)(seed, n=n)
+    t0 = time.time()
+    res = O.exact_topk_diag(wl.series, wl.w, wl.d, wl.k, tau0=tau0)
+    dt = time.time() - t0
+    rec = {
+        "workload": name, "seed": seed, "D": wl.D, "n": wl.n, "w": wl.w, "d": wl.d, "k": wl.k,
+        "planted": [[a, b, list(dims)] for a, b, dims in wl.planted],
+        "motifs": [[m[0], m[1], m[2], list(m[3]), m[4]] for m in res],
+        "oracle": "exact_topk_diag", "oracle_seconds": dt, "host_threads": os.cpu_count(),
+    }
+    path = os.path.join(OUT, f"exact_{name}_n{n}_seed{seed}.json")
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(path, f"{dt:.1f}s")
+
+
 if __name__ == "__main__":
     for nm in sys.argv[1:] or ["plain_small"]:
         if nm == "batch_small":
             make_batch_small()
         elif nm == "guarantee":
             make_guarantee()
+        elif nm in PREFIX:
+            make_prefix(nm)
         else:
             make(nm)

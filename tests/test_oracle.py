@@ -531,3 +531,68 @@ def test_tensored_search_stops_on_its_bound_or_is_exact():
             p = O.collision_probability(res["motifs"][-1][4], r) ** wl.d
             assert res["fail_bound"] == O.tensoring_failure_bound(p, i, j, 8, 225) <= 0.2
     assert stopped >= 2
+
+
+# ------------------------- the oracle's C pair enumeration (exact_pairs.c)
+
+def _same_topk(got, ref, rel=1e-9):
+    assert [(g[1], g[2], tuple(g[3])) for g in got] == [(r[1], r[2], tuple(r[3])) for r in ref]
+    for g, r in zip(got, ref):
+        assert g[0] == pytest.approx(r[0], rel=rel, abs=1e-9)
+        assert g[4] == pytest.approx(r[4], rel=rel, abs=1e-9)
+
+
+@pytest.mark.parametrize("seed,n,D,w,d,k", [(0, 300, 3, 20, 2, 3), (1, 700, 2, 33, 1, 2),
+                                           (2, 1500, 4, 50, 2, 3), (11, 900, 12, 40, 4, 2),
+                                           (13, 500, 40, 24, 10, 2), (14, 400, 5, 30, 5, 3)])
+def test_diagonal_enumeration_matches_the_matrix_form(seed, n, D, w, d, k):
+    # exact_topk forms every dot product with a matrix product; the C code
+    # slides them along diagonals: the same top-k (pairs, dims, distances)
+    wl = synth.tiny(seed, n=n, D=D, w=w, d=d, k=k, n_motifs=1)
+    _same_topk(O.exact_topk_diag(wl.series, w, d, k), O.exact_topk(wl.series, w, d, k))
+
+
+def test_diagonal_enumeration_matches_the_definitions_on_tiny_series():
+    for seed in (3, 4):
+        wl = synth.tiny(seed, n=90, D=3, w=12, d=2, k=2, n_motifs=1)
+        _same_topk(O.exact_topk_diag(wl.series, wl.w, 2, 2), O.naive_topk(wl.series, wl.w, 2, 2))
+
+
+def test_diagonal_recurrence_over_long_diagonals():
+    # n - w >> 1024: the slid dot products are recomputed every 1024 steps
+    # and must still agree with the direct ones (float64)
+    wl = synth.tiny(15, n=6000, D=2, w=16, d=1, k=3, n_motifs=1)
+    wl.series[:, :] += 1e3          # a large level stresses the Pearson form's cancellation
+    _same_topk(O.exact_topk_diag(wl.series, wl.w, 1, 3), O.exact_topk(wl.series, wl.w, 1, 3),
+               rel=1e-7)
+
+
+def test_pairs_below_is_every_pair_below_the_threshold():
+    wl = synth.tiny(5, n=120, D=3, w=10, d=2, k=1, n_motifs=0)
+    tau = 5.0
+    got = O.pairs_below(wl.series, wl.w, 2, tau)
+    ref = []
+    M, eps = wl.n - wl.w + 1, O.exclusion_zone(wl.w)
+    for a in range(M):
+        for b in range(a + eps + 1, M):
+            dd, dims, mx = O.select_d(O.per_dim_distances(wl.series, wl.w, a, b), 2)
+            if dd <= tau:
+                ref.append((a, b, dd, O.dims_mask(dims), mx))
+    assert len(got) == len(ref) > 10
+    ref.sort(key=lambda x: (x[2], x[0], x[1]))
+    for g, r in zip(got, ref):
+        assert (int(g["a"]), int(g["b"]), int(g["dims"])) == (r[0], r[1], r[3])
+        assert g["dist_d"] == pytest.approx(r[2], rel=1e-9)
+        assert g["dist_max"] == pytest.approx(r[4], rel=1e-9)
+
+
+def test_diagonal_enumeration_of_flat_windows():
+    # flat windows z-normalise to zero: distance 0 between two of them,
+    # sqrt(w) to any other (reading 2), as in znorm_windows
+    rng = np.random.default_rng(3)
+    T = np.cumsum(rng.standard_normal((2, 400)), axis=1)
+    T[0, 50:120] = 7.0
+    T[0, 250:330] = -2.0
+    got = O.exact_topk_diag(T, 20, 1, 3)
+    _same_topk(got, O.exact_topk(T, 20, 1, 3))
+    assert got[0][0] == 0.0
