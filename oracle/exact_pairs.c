@@ -60,29 +60,42 @@ int64_t oracle_pairs_below(const double* T, int D, int64_t n, int w, int d, int6
                            double tau, double flat_rel, oracle_pair* out, int64_t cap) {
   const int64_t M = n - w + 1;
   if (M < 1 || D < 1 || D > 64 || d < 1 || d > D) return 0;
-  double* mu = malloc(sizeof(double) * (size_t)(D * M));
-  double* sg = malloc(sizeof(double) * (size_t)(D * M));
-  unsigned char* flat = malloc((size_t)(D * M));
-  /* each dimension less its overall mean: z-normalised windows do not
-     change, and the raw dot products of the Pearson form lose less to
-     cancellation */
+  /* per dimension: the series less its overall mean (a shift: z-normalised
+     windows do not change, and the raw dot products of the Pearson form
+     lose less to cancellation), then every window's mean and population
+     sigma by two passes; stored point-major ([t][f], [a][f]) so that the
+     D values of a step are contiguous */
   double* X = malloc(sizeof(double) * (size_t)(D * n));
-  if (!mu || !sg || !flat || !X) {
-    free(mu); free(sg); free(flat); free(X);
+  double* mu = malloc(sizeof(double) * (size_t)(D * M));
+  double* wmu = malloc(sizeof(double) * (size_t)(D * M));
+  double* isw = malloc(sizeof(double) * (size_t)(D * M));      /* 1 / (w sigma), 0 if flat */
+  unsigned char* flat = malloc((size_t)(D * M));
+  double* xf = malloc(sizeof(double) * (size_t)n);
+  double* mf = malloc(sizeof(double) * (size_t)M);
+  double* sf = malloc(sizeof(double) * (size_t)M);
+  if (!X || !mu || !wmu || !isw || !flat || !xf || !mf || !sf) {
+    free(X); free(mu); free(wmu); free(isw); free(flat); free(xf); free(mf); free(sf);
     return -1;
   }
   for (int f = 0; f < D; ++f) {
     double s = 0.0;
     for (int64_t t = 0; t < n; ++t) s += T[(int64_t)f * n + t];
     const double c = s / (double)n;
-    for (int64_t t = 0; t < n; ++t) X[(int64_t)f * n + t] = T[(int64_t)f * n + t] - c;
-    window_stats(X + (int64_t)f * n, M, w, mu + (int64_t)f * M, sg + (int64_t)f * M);
-    /* flat relative to the window's own level (before the shift) */
-    for (int64_t a = 0; a < M; ++a)
-      flat[(int64_t)f * M + a] = sg[(int64_t)f * M + a] <= flat_rel * (1.0 + fabs(mu[(int64_t)f * M + a] + c));
+    for (int64_t t = 0; t < n; ++t) xf[t] = T[(int64_t)f * n + t] - c;
+    window_stats(xf, M, w, mf, sf);
+    for (int64_t t = 0; t < n; ++t) X[t * D + f] = xf[t];
+    for (int64_t q = 0; q < M; ++q) {
+      const int64_t o = q * D + f;
+      /* flat relative to the window's own level (before the shift) */
+      flat[o] = sf[q] <= flat_rel * (1.0 + fabs(mf[q] + c));
+      mu[o] = mf[q];
+      wmu[o] = w * mf[q];
+      isw[o] = flat[o] ? 0.0 : 1.0 / (w * sf[q]);
+    }
   }
-  T = X;
+  free(xf); free(mf); free(sf);
   int64_t found = 0;
+  const double tau2 = tau * tau;
 #pragma omp parallel
   {
     double qt[64], dist[64];
@@ -91,23 +104,36 @@ int64_t oracle_pairs_below(const double* T, int D, int64_t n, int w, int d, int6
     for (int64_t delta = excl + 1; delta < M; ++delta) {
       for (int64_t a = 0; a + delta < M; ++a) {
         const int64_t b = a + delta;
+        const double* xa0 = X + (a - 1) * D;        /* point a - 1 (not read at a = 0) */
+        const double* xb0 = X + (b - 1) * D;
+        const double* xa1 = X + (a + w - 1) * D;    /* point a + w - 1 */
+        const double* xb1 = X + (b + w - 1) * D;
+        const int64_t oa = a * D, ob = b * D;
+        int near = 0;
         for (int f = 0; f < D; ++f) {
-          const double* x = T + (int64_t)f * n;
-          if (a % 1024 == 0)
-            qt[f] = dot(x, a, b, w);
-          else
-            qt[f] = qt[f] - x[a - 1] * x[b - 1] + x[a + w - 1] * x[b + w - 1];
-          const int64_t ia = (int64_t)f * M + a, ib = (int64_t)f * M + b;
-          double df;
-          if (flat[ia] || flat[ib]) {
-            df = (flat[ia] && flat[ib]) ? 0.0 : sqrt((double)w);
+          if (a % 1024 == 0) {
+            double s = 0.0;
+            for (int t = 0; t < w; ++t) s += X[(a + t) * D + f] * X[(b + t) * D + f];
+            qt[f] = s;
           } else {
-            const double corr = (qt[f] - w * mu[ia] * mu[ib]) / (w * sg[ia] * sg[ib]);
-            const double sq = 2.0 * w * (1.0 - corr);
-            df = sqrt(sq > 0.0 ? sq : 0.0);
+            qt[f] = qt[f] - xa0[f] * xb0[f] + xa1[f] * xb1[f];
           }
-          dist[f] = df;
+          double sq;
+          if (flat[oa + f] || flat[ob + f]) {
+            sq = (flat[oa + f] && flat[ob + f]) ? 0.0 : (double)w;
+          } else {
+            /* corr = (QT - w mu_a mu_b) / (w sigma_a sigma_b) */
+            const double corr = (qt[f] - wmu[oa + f] * mu[ob + f]) * isw[oa + f] * isw[ob + f] * w;
+            sq = 2.0 * w * (1.0 - corr);
+            if (sq < 0.0) sq = 0.0;
+          }
+          dist[f] = sq;                        /* squared for now */
+          near += sq <= tau2;
         }
+        /* fewer than d dims within tau: one of the d smallest exceeds tau,
+           so dist_d > tau (distances are >= 0) */
+        if (near < d) continue;
+        for (int f = 0; f < D; ++f) dist[f] = sqrt(dist[f]);
         /* the d smallest, ties to the lower dimension: insertion into an
            ordered list of dimension indices */
         int m = 0;
@@ -142,9 +168,10 @@ int64_t oracle_pairs_below(const double* T, int D, int64_t n, int w, int d, int6
       }
     }
   }
-  free(mu);
-  free(sg);
-  free(flat);
   free(X);
+  free(mu);
+  free(wmu);
+  free(isw);
+  free(flat);
   return found;
 }

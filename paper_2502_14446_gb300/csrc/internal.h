@@ -27,7 +27,9 @@ struct Index {
   float* xs_lo = nullptr;     // [D][n]  float64 input only: x - double(hi), as float
   float* xT = nullptr;        // [n][Dp] point-major copy of xs_hi (D <= 8), dims padded with 0
   float* xlT = nullptr;       // [n][Dp] point-major copy of xs_lo
-  int Dp = 0;                 // 4 or 8 when xT is present
+  int Dp = 0;                 // 4, 8 or 16 when xT is present
+  float* xW = nullptr;        // [n][DW] point-major copy of xs_hi for 16 < D <= 64, float32 input
+  int DW = 0;                 // 32 or 64 when xW is present
   float* smT = nullptr;       // [n-15][Dp] means of 16 consecutive points (D <= 8, w >= 32)
   float* stT = nullptr;       // [M][3][Dp] point-major mu_hi, mu_lo, inv_sig (D <= 8)
   double* mu = nullptr;       // [D][M]
@@ -282,6 +284,9 @@ struct ApRec {
   float hscale = 0.f;          // kApBins / (thr - lo)
 };
 cudaError_t launch_allpairs(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s);
+// Whether the row-staged sweep of wide series (16 < D <= 64) takes this index
+// (a point-major copy, and its staged rows fit a CTA's shared memory).
+bool rows2_usable(const Index& ix);
 // Recorded pairs whose approximate distance lies in (lo, hi], compacted.
 cudaError_t launch_select_pairs(const uint64_t* pairs, const float* dd, uint64_t m, float lo,
                                 float hi, uint64_t* out, unsigned long long* count, cudaStream_t s);

@@ -349,7 +349,9 @@ cudaError_t launch_window_stats(const Index& ix, cudaStream_t s) {
 }
 
 cudaError_t launch_point_major(const Index& ix, cudaStream_t s) {
-  if (!ix.xT) return cudaSuccess;
+  if (ix.xW)
+    MOMENTI_LAUNCH("point_major", s, k_point_major<<<grid_for(ix.n * ix.DW, 256), 256, 0, s>>>(ix.xs_hi, nullptr, ix.n, ix.D, ix.DW, ix.xW, nullptr));
+  if (!ix.xT) return cudaGetLastError();
   MOMENTI_LAUNCH("point_major", s, k_point_major<<<grid_for(ix.n * ix.Dp, 256), 256, 0, s>>>(ix.xs_hi, ix.has_lo ? ix.xs_lo : nullptr, ix.n, ix.D, ix.Dp, ix.xT, ix.xlT));
   if (ix.smT) {
     const int64_t chunks = (ix.n - 15 + 255) / 256;

@@ -877,6 +877,285 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   }
 }
 
+// Row-staged sweep for 16 < D <= DW (point-major copy X [n][DW], float32
+// input): the rows kernel above with the dims of each diagonal split over
+// G = DW / 16 adjacent lanes, 16 dims each, so that every lane keeps the
+// state of the D <= 16 form (cross products, column sums, column centring
+// of its 16 dims).  The lanes of a diagonal add their threshold-test
+// counts with shuffles; a candidate's state goes to a per-warp queue
+// (one entry per diagonal, each lane writing its dims) and its distances
+// are computed by one lane over all dims.  A stage stages only what its
+// rows consume: the outgoing point a - 1 and the incoming point a + w - 1
+// of each row window (2 kRowSub2 points per dim, whatever w is), and
+// takes the row windows' centred sums from the float64 window statistics
+// (sum w (mu - c), w^2 var w^2 sigma^2); the first row window's points,
+// needed once per block for the direct start, are read from global memory.
+constexpr int kRowSub2 = 96;
+
+template <int DW, bool ROWMIN>
+__global__ void __launch_bounds__(kDiagBlock, DW <= 32 ? 2 : 1)
+k_allpairs_rows2(Index ix, const float* __restrict__ X, int d, float thr, ApRec rc,
+                 float* __restrict__ rowmin, int64_t ybase) {
+  constexpr int G = DW / 16;                 // lanes per diagonal
+  constexpr int NDG = kDiagBlock / G;        // diagonals per block
+  constexpr int DH = 8;                      // float2 pairs of dims per lane
+  constexpr int DW2 = DW / 2;
+  constexpr int RS = kRowSub2;
+  constexpr int QS = 3 * DW + 2;             // queued state: qt, s1b, s2b per dim
+  constexpr int QN = 32 / G;                 // queue entries per warp
+  extern __shared__ float ap_smem[];
+  const int w = ix.w, D = ix.D;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = threadIdx.x % G;
+  const int f0 = 16 * g;                     // this lane's first dim
+  const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  const int64_t dlo = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * NDG;
+  if (dlo >= ix.M || a0 >= ix.M - dlo) return;                  // block-uniform
+  const int64_t delta = dlo + threadIdx.x / G;
+  const bool live = delta < ix.M && a0 < ix.M - delta;
+  const int64_t a1 = live ? min(a0 + kSeg, ix.M - delta) : a0;
+  const int64_t nrow = min(int64_t(kSeg), ix.M - dlo - a0);
+  float* outx = ap_smem;                                        // [RS][DW] point a - 1, centred
+  float* inx = outx + RS * DW;                                  // [RS][DW] point a + w - 1, centred
+  float* sa1 = inx + RS * DW;                                   // [RS][DW] centred row sums
+  float* sa2 = sa1 + RS * DW;                                   // [RS][DW] w^2 var (-1: unreliable)
+  float* cav = sa2 + RS * DW;                                   // [2][DW]
+  float* sprev = cav + 2 * DW;                                  // [DW]
+  float* qall = sprev + DW;                                     // [warps][QN][QS]
+  uint32_t* qmeta = reinterpret_cast<uint32_t*>(qall + (kDiagBlock / 32) * QN * QS);
+  uint32_t* qcol = qmeta + (kDiagBlock / 32) * QN;
+  __shared__ int rflag[RS];
+  const float wf = float(w);
+  const double wd = double(w);
+  const float2 wf2 = make_float2(wf, wf);
+  const float2* out2 = reinterpret_cast<const float2*>(outx);
+  const float2* in2 = reinterpret_cast<const float2*>(inx);
+  const float2* sa1_2 = reinterpret_cast<const float2*>(sa1);
+  const float2* sa2_2 = reinterpret_cast<const float2*>(sa2);
+  float2 qt[DH], s1b[DH], s2b[DH], ncb[DH];
+#pragma unroll
+  for (int p = 0; p < DH; ++p) {
+    qt[p] = s1b[p] = s2b[p] = make_float2(0.f, 0.f);
+    const int fa = f0 + 2 * p, fb = fa + 1;
+    ncb[p] = make_float2(live && fa < D ? -ix.mu_hi[int64_t(fa) * ix.M + a0 + delta] : 0.f,
+                         live && fb < D ? -ix.mu_hi[int64_t(fb) * ix.M + a0 + delta] : 0.f);
+  }
+  // the necessary conditions of the rows kernel (x(1) <= thr/d, x(2) <=
+  // thr/(d-1), x(d) <= thr on the sorted per-dim distances)
+  const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
+  const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
+  const float cd = 1.f - thr * thr / (2.f * wf);
+  const float2 k1 = make_float2(c1 * fabsf(c1), c1 * fabsf(c1));
+  const float2 k2 = make_float2(c2 * fabsf(c2), c2 * fabsf(c2));
+  const float2 kd = make_float2(cd * fabsf(cd), cd * fabsf(cd));
+  const uint32_t need2 = d >= 2 ? 2u : 1u;
+  const float2 flat = make_float2(1e-4f * wf, 1e-4f * wf);
+  float* qst = qall + warp * QN * QS;
+  uint32_t* qm = qmeta + warp * QN;
+  uint32_t* qc = qcol + warp * QN;
+  int64_t aS = a0;
+  // distances of queued diagonals, one per lane (lanes below count)
+  auto drain = [&](int count) {
+    __syncwarp();
+    if (lane < count) {
+      const float* st = qst + lane * QS;
+      const int r = int(qm[lane] >> 1);
+      const bool uns = (qm[lane] & 1u) != 0;
+      float dist[DW];
+#pragma unroll
+      for (int f = 0; f < DW; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float qf = st[f], s1 = st[DW + f], s2 = st[2 * DW + f];
+          const float s1a = sa1[r * DW + f], VA = sa2[r * DW + f];
+          const float VB = fmaf(wf, s2, -s1 * s1);
+          const float Cv = fmaf(wf, qf, -s1a * s1);
+          const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+          dist[f] = sqrtf(fmaxf(sq, 0.f));
+        }
+      }
+      const float sm = uns ? 0.f : sum_d_smallest<DW>(dist, D, d);
+      if (sm <= thr && sm > rc.lo) record_pair(rc, aS + r, int64_t(qc[lane]), sm);
+    }
+    __syncwarp();
+  };
+  int qn = 0;                       // queued diagonals of this warp (warp-uniform)
+  for (int stage = 0; aS < a0 + nrow; ++stage, aS += RS) {
+    const int nsub = int(min(int64_t(RS), a0 + nrow - aS));
+    float* cnew = cav + (stage & 1) * DW;
+    const float* cold = cav + ((stage & 1) ^ 1) * DW;
+    __syncthreads();                // the previous stage is fully consumed
+    if (threadIdx.x < DW) {
+      const int f = threadIdx.x;
+      const float c = f < D ? ix.mu_hi[int64_t(f) * ix.M + aS] : 0.f;
+      cnew[f] = c;
+      // centred sum of row window aS - 1 (re-centring of the carried state)
+      sprev[f] = (f < D && aS >= 1) ? float(wd * (ix.mu[int64_t(f) * ix.M + aS - 1] - double(c))) : 0.f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nsub * DW; q += blockDim.x) {
+      const int r = q / DW, f = q - r * DW;
+      const int64_t a = aS + r;
+      if (f < D) {
+        const float c = cnew[f];
+        outx[q] = a >= 1 ? X[(a - 1) * DW + f] - c : 0.f;
+        inx[q] = X[(a + w - 1) * DW + f] - c;
+        // row window a centred on c: sum w (mu - c), w^2 var = w^2 sigma^2;
+        // unreliable (near-flat) when sigma^2 <= 1e-4 (sigma^2 + (mu - c)^2)
+        const double m = ix.mu[int64_t(f) * ix.M + a], sg = ix.sig[int64_t(f) * ix.M + a];
+        const double dm = m - double(c), v = sg * sg;
+        sa1[q] = float(wd * dm);
+        sa2[q] = v > 1e-4 * (v + dm * dm) ? float(wd * wd * v) : -1.f;
+      } else {
+        outx[q] = inx[q] = sa1[q] = 0.f;
+        sa2[q] = __int_as_float(0x7fc00000);      // padding dims: no test passes
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nsub; r += blockDim.x) {
+      int u = 0;
+      for (int f = 0; f < D; ++f) u |= sa2[r * DW + f] < 0.f;
+      rflag[r] = u;
+    }
+    __syncthreads();
+    if (stage == 0) {
+      // direct start: row window a0 against column window a0 + delta
+      for (int t = 0; t < (live ? w : 0); ++t) {
+        float xa[16], xb[16];
+        load_row<16>(X + f0, (a0 + t) * G, xa);                 // same address over the block
+        load_row<16>(X + f0, (a0 + delta + t) * G, xb);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          const float2 u = make_float2(xa[2 * p] - cnew[f0 + 2 * p], xa[2 * p + 1] - cnew[f0 + 2 * p + 1]);
+          const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(u, v, qt[p]);
+          s1b[p] = __fadd2_rn(s1b[p], v);
+          s2b[p] = __ffma2_rn(v, v, s2b[p]);
+        }
+      }
+    } else if (aS - 1 < a1) {
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const int fa = f0 + 2 * p, fb = fa + 1;
+        const float2 dr = make_float2(cold[fa] - cnew[fa], cold[fb] - cnew[fb]);
+        qt[p] = __ffma2_rn(dr, s1b[p], qt[p]);
+        const float2 cbn = make_float2(fa < D ? ix.mu_hi[int64_t(fa) * ix.M + aS - 1 + delta] : 0.f,
+                                       fb < D ? ix.mu_hi[int64_t(fb) * ix.M + aS - 1 + delta] : 0.f);
+        const float2 dc = make_float2(cbn.x + ncb[p].x, cbn.y + ncb[p].y);
+        const float2 sp = make_float2(sprev[fa], sprev[fb]);
+        qt[p] = __ffma2_rn(make_float2(-dc.x, -dc.y), sp, qt[p]);
+        s2b[p] = __ffma2_rn(make_float2(wf * dc.x, wf * dc.y), dc,
+                            __ffma2_rn(make_float2(-2.f * dc.x, -2.f * dc.y), s1b[p], s2b[p]));
+        s1b[p] = __ffma2_rn(make_float2(-wf, -wf), dc, s1b[p]);
+        ncb[p] = make_float2(-cbn.x, -cbn.y);
+      }
+    }
+    for (int r = 0; r < nsub; ++r) {
+      const int64_t a = aS + r;
+      const int64_t b = a + delta;
+      const bool act = a < a1;
+      if (act && (r > 0 || stage > 0)) {
+        float ob[16], ib[16];
+        load_row<16>(X + f0, (b - 1) * G, ob);
+        load_row<16>(X + f0, (b + w - 1) * G, ib);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          const float2 uo = out2[r * DW2 + f0 / 2 + p], ui = in2[r * DW2 + f0 / 2 + p];
+          const float2 vo = __fadd2_rn(make_float2(ob[2 * p], ob[2 * p + 1]), ncb[p]);
+          const float2 vi = __fadd2_rn(make_float2(ib[2 * p], ib[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(ui, vi, __ffma2_rn(make_float2(-uo.x, -uo.y), vo, qt[p]));
+          s1b[p] = __fadd2_rn(s1b[p], __fadd2_rn(vi, make_float2(-vo.x, -vo.y)));
+          s2b[p] = __ffma2_rn(vi, vi, __ffma2_rn(make_float2(-vo.x, -vo.y), vo, s2b[p]));
+        }
+      }
+      uint32_t cnt = 0;            // tests passed: byte 0 x(1), byte 1 x(2), high half x(d)
+      int unsure = 0;
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const float2 s1a = sa1_2[r * DW2 + f0 / 2 + p], VA = sa2_2[r * DW2 + f0 / 2 + p];
+        const float2 VB = __ffma2_rn(wf2, s2b[p], __fmul2_rn(make_float2(-s1b[p].x, -s1b[p].y), s1b[p]));
+        const float2 Cv = __ffma2_rn(wf2, qt[p], __fmul2_rn(make_float2(-s1a.x, -s1a.y), s1b[p]));
+        const float2 P = __fmul2_rn(VA, VB);
+        const float2 S = __fmul2_rn(Cv, make_float2(fabsf(Cv.x), fabsf(Cv.y)));
+        const float2 T1 = __fmul2_rn(k1, P), T2 = __fmul2_rn(k2, P), Td = __fmul2_rn(kd, P);
+        const float2 FB = __fmul2_rn(flat, s2b[p]);
+        const int fa = f0 + 2 * p;
+        unsure |= (fa < D && VB.x < FB.x) | (fa + 1 < D && VB.y < FB.y);
+        cnt += (S.x >= T1.x) + (S.y >= T1.y) + ((S.x >= T2.x) + (S.y >= T2.y)) * 256u +
+               ((S.x >= Td.x) + (S.y >= Td.y)) * 65536u;
+      }
+      // the diagonal's totals over its G lanes
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        unsure |= __shfl_xor_sync(0xffffffffu, unsure, o);
+      }
+      unsure |= rflag[r];
+      if (!ROWMIN) {
+        const bool cand = act && (unsure || ((cnt & 255u) >= 1u && ((cnt >> 8) & 255u) >= need2 &&
+                                             (cnt >> 16) >= uint32_t(d)));
+        const unsigned m = __ballot_sync(0xffffffffu, cand);
+        if (!m) continue;
+        const int n = __popc(m) / G;                  // candidate diagonals of this step
+        if (qn + n > QN) {
+          drain(qn);
+          qn = 0;
+        }
+        if (cand) {
+          const int base = lane - g;                  // the diagonal's first lane
+          const int pos = qn + __popc(m & ((1u << base) - 1u)) / G;
+          float* st = qst + pos * QS;
+#pragma unroll
+          for (int p = 0; p < DH; ++p) {
+            st[f0 + 2 * p] = qt[p].x;           st[f0 + 2 * p + 1] = qt[p].y;
+            st[DW + f0 + 2 * p] = s1b[p].x;     st[DW + f0 + 2 * p + 1] = s1b[p].y;
+            st[2 * DW + f0 + 2 * p] = s2b[p].x; st[2 * DW + f0 + 2 * p + 1] = s2b[p].y;
+          }
+          if (g == 0) {
+            qm[pos] = (uint32_t(r) << 1) | (unsure ? 1u : 0u);
+            qc[pos] = uint32_t(b);
+          }
+        }
+        qn += n;
+        if (qn == QN) {
+          drain(QN);
+          qn = 0;
+        }
+        continue;
+      }
+      // row minima: every pair's dist_d from all its dims (gathered on lane g = 0)
+      float mine[16];
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int f = f0 + 2 * p + h;
+          const float qf = h ? qt[p].y : qt[p].x, s1 = h ? s1b[p].y : s1b[p].x, s2 = h ? s2b[p].y : s2b[p].x;
+          const float s1a = sa1[r * DW + f], VA = sa2[r * DW + f];
+          const float VB = fmaf(wf, s2, -s1 * s1);
+          const float Cv = fmaf(wf, qf, -s1a * s1);
+          const float sq = (VA > 0.f && VB > 0.f) ? 2.f * wf * (1.f - Cv * rsqrtf(VA * VB)) : 0.f;
+          mine[2 * p + h] = f < D ? sqrtf(fmaxf(sq, 0.f)) : INFINITY;
+        }
+      }
+      float dist[DW];
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) dist[16 * gg + q] = __shfl_sync(0xffffffffu, mine[q], lane - g + gg);
+      }
+      if (!act || g != 0) continue;
+      const float sm = sum_d_smallest<DW>(dist, D, d);
+      atomicMin(reinterpret_cast<int*>(rowmin + a), __float_as_int(sm));
+      atomicMin(reinterpret_cast<int*>(rowmin + b), __float_as_int(sm));
+    }
+    if (!ROWMIN) {                  // queued diagonals refer to this stage's rows
+      drain(qn);
+      qn = 0;
+    }
+  }
+}
+
 // Wide series (D > 16): per-window means and 1/sigma are read per step;
 // every thread of a block walks the same row windows a (their values are
 // broadcast loads) against its own diagonal.  Only the D centred cross
@@ -969,11 +1248,48 @@ size_t rows_smem(int w, int dp) {
 
 bool rows_fit(int w, int dp) { return rows_smem(w, dp) <= size_t(200) * 1024; }
 
+// the wide row kernel: two staged points and two row sums per row and dim
+// for kRowSub2 rows of DW dims, a queue of 32/G diagonals per warp
+size_t rows2_smem(int w, int dw) {
+  (void)w;                                   // staging does not grow with w
+  const int G = dw / 16, QN = 32 / G;
+  return (size_t(4 * kRowSub2 * dw + 3 * dw) +
+          size_t(kDiagBlock / 32) * QN * (3 * dw + 2) + 2 * size_t(kDiagBlock / 32) * QN) * sizeof(float);
+}
+
+}  // namespace
+
+bool rows2_usable(const Index& ix) {
+  return ix.xW && !ix.has_lo && (ix.DW == 32 || ix.DW == 64) &&
+         rows2_smem(ix.w, ix.DW) <= size_t(220) * 1024;
+}
+
+namespace {
+
+template <int DW, bool ROWMIN>
+cudaError_t rows2_dispatch(const Index& ix, int d, float thr, const ApRec& rc, float* rowmin,
+                           cudaStream_t s) {
+  const int64_t ndiag = ix.M - (ix.excl + 1);
+  constexpr int NDG = kDiagBlock / (DW / 16);
+  const int64_t gy = (ndiag + NDG - 1) / NDG;
+  const size_t smem = rows2_smem(ix.w, DW);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows2<DW, ROWMIN>), smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows2<DW, ROWMIN><<<grid, kDiagBlock, smem, s>>>(ix, ix.xW, d, thr, rc, rowmin, y0));
+  }
+  return cudaGetLastError();
+}
+
 template <bool ROWMIN>
 cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc, float* rowmin,
                               cudaStream_t s) {
   const int64_t ndiag = ix.M - (ix.excl + 1);
   if (ndiag <= 0) return cudaSuccess;
+  if (rows2_usable(ix))
+    return ix.DW == 32 ? rows2_dispatch<32, ROWMIN>(ix, d, thr, rc, rowmin, s)
+                       : rows2_dispatch<64, ROWMIN>(ix, d, thr, rc, rowmin, s);
   const int64_t gy = (ndiag + kDiagBlock - 1) / kDiagBlock;
   for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
   dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};

@@ -390,6 +390,7 @@ double predict_exact_ms(const Index& ix, int passes) {
   if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 5.0;
   else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 11.0;
   else if (ix.xT && !ix.has_lo && ix.Dp == 16) ps_pair = 40.0;
+  else if (ix.xW && rows2_usable(ix)) ps_pair = 1.6 * double(ix.DW);
   else if (ix.D <= 32) ps_pair = 8.0 * double(ix.D);
   else ps_pair = 31.0 * double(ix.D);
   const double pairs = 0.5 * double(ix.M) * double(ix.M);
@@ -508,11 +509,22 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
                double* max_err) {
   Index& ix = h->ix;
   const int k = h->p.k;
+  // First threshold.  TOP's k-th (tau0) when it is informative; a TOP that
+  // holds only background pairs (its k-th above a quarter of the largest
+  // possible dist_d, 2 d sqrt(w)) would let most pairs through the sweep's
+  // filters, so then, and on large series instead of a row-minima sweep
+  // (which evaluates every pair in full), the slices start at 5% of the
+  // largest dist_d and double.  Any start gives the same exact result.
+  const double dmax_all = 2.0 * double(d) * std::sqrt(double(ix.w));
+  const double tau_low = 0.05 * dmax_all;
   double tau = tau0;
+  if (tau > 0.25 * dmax_all) tau = std::min(tau, tau_low);
+  if (!(tau > 0) && double(ix.M) * double(ix.M) * double(ix.D) > 4e11) tau = tau_low;
   if (!(tau > 0)) {
     float* rowmin = nullptr;
     CK(pool_malloc(&rowmin, ix.M * 4, h->stream));
     CK(cudaMemsetAsync(rowmin, 0x7f, ix.M * 4, h->stream));
+    const auto tr0 = std::chrono::steady_clock::now();
     CK(launch_allpairs_rowmin(ix, d, rowmin, h->stream));
     std::vector<float> rm(ix.M);
     CK(cudaMemcpyAsync(rm.data(), rowmin, ix.M * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -539,9 +551,14 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
       return MOMENTI_OK;
     }
     tau = std::max(val * 1.2, 1e-3);
+    if (const char* t1 = std::getenv("MOMENTI_TRACE"); t1 && t1[0] == '1')
+      std::fprintf(stderr, "momenti trace: exact row minima ms=%.1f\n",
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tr0).count());
   }
   if (const char* t0 = std::getenv("MOMENTI_TRACE"); t0 && t0[0] == '1')
-    std::fprintf(stderr, "momenti trace: exact tau=%.5g (%s)\n", tau, tau0 > 0 ? "from TOP" : "from row minima");
+    std::fprintf(stderr, "momenti trace: exact tau=%.5g (%s)\n", tau,
+                 tau == tau0 ? "from TOP" : (tau == tau_low ? "low start" : "from row minima"));
+  const auto te0 = std::chrono::steady_clock::now();
   // Pairs are taken in slices of their approximate dist_d (float32 Pearson
   // form, within 1% + 0.01 of the exact value): each all-pairs sweep records
   // the pairs with approximate distance in (lo, hi] and a histogram of them;
@@ -630,14 +647,16 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
     ar.hist = dhist;
     ar.lo = lo;
     ar.hscale = float(kApBins) / (hi - lo);
+    const auto tp0 = std::chrono::steady_clock::now();
     CK(launch_allpairs(ix, d, hi, ar, h->stream));
     unsigned long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(hist.data(), dhist, kApBins * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (trace)
-      std::fprintf(stderr, "momenti trace: exact pass=%d lo=%.5g hi=%.5g pairs=%llu cap=%llu held=%zu\n",
-                   pass, double(lo), double(hi), cnt, (unsigned long long)cap, got.size());
+      std::fprintf(stderr, "momenti trace: exact pass=%d lo=%.5g hi=%.5g pairs=%llu cap=%llu held=%zu ms=%.1f\n",
+                   pass, double(lo), double(hi), cnt, (unsigned long long)cap, got.size(),
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count());
     const double width = double(hi - lo) / kApBins;
     if (cnt > cap) {
       // lower the upper edge to the largest bin edge whose pairs fit; grow
@@ -690,6 +709,9 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
   }
   cudaFreeAsync(dcnt, h->stream);
   cudaFreeAsync(dhist, h->stream);
+  if (trace)
+    std::fprintf(stderr, "momenti trace: exact done ms=%.1f\n",
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - te0).count());
   if (rc == MOMENTI_ERR_OVERFLOW) return fail(h, rc, "exact path: threshold search did not converge");
   return rc;
 }
@@ -802,6 +824,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                            + uint64_t(D) * n * elem                          // transient staging
                            + uint64_t(D) * M * (8 + 8 + 4 + 4 + 4)           // stats
                            + (D <= 16 ? uint64_t(16) * (3 * n + 3 * M) * 4 : 0)  // point-major copies
+                           + (D > 16 ? uint64_t(64) * n * 4 : 0)             // point-major wide copy
                            + (D <= 16 && p.d >= 2 ? job_cap_for(M, D) * sizeof(BucketJob) : 0)
                            + (uint64_t(64) << 20);                           // small scratch
     const uint64_t per_rep = uint64_t(M) * D * (8 + 4 + 1)                   // keys, order, lcp
@@ -866,6 +889,10 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     const int N = (tens ? 2 * isqrt(L) : L) * kRepStride;
     CK(dalloc(h, &ix.xs_hi, size_t(D) * n));
     if (ix.has_lo) CK(dalloc(h, &ix.xs_lo, size_t(D) * n));
+    if (D > 16 && dtype == MOMENTI_F32) {       // the row-staged sweep of wide series
+      ix.DW = D <= 32 ? 32 : 64;
+      CK(dalloc(h, &ix.xW, size_t(ix.DW) * n));
+    }
     if (D <= 16) {
       ix.Dp = D <= 4 ? 4 : (D <= 8 ? 8 : 16);
       CK(dalloc(h, &ix.xT, size_t(ix.Dp) * n));
