@@ -83,7 +83,8 @@ def parse():
                     help="plain_fp32: D=8 n=1e5 w=300 (the default line); precision_form: "
                          "D=32 n=1e6 w=500 d=8 (minutes per step)")
     ap.add_argument("--r", type=float, default=0.0, help="quantisation width (0: Section 6.1 heuristic)")
-    ap.add_argument("--no-rsweep", action="store_true", help="skip the fixed-r sweep leg")
+    ap.add_argument("--no-rsweep", action="store_true",
+                    help="skip the parameter legs (r, K, L, delta sweeps, tensoring, scalability)")
     return ap.parse_args()
 
 
@@ -285,7 +286,8 @@ def run_momenti(args):
     # device time of each candidate kernel over one step: the dominant one is
     # timed live in the timed steps; the others' rooflines come from this step
     per_kernel = {}
-    for kname in dict.fromkeys(DOMINANT + SECONDARY):
+    candidates = DOMINANT + SECONDARY if args.kernel == "auto" else SECONDARY + (args.kernel,)
+    for kname in dict.fromkeys(candidates):
         mom.time_kernel(kname)
         _, st_k = step()
         ms, n = mom.kernel_time()
@@ -370,10 +372,12 @@ def run_momenti(args):
                      "value": units_step / (statistics.mean(ts) / 1e3),
                      "t_hash_ms": st32["t_hash_ms"]}
             h32.close()
-        rsweep = tens = None
+        rsweep = tens = sweeps = scal = None
         if wl.name == "plain_fp32" and not args.no_rsweep:
             rsweep = r_sweep_leg(mom, wl, series, stream, flush, prec)
             tens = tensoring_leg(mom, wl, series, stream, flush, prec)
+            sweeps = param_sweep_leg(mom, wl, series, stream, flush, prec)
+            scal = scalability_leg(mom, dev, stream, flush, prec)
         batch = batch_leg(mom, args.batch_series, dev) if args.batch_series > 0 else None
         base = None if args.no_baseline else cpu_baseline(wl)
         # float64 error of each result: the float32 traversal distance
@@ -403,6 +407,8 @@ def run_momenti(args):
             "motifs": [[m["a"], m["b"], round(m["dist_d"], 6), list(m["dims"])] for m in motifs],
             "plain_fp32": plain,
             "r_sweep": rsweep,
+            "param_sweeps": sweeps,
+            "scalability": scal,
             "tensoring": tens,
             "batch_form": batch,
             "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
@@ -459,6 +465,80 @@ def tensoring_leg(mom, wl, series, stream, flush, prec, m=14):
                      "n_verified": st["n_verified"], "r": st["r"]}
     out["same_motifs"] = motifs["plain"] == motifs["tensored"]
     return out
+
+
+def timed_search(mom, params, series, stream, flush, reps=2):
+    """hash_all + topk with ``params`` on a device series: one warm-up, then
+    the mean of ``reps`` steps (L2 flushed before each, CUDA events on the
+    stream); returns (ms, motifs, stats)."""
+    import torch
+    hh = mom.Momenti(params)
+    hh.hash_all(series, stream=stream.cuda_stream)
+    hh.topk()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hh.hash_all(series, stream=stream.cuda_stream)
+        m, st = hh.topk()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    hh.close()
+    return statistics.mean(ts), m, st
+
+
+def param_sweep_leg(mom, wl, series, stream, flush, prec):
+    """The paper's parameter experiments (Section 7: impact of K, L and
+    delta) on this workload, the other parameters at their defaults (K=8,
+    L=200, the r heuristic, cost switch on).  K stops at 8: a composite key
+    holds at most 8 hash values here.  Per setting: time to top-k, the
+    stopping (i, j) or the exact path, distance computations, device memory
+    and whether the motifs equal the stored exact top-k."""
+    gold = None
+    path = os.path.join(ROOT, "tests", "golden", "exact_plain_fp32_seed0.json")
+    if wl.n == 100_000 and wl.seed == 0 and os.path.exists(path):
+        gold = [(m[1], m[2]) for m in json.load(open(path))["motifs"]]
+    out = {}
+    for name, values in (("K", (2, 4, 6, 8)), ("L", (10, 50, 100, 200, 400)),
+                         ("delta", (0.05, 0.1, 0.2, 0.4))):
+        rows = []
+        for v in values:
+            p = params_for(mom, wl, prec)
+            setattr(p, name, v)
+            ms, m, st = timed_search(mom, p, series, stream, flush)
+            rows.append({name: v, "time_to_topk_ms": ms, "stop": [st["stop_i"], st["stop_j"]],
+                         "fallback": st["fallback"], "switch_level": st["switch_level"],
+                         "n_verified": st["n_verified"], "device_bytes": st["device_bytes"],
+                         "L_used": st["L"],
+                         "matches_exact": None if gold is None else [(x["a"], x["b"]) for x in m] == gold})
+        out[name] = rows
+    return out
+
+
+def scalability_leg(mom, dev, stream, flush, prec, ns=(10_000, 30_000, 100_000, 300_000, 1_000_000)):
+    """The synthetic scalability workload of Section 7 (synth.scalability:
+    D=5 random walks, one sinusoidal motif of w=300 in 2 dims, d=2, k=1)
+    at growing n: time to top-k, hashing time, how the search ended, and
+    whether the planted pair is the returned motif."""
+    import torch
+    from paper_2502_14446_gb300 import synth
+    rows = []
+    for n in ns:
+        wl = synth.scalability(0, n=n)
+        x = torch.from_numpy(wl.series).to(dev)
+        p = mom.default_params(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, precision=prec)
+        ms, m, st = timed_search(mom, p, x, stream, flush, reps=1)
+        a, b, _ = wl.planted[0]
+        rows.append({"n": n, "time_to_topk_ms": ms, "t_hash_ms": st["t_hash_ms"],
+                     "stop": [st["stop_i"], st["stop_j"]], "fallback": st["fallback"],
+                     "n_verified": st["n_verified"],
+                     "planted_found": bool(m) and (m[0]["a"], m[0]["b"]) == (a, b)})
+        del x
+    return {"workload": "scalability: D=5 random walks, sinusoidal motif w=300 in 2 dims, "
+                        "noise 0.1, d=2, k=1, delta=0.05, float32", "runs": rows}
 
 
 def r_sweep_leg(mom, wl, series, stream, flush, prec, rs=(0.0, 4.0, 8.0, 12.0, 16.0)):
@@ -530,12 +610,13 @@ def batch_leg(mom, count: int, dev, threads: int = 8):
 
 def cpu_baseline(wl, budget_s: float = 20.0):
     """The CPU oracle (Algorithm 1 rendering, float64 numpy) on a bounded
-    prefix of the same workload: n = 2,000 points of the same series, all D
-    dims, w, d, k, delta as the workload, K=8, L=200 hash functions drawn by
-    the same generator."""
+    prefix of the same workload: the first 2,000 points of the series
+    (1,200 for the 32-dimension precision form), all D dims, w, d, k, delta
+    as the workload, K=8, L=200 hash functions drawn by the same
+    generator."""
     from oracle import momenti_oracle as O
     from paper_2502_14446_gb300 import synth
-    n = 2000
+    n = 1200 if wl.D > 16 else 2000
     T = wl.series[:, :n].astype("float64")
     A, U = synth.hash_draws(wl.D, 200, 8, wl.w, 0)
     t0 = time.perf_counter()

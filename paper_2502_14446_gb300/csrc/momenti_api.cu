@@ -831,7 +831,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
                              + uint64_t(D) * kRepStride * Wp * (2 + 4)       // a16, a32
                              + uint64_t(D) * kRepStride * 4                  // boff
                              + uint64_t(D) * K * (w + 1) * 4                 // draws
-                             + uint64_t(D) * M * kRepStride * 8 / 100;       // rehash flags
+                             + uint64_t(D) * M * kRepStride * 8 / 400;       // rehash flags (0.25%)
     const int L_cap = p.L > 0 ? p.L : 4096;
     int L_user = h->user_a.empty() ? L_cap : std::min(L_cap, h->user_L);
     if (tens && !h->user_a.empty()) L_user = std::min(L_cap, (h->user_L / 2) * (h->user_L / 2));
@@ -923,8 +923,10 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     const size_t nu = h->user_a.empty() ? size_t(D) * n_fn * K_fn : h->user_u.size();
     CK(dalloc(h, &h->draw_a, na));
     CK(dalloc(h, &h->draw_u, nu));
-    h->flag_cap = uint32_t(std::min<uint64_t>(uint64_t(1) << 24,
-                                              std::max<uint64_t>(uint64_t(1) << 16, uint64_t(D) * M * N / 100)));
+    // near-boundary values of the tensor-core form (about 0.1% of them; room
+    // for 0.25%, beyond which the projections are redone in float32)
+    h->flag_cap = uint32_t(std::min<uint64_t>(uint64_t(1) << 28,
+                                              std::max<uint64_t>(uint64_t(1) << 16, uint64_t(D) * M * N / 400)));
     CK(dalloc(h, &h->flags, size_t(h->flag_cap)));
     CK(dalloc(h, &h->small, 16));
     // index sort scratch

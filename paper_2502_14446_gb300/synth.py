@@ -210,6 +210,29 @@ def tiny(seed: int, n: int, D: int, w: int, d: int, k: int = 2, n_motifs: int = 
                     planted=planted, seed=seed)
 
 
+def scalability(seed: int = 0, n: int = 100_000, noise: float = 0.1) -> Workload:
+    """The synthetic scalability workload of Section 7: D=5 Gaussian random
+    walks of length n, one sinusoidal motif of length w=300 planted in dims
+    {0, 1} at two offsets 2w or more apart (one period of a sine, written
+    with the host window's level and spread), perturbed by Gaussian noise of
+    ``noise`` times that spread (a low-contrast motif); d=2, k=1,
+    delta=0.05."""
+    rng = _rng(6000 + seed)
+    D, w = 5, 300
+    T = random_walk(rng, D, n)
+    a, b = sorted(_pick_offsets(rng, 2, n, w, 2 * w))
+    shape = np.sin(2 * np.pi * np.arange(w) / w)
+    shape = (shape - shape.mean()) / shape.std()
+    for f in (0, 1):
+        for off in (a, b):
+            host = T[f, off:off + w]
+            lvl, spread = host.mean(), host.std()
+            T[f, off:off + w] = lvl + (spread if spread > 0 else 1.0) * (
+                shape + noise * rng.standard_normal(w))
+    return Workload("scalability", np.ascontiguousarray(T, dtype=np.float32), w, 2, 1, 0.05,
+                    planted=[(a, b, [0, 1])], seed=seed)
+
+
 def with_noise_dims(wl: Workload, extra: int, seed: int = 0) -> Workload:
     """The robustness workload of Section 7 (impact of noise): ``wl`` with
     ``extra`` more dimensions appended, each an independent Gaussian random
