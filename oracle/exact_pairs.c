@@ -23,8 +23,8 @@
  *   - dist_d = the sum of the d smallest per-dimension distances
  *     (Definition distdims), dims_d those d dimensions (ties to the lower
  *     index), dist_d^max the largest of them (Eq. distdmax).
- * Diagonals are shared among threads (OpenMP); the output order is not
- * specified (the caller sorts).
+ * Blocks of 32 diagonals are shared among threads (OpenMP) and advance row
+ * by row; the output order is not specified (the caller sorts).
  */
 #include <math.h>
 #include <stdint.h>
@@ -98,71 +98,83 @@ int64_t oracle_pairs_below(const double* T, int D, int64_t n, int w, int d, int6
   const double tau2 = tau * tau;
 #pragma omp parallel
   {
-    double qt[64], dist[64];
+    /* diagonals advance in blocks of DB, row by row, so that the rows a
+       and a + delta of consecutive steps stay in cache; each diagonal's
+       recurrence runs in the same order as one diagonal at a time */
+    enum { DB = 32 };
+    static double qts[DB][64];
+#pragma omp threadprivate(qts)
+    double dist[64];
     int ord[64];
-#pragma omp for schedule(dynamic, 16)
-    for (int64_t delta = excl + 1; delta < M; ++delta) {
-      for (int64_t a = 0; a + delta < M; ++a) {
-        const int64_t b = a + delta;
-        const double* xa0 = X + (a - 1) * D;        /* point a - 1 (not read at a = 0) */
-        const double* xb0 = X + (b - 1) * D;
-        const double* xa1 = X + (a + w - 1) * D;    /* point a + w - 1 */
-        const double* xb1 = X + (b + w - 1) * D;
-        const int64_t oa = a * D, ob = b * D;
-        int near = 0;
-        for (int f = 0; f < D; ++f) {
-          if (a % 1024 == 0) {
-            double s = 0.0;
-            for (int t = 0; t < w; ++t) s += X[(a + t) * D + f] * X[(b + t) * D + f];
-            qt[f] = s;
-          } else {
-            qt[f] = qt[f] - xa0[f] * xb0[f] + xa1[f] * xb1[f];
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t d0 = excl + 1; d0 < M; d0 += DB) {
+      const int nb = (int)((M - d0) < DB ? (M - d0) : DB);
+      for (int64_t a = 0; a + d0 < M; ++a) {
+        for (int j = 0; j < nb; ++j) {
+          const int64_t delta = d0 + j;
+          const int64_t b = a + delta;
+          if (b >= M) break;                        /* longer diagonals first */
+          double* qt = qts[j];
+          const double* xa0 = X + (a - 1) * D;      /* point a - 1 (not read at a = 0) */
+          const double* xb0 = X + (b - 1) * D;
+          const double* xa1 = X + (a + w - 1) * D;  /* point a + w - 1 */
+          const double* xb1 = X + (b + w - 1) * D;
+          const int64_t oa = a * D, ob = b * D;
+          int near = 0;
+          for (int f = 0; f < D; ++f) {
+            if (a % 1024 == 0) {
+              double s = 0.0;
+              for (int t = 0; t < w; ++t) s += X[(a + t) * D + f] * X[(b + t) * D + f];
+              qt[f] = s;
+            } else {
+              qt[f] = qt[f] - xa0[f] * xb0[f] + xa1[f] * xb1[f];
+            }
+            double sq;
+            if (flat[oa + f] || flat[ob + f]) {
+              sq = (flat[oa + f] && flat[ob + f]) ? 0.0 : (double)w;
+            } else {
+              /* corr = (QT - w mu_a mu_b) / (w sigma_a sigma_b) */
+              const double corr = (qt[f] - wmu[oa + f] * mu[ob + f]) * isw[oa + f] * isw[ob + f] * w;
+              sq = 2.0 * w * (1.0 - corr);
+              if (sq < 0.0) sq = 0.0;
+            }
+            dist[f] = sq;                        /* squared for now */
+            near += sq <= tau2;
           }
-          double sq;
-          if (flat[oa + f] || flat[ob + f]) {
-            sq = (flat[oa + f] && flat[ob + f]) ? 0.0 : (double)w;
-          } else {
-            /* corr = (QT - w mu_a mu_b) / (w sigma_a sigma_b) */
-            const double corr = (qt[f] - wmu[oa + f] * mu[ob + f]) * isw[oa + f] * isw[ob + f] * w;
-            sq = 2.0 * w * (1.0 - corr);
-            if (sq < 0.0) sq = 0.0;
+          /* fewer than d dims within tau: one of the d smallest exceeds
+             tau, so dist_d > tau (distances are >= 0) */
+          if (near < d) continue;
+          for (int f = 0; f < D; ++f) dist[f] = sqrt(dist[f]);
+          /* the d smallest, ties to the lower dimension: insertion into an
+             ordered list of dimension indices */
+          int m = 0;
+          for (int f = 0; f < D; ++f) {
+            int p = m < d ? m : d;
+            while (p > 0 && dist[ord[p - 1]] > dist[f]) --p;
+            if (p >= d) continue;
+            const int last = m < d ? m : d - 1;
+            for (int q = last; q > p; --q) ord[q] = ord[q - 1];
+            ord[p] = f;
+            if (m < d) ++m;
           }
-          dist[f] = sq;                        /* squared for now */
-          near += sq <= tau2;
-        }
-        /* fewer than d dims within tau: one of the d smallest exceeds tau,
-           so dist_d > tau (distances are >= 0) */
-        if (near < d) continue;
-        for (int f = 0; f < D; ++f) dist[f] = sqrt(dist[f]);
-        /* the d smallest, ties to the lower dimension: insertion into an
-           ordered list of dimension indices */
-        int m = 0;
-        for (int f = 0; f < D; ++f) {
-          int p = m < d ? m : d;
-          while (p > 0 && dist[ord[p - 1]] > dist[f]) --p;
-          if (p >= d) continue;
-          const int last = m < d ? m : d - 1;
-          for (int q = last; q > p; --q) ord[q] = ord[q - 1];
-          ord[p] = f;
-          if (m < d) ++m;
-        }
-        double sum = 0.0, mx = 0.0;
-        uint64_t dims = 0;
-        for (int q = 0; q < d; ++q) {
-          sum += dist[ord[q]];
-          if (dist[ord[q]] > mx) mx = dist[ord[q]];
-          dims |= (uint64_t)1 << ord[q];
-        }
-        if (sum <= tau) {
-          int64_t slot;
+          double sum = 0.0, mx = 0.0;
+          uint64_t dims = 0;
+          for (int q = 0; q < d; ++q) {
+            sum += dist[ord[q]];
+            if (dist[ord[q]] > mx) mx = dist[ord[q]];
+            dims |= (uint64_t)1 << ord[q];
+          }
+          if (sum <= tau) {
+            int64_t slot;
 #pragma omp atomic capture
-          slot = found++;
-          if (slot < cap) {
-            out[slot].a = a;
-            out[slot].b = b;
-            out[slot].dist_d = sum;
-            out[slot].dist_max = mx;
-            out[slot].dims = dims;
+            slot = found++;
+            if (slot < cap) {
+              out[slot].a = a;
+              out[slot].b = b;
+              out[slot].dist_d = sum;
+              out[slot].dist_max = mx;
+              out[slot].dims = dims;
+            }
           }
         }
       }

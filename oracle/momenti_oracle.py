@@ -321,22 +321,29 @@ def exact_topk_diag(T, w, d, k, excl=None, tau0: float = 1.0):
     (dist_d, a, b) order, and double tau until k pairs are selected with
     the k-th at or below tau (then no unseen pair can change the
     selection).  Fewer than k are returned only when tau covers every pair
-    (2 d sqrt(w), the largest possible dist_d)."""
+    (2 d sqrt(w), the largest possible dist_d).
+
+    The sliding recurrence of pairs_below carries float64 rounding drift
+    (about 1e-9 relative), so it only picks the candidates: every pair up
+    to just past the k-th selected one (1e-6 relative, far above the drift)
+    is evaluated again by the definition (Eq. zned per dimension, direct
+    sums) and the greedy selection runs on those values."""
     eps = exclusion_zone(w, excl)
+    T64 = np.ascontiguousarray(T, dtype=np.float64)
     tau = float(tau0)
     top = 2.0 * d * math.sqrt(w)
     while True:
         cands = pairs_below(T, w, d, tau, excl)
-        acc = []
+        rough = greedy_topk([(float(c["dist_d"]), int(c["a"]), int(c["b"])) for c in cands], k, eps)
+        edge = tau if len(rough) < k else rough[-1][0] * (1.0 + 1e-6) + 1e-9
+        exact = []
         for c in cands:
-            a, b = int(c["a"]), int(c["b"])
-            if any(abs(a - q[1]) <= eps or abs(a - q[2]) <= eps or abs(b - q[1]) <= eps
-                   or abs(b - q[2]) <= eps for q in acc):
-                continue
-            dims = tuple(f for f in range(64) if int(c["dims"]) >> f & 1)
-            acc.append((float(c["dist_d"]), a, b, dims, float(c["dist_max"])))
-            if len(acc) == k:
+            if float(c["dist_d"]) > edge:
                 break
+            a, b = int(c["a"]), int(c["b"])
+            dd, dims, dmax = select_d(per_dim_distances(T64, w, a, b), d)
+            exact.append((dd, a, b, dims, dmax))
+        acc = greedy_topk(exact, k, eps)
         if (len(acc) == k and acc[-1][0] <= tau) or tau >= top:
             return acc
         tau *= 2.0
