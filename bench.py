@@ -202,9 +202,12 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
       proj_hash_tc    2 w flop per useful projection (M D L K of them)
       proj_hash_fp32  the same, on FP32 CUDA cores
       verify_events   8 D w bytes per verified pair (both windows, all dims)
-      allpairs        18 flop per pair and dim: the diagonal recurrence of
-                      the centred dot product and both window sums (10) and
-                      the Pearson threshold test (8)
+      allpairs        8 flop per pair and dim, the method's minimal count:
+                      the sliding cross product of the diagonal recurrence
+                      (two FMA, 4 flop) and the Pearson threshold test on
+                      per-window factors (one FMA, one multiply, one
+                      compare: 4); the kernels execute more (centring,
+                      column sums, three thresholds)
       sort_*          20 bytes per index entry (window, dim, repetition):
                       its 8-byte key read, the sorted 12-byte (key, window)
                       written; every kernel of the index sort together
@@ -229,7 +232,7 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
     elif kernel == "allpairs":
         excl = w // 2
         pairs = max(0, M - excl - 1) * max(0, M - excl) / 2.0
-        work = 18.0 * D * pairs * steps
+        work = 8.0 * D * pairs * steps
         bound, unit = "alu", "TFLOP/s"
         achieved = work / secs / 1e12
         peak, src = sm_peak, sm_src

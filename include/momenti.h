@@ -450,11 +450,11 @@ uint64_t momenti_launch_count(void);
  * A name ending in '*' selects every kernel whose name starts with the part
  * before it (for example "sort_*": all kernels of the index sort).
  * Kernel names: split_f32, split_f64, point_major, window_stats,
- * stats_pm, mean16, r_sample, draw, layout_hash, layout_boff,
+ * stats_pm, col_prep, mean16, r_sample, draw, layout_hash, layout_boff,
  * proj_hash_fp32, proj_hash_tc, rehash, sort_init, sort_hist, sort_scan,
  * sort_scatter, sort_local, tensor_keys, chunk_agg, chunk_scan, scan_local, scan_top,
  * scan_add, collide, bucket_jobs, subbucket, subwarp, hs_clear,
- * verify_events, verify_pairs, allpairs, select_pairs. */
+ * verify_events, verify_pairs, allpairs, allpairs_batch, select_pairs. */
 int momenti_time_kernel(const char* name);
 
 /* Device time in milliseconds accumulated by the timed kernel since the

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 
+#include <vector>
+
 namespace momenti {
 
 // Window count limit: the index sort puts tiles of 2048 windows on the
@@ -32,6 +34,9 @@ struct Index {
   int DW = 0;                 // 32 or 64 when xW is present
   float* smT = nullptr;       // [n-15][Dp] means of 16 consecutive points (D <= 8, w >= 32)
   float* stT = nullptr;       // [M][3][Dp] point-major mu_hi, mu_lo, inv_sig (D <= 8)
+  float* isT = nullptr;       // [M][Dp] 1/sigma (padding dims 1), float32 input, D <= 16
+  float* isW = nullptr;       // [M][DW] 1/sigma (padding dims 1), with xW
+  uint8_t* cflag = nullptr;   // [M] column window not testable in float32 by the sweep
   double* mu = nullptr;       // [D][M]
   double* sig = nullptr;      // [D][M]
   float* mu_hi = nullptr;     // [D][M]  float(mu)
@@ -287,6 +292,26 @@ cudaError_t launch_allpairs(const Index& ix, int d, float thr, const ApRec& rc, 
 // Whether the row-staged sweep of wide series (16 < D <= 64) takes this index
 // (a point-major copy, and its staged rows fit a CTA's shared memory).
 bool rows2_usable(const Index& ix);
+// One series' recording sweep inside a batched launch.
+struct SweepJob {
+  Index ix;
+  ApRec rc;
+  float thr = 0.f;
+  int d = 0;
+};
+struct SweepItem {
+  uint32_t job, bx, by;     // series, row block (kSeg windows), diagonal block
+};
+// Whether the sweep of this index can join a batched launch (float32
+// input, D <= 16, the statistics form).
+bool sweep_batchable(const Index& ix);
+// The recording sweeps of several series (each batchable) in one
+// persistent launch per padded dimension count, on stream s; every job's
+// record buffers must be ready on s.
+cudaError_t launch_allpairs_batch(const std::vector<SweepJob>& jobs, cudaStream_t s);
+// The column table of the statistics sweep (isT, cflag), after the window
+// statistics; nothing when the index has no isT.
+cudaError_t launch_col_prep(const Index& ix, cudaStream_t s);
 // Recorded pairs whose approximate distance lies in (lo, hi], compacted.
 cudaError_t launch_select_pairs(const uint64_t* pairs, const float* dd, uint64_t m, float lo,
                                 float hi, uint64_t* out, unsigned long long* count, cudaStream_t s);

@@ -19,6 +19,13 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
 
 namespace momenti {
 
@@ -151,6 +158,28 @@ __device__ __forceinline__ void load_row(const float* __restrict__ base, int64_t
     const float4 u = p[q];
     v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
   }
+}
+
+// The same through the read-only path with 256-bit loads (DP a multiple of
+// 8, rows 32-byte aligned): a lane's row is whole 32-byte sectors, one
+// instruction per 8 values.
+template <int DP>
+__device__ __forceinline__ void load_row_v8(const float* __restrict__ base, int64_t t, float (&v)[DP]) {
+  static_assert(DP % 8 == 0, "rows of whole 32-byte sectors");
+  const float* p = base + t * DP;
+#pragma unroll
+  for (int q = 0; q < DP / 8; ++q)
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[8 * q]), "=f"(v[8 * q + 1]), "=f"(v[8 * q + 2]), "=f"(v[8 * q + 3]),
+          "=f"(v[8 * q + 4]), "=f"(v[8 * q + 5]), "=f"(v[8 * q + 6]), "=f"(v[8 * q + 7])
+        : "l"(p + 8 * q));
+}
+
+// Column rows of the statistics sweeps: 256-bit loads where a row is whole sectors.
+template <int DP>
+__device__ __forceinline__ void load_col(const float* __restrict__ base, int64_t t, float (&v)[DP]) {
+  if constexpr (DP % 8 == 0) load_row_v8<DP>(base, t, v);
+  else load_row<DP>(base, t, v);
 }
 
 // dist_d of a pair from per-dim distances (registers), the d smallest.
@@ -877,6 +906,241 @@ k_allpairs_rows(Index ix, int d, float thr, ApRec rc, float* __restrict__ rowmin
   }
 }
 
+// Row-staged sweep with the threshold test on window statistics (float32
+// input, D <= 16, not the row minima).  The state of a diagonal is what the
+// rows kernel above slides, less the column sums of squares: the cross
+// product qt = sum (x_a - c_a)(x_b - c_b) of the row window a and the
+// column window b = a + delta, each centred on a constant (c_a per stage,
+// c_b per diagonal and stage), and the column sum s1b = sum (x_b - c_b).
+// The identity
+//   sum (x_a - mu_a)(x_b - mu_b) = qt - (mu_a - c_a) s1b  =: u
+// gives corr = u / (w sigma_a sigma_b), so for sigma > 0
+//   dist_f <= t  <=>  corr >= c(t) = 1 - t^2 / 2w  <=>  u / sigma_b >= c(t) w sigma_a.
+// mu_a - c_a and w sigma_a come per staged row from the float64 window
+// statistics, 1/sigma_b per column from the point-major table isT, so a
+// pair and dim costs one FMA (u), one more (v = u / sigma_b) and one FMA
+// per threshold whose sign bit is counted: the necessary conditions of the
+// rows kernel (x(1) <= thr/d, x(d) <= thr, with more than 8 dims also
+// x(2) <= thr/(d-1)).  Padding dims carry qt = -1 and 1/sigma = 1, so
+// every test on them fails.  A pair whose row or column window cannot be
+// tested reliably in float32 (flat, or its centring offset large against
+// its sigma: rflag per stage, cflag per column) is always a candidate.
+// Candidates go to a per-warp queue with their v per dim; their distances
+// are computed 32 at a time.
+constexpr int kRowSub3 = 256;
+
+// One block of the sweep: row windows [bx kSeg, bx kSeg + kSeg), diagonals
+// from eps + 1 + by kDiagBlock; RS rows staged at a time.
+template <int DP, int RS>
+__device__ __forceinline__ void rows3_body(const Index& ix, int d, float thr, const ApRec& rc,
+                                           int64_t bx, int64_t by) {
+  constexpr int DH = DP / 2;
+  constexpr bool kMid = DP >= 16;
+  constexpr int QS = DP + 2;                                    // queued: v per dim, row/unsure, column
+  extern __shared__ float ap_smem[];
+  const int w = ix.w, D = ix.D;
+  const int64_t a0 = bx * kSeg;
+  const int64_t dlo = int64_t(ix.excl) + 1 + by * kDiagBlock;
+  if (dlo >= ix.M || a0 >= ix.M - dlo) return;                  // block-uniform
+  const int64_t delta = dlo + threadIdx.x;
+  const bool live = delta < ix.M && a0 < ix.M - delta;
+  const int64_t a1 = live ? min(a0 + kSeg, ix.M - delta) : a0;
+  const int64_t nrow = min(int64_t(kSeg), ix.M - dlo - a0);
+  float* rowx = ap_smem;                                        // [RS][DH] {-(x_{a-1} - c_a) x2, x_{a+w-1} - c_a x2}
+  float* rowc = rowx + RS * 2 * DP;                             // [RS][DH] {-(mu_a - c_a) x2, w sigma_a x2}
+  float* cav = rowc + RS * 2 * DP;                              // [2][DP]
+  float* sprev = cav + 2 * DP;                                  // [DP]
+  float* qall = sprev + DP;                                     // [warps][32][QS]
+  __shared__ int rflag[RS];
+  const float* X = ix.xT;
+  const float wf = float(w);
+  const double wd = double(w);
+  const float4* rowx4 = reinterpret_cast<const float4*>(rowx);
+  const float4* rowc4 = reinterpret_cast<const float4*>(rowc);
+  float2 qt[DH], s1b[DH], ncb[DH];
+#pragma unroll
+  for (int p = 0; p < DH; ++p) {
+    const int f0 = 2 * p, f1 = 2 * p + 1;
+    qt[p] = make_float2(f0 < D ? 0.f : -1.f, f1 < D ? 0.f : -1.f);
+    s1b[p] = make_float2(0.f, 0.f);
+    ncb[p] = make_float2(live && f0 < D ? -ix.mu_hi[int64_t(f0) * ix.M + a0 + delta] : 0.f,
+                         live && f1 < D ? -ix.mu_hi[int64_t(f1) * ix.M + a0 + delta] : 0.f);
+  }
+  const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
+  const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
+  const float cd = 1.f - thr * thr / (2.f * wf);
+  const float2 nc1 = make_float2(-c1, -c1), nc2 = make_float2(-c2, -c2), ncd = make_float2(-cd, -cd);
+  const int need2 = d >= 2 ? 2 : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* qst = qall + warp * 32 * QS;
+  int64_t aS = a0;
+  auto drain = [&](int count) {
+    __syncwarp();
+    if (lane < count) {
+      const float* st = qst + lane * QS;
+      const uint32_t meta = __float_as_uint(st[DP]);
+      const int r = int(meta >> 1);
+      const bool uns = (meta & 1u) != 0;
+      float dist[DP];
+#pragma unroll
+      for (int f = 0; f < DP; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float wsa = rowc[(r * DH + (f >> 1)) * 4 + 2 + (f & 1)];
+          const float corr = st[f] / wsa;
+          dist[f] = sqrtf(fmaxf(2.f * wf * (1.f - corr), 0.f));
+        }
+      }
+      const float sm = uns ? 0.f : sum_d_smallest<DP>(dist, D, d);
+      if (sm <= thr && sm > rc.lo) record_pair(rc, aS + r, int64_t(__float_as_uint(st[DP + 1])), sm);
+    }
+    __syncwarp();
+  };
+  int qn = 0;
+  for (int stage = 0; aS < a0 + nrow; ++stage, aS += RS) {
+    const int nsub = int(min(int64_t(RS), a0 + nrow - aS));
+    float* cnew = cav + (stage & 1) * DP;
+    const float* cold = cav + ((stage & 1) ^ 1) * DP;
+    __syncthreads();                // the previous stage is fully consumed
+    if (threadIdx.x < DP) {
+      const int f = threadIdx.x;
+      const float c = f < D ? ix.mu_hi[int64_t(f) * ix.M + aS] : 0.f;
+      cnew[f] = c;
+      sprev[f] = (f < D && aS >= 1) ? float(wd * (ix.mu[int64_t(f) * ix.M + aS - 1] - double(c))) : 0.f;
+    }
+    for (int r = threadIdx.x; r < RS; r += blockDim.x) rflag[r] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nsub * DP; q += blockDim.x) {
+      const int r = q / DP, f = q - r * DP;
+      const int64_t a = aS + r;
+      float* rcq = rowc + (r * DH + (f >> 1)) * 4 + (f & 1);
+      float* rxq = rowx + (r * DH + (f >> 1)) * 4 + (f & 1);
+      if (f < D) {
+        const float c = cnew[f];
+        rxq[0] = a >= 1 ? c - X[(a - 1) * DP + f] : 0.f;
+        rxq[2] = X[(a + w - 1) * DP + f] - c;
+        // unreliable (flat, or the centring offset large against sigma):
+        // sigma^2 <= 1e-4 (sigma^2 + (mu - c)^2)
+        const double m = ix.mu[int64_t(f) * ix.M + a], sg = ix.sig[int64_t(f) * ix.M + a];
+        const double dm = m - double(c), v = sg * sg;
+        const bool ok = v > 1e-4 * (v + dm * dm) && ix.inv_sig[int64_t(f) * ix.M + a] != 0.f;
+        rcq[0] = ok ? float(-dm) : 0.f;
+        rcq[2] = ok ? float(wd * sg) : 1.f;
+        if (!ok) atomicOr(&rflag[r], 1);
+      } else {
+        rxq[0] = rxq[2] = 0.f;
+        rcq[0] = 0.f;
+        rcq[2] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (stage == 0) {
+      // direct start: row window a0 against column window a0 + delta
+      for (int t = 0; t < (live ? w : 0); ++t) {
+        float xa[DP], xb[DP];
+        load_row<DP>(X, a0 + t, xa);                            // same address over the block
+        load_row<DP>(X, a0 + delta + t, xb);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          const float2 u = make_float2(xa[2 * p] - cnew[2 * p], xa[2 * p + 1] - cnew[2 * p + 1]);
+          const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(u, v, qt[p]);
+          s1b[p] = __fadd2_rn(s1b[p], v);
+        }
+      }
+    } else if (aS - 1 < a1) {
+      // the state holds row window aS - 1 and column window aS - 1 + delta:
+      // re-centre the rows on this stage's constant, then the column on
+      // that column window's mean
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const int f0 = 2 * p, f1 = 2 * p + 1;
+        const float2 dr = make_float2(cold[f0] - cnew[f0], cold[f1] - cnew[f1]);
+        qt[p] = __ffma2_rn(dr, s1b[p], qt[p]);
+        const float2 cbn = make_float2(f0 < D ? ix.mu_hi[int64_t(f0) * ix.M + aS - 1 + delta] : 0.f,
+                                       f1 < D ? ix.mu_hi[int64_t(f1) * ix.M + aS - 1 + delta] : 0.f);
+        const float2 dc = make_float2(cbn.x + ncb[p].x, cbn.y + ncb[p].y);
+        qt[p] = __ffma2_rn(make_float2(-dc.x, -dc.y), make_float2(sprev[f0], sprev[f1]), qt[p]);
+        s1b[p] = __ffma2_rn(make_float2(-wf, -wf), dc, s1b[p]);
+        ncb[p] = make_float2(-cbn.x, -cbn.y);
+      }
+    }
+    for (int r = 0; r < nsub; ++r) {
+      const int64_t a = aS + r;
+      const int64_t b = a + delta;
+      const bool act = a < a1;
+      float isb[DP];
+      int unsure = rflag[r];
+      if (act) {
+        if (r > 0 || stage > 0) {
+          float ob[DP], ib[DP];
+          load_col<DP>(X, b - 1, ob);
+          load_col<DP>(X, b + w - 1, ib);
+#pragma unroll
+          for (int p = 0; p < DH; ++p) {
+            const float4 xq = rowx4[r * DH + p];
+            const float2 o = make_float2(ob[2 * p], ob[2 * p + 1]);
+            const float2 i = make_float2(ib[2 * p], ib[2 * p + 1]);
+            const float2 vo = __fadd2_rn(o, ncb[p]), vi = __fadd2_rn(i, ncb[p]);
+            qt[p] = __ffma2_rn(make_float2(xq.z, xq.w), vi, __ffma2_rn(make_float2(xq.x, xq.y), vo, qt[p]));
+            s1b[p] = __ffma2_rn(make_float2(-1.f, -1.f), o, __fadd2_rn(s1b[p], i));
+          }
+        }
+        load_col<DP>(ix.isT, b, isb);
+        unsure |= ix.cflag[b];
+      } else {
+#pragma unroll
+        for (int f = 0; f < DP; ++f) isb[f] = 0.f;
+      }
+      uint32_t all1 = 0xffffffffu;  // sign bits of x(1)'s test: all set = no dim passes
+      int negd = 0, neg2 = 0;       // dims failing x(d)'s and x(2)'s tests
+      float2 v[DH];
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const float4 rq = rowc4[r * DH + p];
+        const float2 u = __ffma2_rn(make_float2(rq.x, rq.y), s1b[p], qt[p]);
+        v[p] = __fmul2_rn(u, make_float2(isb[2 * p], isb[2 * p + 1]));
+        const float2 wsa = make_float2(rq.z, rq.w);
+        const float2 e1 = __ffma2_rn(nc1, wsa, v[p]);
+        const float2 ed = __ffma2_rn(ncd, wsa, v[p]);
+        all1 &= __float_as_uint(e1.x) & __float_as_uint(e1.y);
+        negd += int(__float_as_uint(ed.x) >> 31) + int(__float_as_uint(ed.y) >> 31);
+        if constexpr (kMid) {
+          const float2 e2 = __ffma2_rn(nc2, wsa, v[p]);
+          neg2 += int(__float_as_uint(e2.x) >> 31) + int(__float_as_uint(e2.y) >> 31);
+        }
+      }
+      const bool cand = act && (unsure || ((all1 >> 31) == 0u && DP - negd >= d &&
+                                           (!kMid || DP - neg2 >= need2)));
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (!m) continue;
+      const int n = __popc(m);
+      if (qn + n > 32) {
+        drain(qn);
+        qn = 0;
+      }
+      if (cand) {
+        const int pos = qn + __popc(m & ((1u << lane) - 1u));
+        float* st = qst + pos * QS;
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          st[2 * p] = v[p].x;
+          st[2 * p + 1] = v[p].y;
+        }
+        st[DP] = __uint_as_float((uint32_t(r) << 1) | (unsure ? 1u : 0u));
+        st[DP + 1] = __uint_as_float(uint32_t(b));
+      }
+      qn += n;
+      if (qn == 32) {
+        drain(32);
+        qn = 0;
+      }
+    }
+    drain(qn);                      // queued pairs refer to this stage's rows
+    qn = 0;
+  }
+}
+
 // Row-staged sweep for 16 < D <= DW (point-major copy X [n][DW], float32
 // input): the rows kernel above with the dims of each diagonal split over
 // G = DW / 16 adjacent lanes, 16 dims each, so that every lane keeps the
@@ -1156,6 +1420,259 @@ k_allpairs_rows2(Index ix, const float* __restrict__ X, int d, float thr, ApRec 
   }
 }
 
+// The sweep as a grid of blocks (x: row blocks, y: diagonal blocks from ybase).
+template <int DP, int RS, int MINB>
+__global__ void __launch_bounds__(kDiagBlock, MINB)
+k_allpairs_rows3(Index ix, int d, float thr, ApRec rc, int64_t ybase) {
+  rows3_body<DP, RS>(ix, d, thr, rc, int64_t(blockIdx.x), ybase + int64_t(blockIdx.y));
+}
+
+// The sweeps of several series in one persistent launch: each CTA takes
+// (series, row block, diagonal block) items from a device queue in order
+// (largest series first) until the queue is empty; an item is one block of
+// the sweep above on that series' index, threshold and record buffers.
+template <int DP, int RS, int MINB>
+__global__ void __launch_bounds__(kDiagBlock, MINB)
+k_allpairs_rows3_batch(const SweepJob* __restrict__ jobs, const SweepItem* __restrict__ items,
+                       int nitems, int* __restrict__ next) {
+  __shared__ int cur;
+  for (;;) {
+    __syncthreads();                // every thread has read the previous item
+    if (threadIdx.x == 0) cur = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) return;       // block-uniform
+    const SweepItem q = items[it];
+    const SweepJob& j = jobs[q.job];
+    rows3_body<DP, RS>(j.ix, j.d, j.thr, j.rc, int64_t(q.bx), int64_t(q.by));
+  }
+}
+
+// The statistics form of the threshold test (the rows3 kernel above) for
+// wide series, 16 < D <= DW (point-major copy X [n][DW], float32 input),
+// with the dims of a diagonal split over G = DW / 16 adjacent lanes as in
+// the rows2 kernel.  Each lane slides qt and s1b of its 16 dims and tests
+// them against its row factors and the column table isW; the lanes of a
+// diagonal combine their sign-bit counts with shuffles.  A candidate's v
+// per dim goes to a per-warp queue (one entry per diagonal, each lane
+// writing its dims) and its distances are computed by one lane.
+template <int DW>
+__global__ void __launch_bounds__(kDiagBlock, DW <= 32 ? 2 : 1)
+k_allpairs_rows4(Index ix, const float* __restrict__ X, int d, float thr, ApRec rc, int64_t ybase) {
+  constexpr int G = DW / 16;                 // lanes per diagonal
+  constexpr int NDG = kDiagBlock / G;        // diagonals per block
+  constexpr int DH = 8;                      // float2 pairs of dims per lane
+  constexpr int DW2 = DW / 2;
+  constexpr int RS = kRowSub2;
+  constexpr int QS = DW + 2;                 // queued: v per dim, row/unsure, column
+  constexpr int QN = 32 / G;                 // queue entries per warp
+  extern __shared__ float ap_smem[];
+  const int w = ix.w, D = ix.D;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = threadIdx.x % G;
+  const int f0 = 16 * g;                     // this lane's first dim
+  const int64_t a0 = int64_t(blockIdx.x) * kSeg;
+  const int64_t dlo = int64_t(ix.excl) + 1 + (ybase + int64_t(blockIdx.y)) * NDG;
+  if (dlo >= ix.M || a0 >= ix.M - dlo) return;                  // block-uniform
+  const int64_t delta = dlo + threadIdx.x / G;
+  const bool live = delta < ix.M && a0 < ix.M - delta;
+  const int64_t a1 = live ? min(a0 + kSeg, ix.M - delta) : a0;
+  const int64_t nrow = min(int64_t(kSeg), ix.M - dlo - a0);
+  float* nuo = ap_smem;                                         // [RS][DW] -(x_{a-1} - c_a)
+  float* uin = nuo + RS * DW;                                   // [RS][DW] x_{a+w-1} - c_a
+  float* rowc = uin + RS * DW;                                  // [RS][DW2] {-(mu_a - c_a) x2, w sigma_a x2}
+  float* cav = rowc + RS * 2 * DW;                              // [2][DW]
+  float* sprev = cav + 2 * DW;                                  // [DW]
+  float* qall = sprev + DW;                                     // [warps][QN][QS]
+  __shared__ int rflag[RS];
+  const float wf = float(w);
+  const double wd = double(w);
+  const float2* nuo2 = reinterpret_cast<const float2*>(nuo);
+  const float2* uin2 = reinterpret_cast<const float2*>(uin);
+  const float4* rowc4 = reinterpret_cast<const float4*>(rowc);
+  float2 qt[DH], s1b[DH], ncb[DH];
+#pragma unroll
+  for (int p = 0; p < DH; ++p) {
+    const int fa = f0 + 2 * p, fb = fa + 1;
+    qt[p] = make_float2(fa < D ? 0.f : -1.f, fb < D ? 0.f : -1.f);
+    s1b[p] = make_float2(0.f, 0.f);
+    ncb[p] = make_float2(live && fa < D ? -ix.mu_hi[int64_t(fa) * ix.M + a0 + delta] : 0.f,
+                         live && fb < D ? -ix.mu_hi[int64_t(fb) * ix.M + a0 + delta] : 0.f);
+  }
+  const float t1 = thr / float(d), t2 = d >= 2 ? thr / float(d - 1) : thr;
+  const float c1 = 1.f - t1 * t1 / (2.f * wf), c2 = 1.f - t2 * t2 / (2.f * wf);
+  const float cd = 1.f - thr * thr / (2.f * wf);
+  const float2 nc1 = make_float2(-c1, -c1), nc2 = make_float2(-c2, -c2), ncd = make_float2(-cd, -cd);
+  const int need2 = d >= 2 ? 2 : 1;
+  float* qst = qall + warp * QN * QS;
+  int64_t aS = a0;
+  auto drain = [&](int count) {
+    __syncwarp();
+    if (lane < count) {
+      const float* st = qst + lane * QS;
+      const uint32_t meta = __float_as_uint(st[DW]);
+      const int r = int(meta >> 1);
+      const bool uns = (meta & 1u) != 0;
+      float dist[DW];
+#pragma unroll
+      for (int f = 0; f < DW; ++f) {
+        dist[f] = INFINITY;
+        if (f < D) {
+          const float wsa = rowc[(r * DW2 + (f >> 1)) * 4 + 2 + (f & 1)];
+          const float corr = st[f] / wsa;
+          dist[f] = sqrtf(fmaxf(2.f * wf * (1.f - corr), 0.f));
+        }
+      }
+      const float sm = uns ? 0.f : sum_d_smallest<DW>(dist, D, d);
+      if (sm <= thr && sm > rc.lo) record_pair(rc, aS + r, int64_t(__float_as_uint(st[DW + 1])), sm);
+    }
+    __syncwarp();
+  };
+  int qn = 0;                       // queued diagonals of this warp (warp-uniform)
+  for (int stage = 0; aS < a0 + nrow; ++stage, aS += RS) {
+    const int nsub = int(min(int64_t(RS), a0 + nrow - aS));
+    float* cnew = cav + (stage & 1) * DW;
+    const float* cold = cav + ((stage & 1) ^ 1) * DW;
+    __syncthreads();                // the previous stage is fully consumed
+    if (threadIdx.x < DW) {
+      const int f = threadIdx.x;
+      const float c = f < D ? ix.mu_hi[int64_t(f) * ix.M + aS] : 0.f;
+      cnew[f] = c;
+      sprev[f] = (f < D && aS >= 1) ? float(wd * (ix.mu[int64_t(f) * ix.M + aS - 1] - double(c))) : 0.f;
+    }
+    for (int r = threadIdx.x; r < RS; r += blockDim.x) rflag[r] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nsub * DW; q += blockDim.x) {
+      const int r = q / DW, f = q - r * DW;
+      const int64_t a = aS + r;
+      float* rcq = rowc + (r * DW2 + (f >> 1)) * 4 + (f & 1);
+      if (f < D) {
+        const float c = cnew[f];
+        nuo[q] = a >= 1 ? c - X[(a - 1) * DW + f] : 0.f;
+        uin[q] = X[(a + w - 1) * DW + f] - c;
+        const double m = ix.mu[int64_t(f) * ix.M + a], sg = ix.sig[int64_t(f) * ix.M + a];
+        const double dm = m - double(c), v = sg * sg;
+        const bool ok = v > 1e-4 * (v + dm * dm) && ix.inv_sig[int64_t(f) * ix.M + a] != 0.f;
+        rcq[0] = ok ? float(-dm) : 0.f;
+        rcq[2] = ok ? float(wd * sg) : 1.f;
+        if (!ok) atomicOr(&rflag[r], 1);
+      } else {
+        nuo[q] = uin[q] = 0.f;
+        rcq[0] = 0.f;
+        rcq[2] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (stage == 0) {
+      for (int t = 0; t < (live ? w : 0); ++t) {
+        float xa[16], xb[16];
+        load_row<16>(X + f0, (a0 + t) * G, xa);                 // same address over the block
+        load_row<16>(X + f0, (a0 + delta + t) * G, xb);
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          const float2 u = make_float2(xa[2 * p] - cnew[f0 + 2 * p], xa[2 * p + 1] - cnew[f0 + 2 * p + 1]);
+          const float2 v = __fadd2_rn(make_float2(xb[2 * p], xb[2 * p + 1]), ncb[p]);
+          qt[p] = __ffma2_rn(u, v, qt[p]);
+          s1b[p] = __fadd2_rn(s1b[p], v);
+        }
+      }
+    } else if (aS - 1 < a1) {
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const int fa = f0 + 2 * p, fb = fa + 1;
+        const float2 dr = make_float2(cold[fa] - cnew[fa], cold[fb] - cnew[fb]);
+        qt[p] = __ffma2_rn(dr, s1b[p], qt[p]);
+        const float2 cbn = make_float2(fa < D ? ix.mu_hi[int64_t(fa) * ix.M + aS - 1 + delta] : 0.f,
+                                       fb < D ? ix.mu_hi[int64_t(fb) * ix.M + aS - 1 + delta] : 0.f);
+        const float2 dc = make_float2(cbn.x + ncb[p].x, cbn.y + ncb[p].y);
+        qt[p] = __ffma2_rn(make_float2(-dc.x, -dc.y), make_float2(sprev[fa], sprev[fb]), qt[p]);
+        s1b[p] = __ffma2_rn(make_float2(-wf, -wf), dc, s1b[p]);
+        ncb[p] = make_float2(-cbn.x, -cbn.y);
+      }
+    }
+    for (int r = 0; r < nsub; ++r) {
+      const int64_t a = aS + r;
+      const int64_t b = a + delta;
+      const bool act = a < a1;
+      float isb[16];
+      int unsure = rflag[r];
+      if (act) {
+        if (r > 0 || stage > 0) {
+          float ob[16], ib[16];
+          load_row_v8<16>(X + f0, (b - 1) * G, ob);
+          load_row_v8<16>(X + f0, (b + w - 1) * G, ib);
+#pragma unroll
+          for (int p = 0; p < DH; ++p) {
+            const float2 o = make_float2(ob[2 * p], ob[2 * p + 1]);
+            const float2 i = make_float2(ib[2 * p], ib[2 * p + 1]);
+            const float2 vo = __fadd2_rn(o, ncb[p]), vi = __fadd2_rn(i, ncb[p]);
+            qt[p] = __ffma2_rn(uin2[r * DW2 + f0 / 2 + p], vi, __ffma2_rn(nuo2[r * DW2 + f0 / 2 + p], vo, qt[p]));
+            s1b[p] = __ffma2_rn(make_float2(-1.f, -1.f), o, __fadd2_rn(s1b[p], i));
+          }
+        }
+        load_row_v8<16>(ix.isW + f0, b * G, isb);
+        unsure |= ix.cflag[b];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 16; ++f) isb[f] = 0.f;
+      }
+      uint32_t all1 = 0xffffffffu;
+      int negs = 0;                 // dims failing x(d)'s test (low half) and x(2)'s (high half)
+      float2 v[DH];
+#pragma unroll
+      for (int p = 0; p < DH; ++p) {
+        const float4 rq = rowc4[r * DW2 + f0 / 2 + p];
+        const float2 u = __ffma2_rn(make_float2(rq.x, rq.y), s1b[p], qt[p]);
+        v[p] = __fmul2_rn(u, make_float2(isb[2 * p], isb[2 * p + 1]));
+        const float2 wsa = make_float2(rq.z, rq.w);
+        const float2 e1 = __ffma2_rn(nc1, wsa, v[p]);
+        const float2 ed = __ffma2_rn(ncd, wsa, v[p]);
+        const float2 e2 = __ffma2_rn(nc2, wsa, v[p]);
+        all1 &= __float_as_uint(e1.x) & __float_as_uint(e1.y);
+        negs += int(__float_as_uint(ed.x) >> 31) + int(__float_as_uint(ed.y) >> 31) +
+                ((int(__float_as_uint(e2.x) >> 31) + int(__float_as_uint(e2.y) >> 31)) << 16);
+      }
+      // the diagonal's totals over its G lanes
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        all1 &= __shfl_xor_sync(0xffffffffu, all1, o);
+        negs += __shfl_xor_sync(0xffffffffu, negs, o);
+        unsure |= __shfl_xor_sync(0xffffffffu, unsure, o);
+      }
+      const int negd = negs & 0xffff, neg2 = negs >> 16;
+      const bool cand = act && (unsure || ((all1 >> 31) == 0u && DW - negd >= d && DW - neg2 >= need2));
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (!m) continue;
+      const int n = __popc(m) / G;                  // candidate diagonals of this step
+      if (qn + n > QN) {
+        drain(qn);
+        qn = 0;
+      }
+      if (cand) {
+        const int base = lane - g;                  // the diagonal's first lane
+        const int pos = qn + __popc(m & ((1u << base) - 1u)) / G;
+        float* st = qst + pos * QS;
+#pragma unroll
+        for (int p = 0; p < DH; ++p) {
+          st[f0 + 2 * p] = v[p].x;
+          st[f0 + 2 * p + 1] = v[p].y;
+        }
+        if (g == 0) {
+          st[DW] = __uint_as_float((uint32_t(r) << 1) | (unsure ? 1u : 0u));
+          st[DW + 1] = __uint_as_float(uint32_t(b));
+        }
+      }
+      qn += n;
+      if (qn == QN) {
+        drain(QN);
+        qn = 0;
+      }
+    }
+    drain(qn);                      // queued diagonals refer to this stage's rows
+    qn = 0;
+  }
+}
+
 // Wide series (D > 16): per-window means and 1/sigma are read per step;
 // every thread of a block walks the same row windows a (their values are
 // broadcast loads) against its own diagonal.  Only the D centred cross
@@ -1257,7 +1774,327 @@ size_t rows2_smem(int w, int dw) {
           size_t(kDiagBlock / 32) * QN * (3 * dw + 2) + 2 * size_t(kDiagBlock / 32) * QN) * sizeof(float);
 }
 
+// the statistics sweep: two staged points and the row factors per row and
+// dim for rs rows, a queue of 32 candidates (v per dim, row, column) per warp
+size_t rows3_smem(int dp, int rs) {
+  return size_t(4 * rs * dp + 3 * dp + kDiagBlock * (dp + 2)) * sizeof(float);
+}
+
+// the wide statistics sweep: rows3's staging for kRowSub2 rows of DW dims,
+// a queue of 32/G diagonals per warp
+size_t rows4_smem(int dw) {
+  const int G = dw / 16, QN = 32 / G;
+  return size_t(4 * kRowSub2 * dw + 3 * dw + (kDiagBlock / 32) * QN * (dw + 2)) * sizeof(float);
+}
+
+// ---- recording-sweep variants and their autotuner -------------------------
+// A float32 index has several forms of the recording sweep, all recording
+// the same pairs: for D <= 16 the statistics form with two stage heights
+// and the slid form (k_allpairs_rows, whose staging grows with w); for
+// 16 < D <= 64 the statistics and the slid wide forms.  Which one is
+// fastest depends on the padded D, w and M.  The grid of every launch
+// below may be cut to its first gy_max diagonal blocks (the autotuner's
+// probe).
+
+template <int DP, int RS, int MINB>
+cudaError_t rows3_launch(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                         int64_t gy_max) {
+  const int64_t ndiag = ix.M - (ix.excl + 1);
+  const int64_t gy = std::min<int64_t>((ndiag + kDiagBlock - 1) / kDiagBlock, gy_max);
+  const size_t smem = rows3_smem(DP, RS);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows3<DP, RS, MINB>), smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows3<DP, RS, MINB><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, y0));
+  }
+  return cudaGetLastError();
+}
+
+template <int DP>
+cudaError_t rows_slid_launch(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                             int64_t gy_max) {
+  const int64_t ndiag = ix.M - (ix.excl + 1);
+  const int64_t gy = std::min<int64_t>((ndiag + kDiagBlock - 1) / kDiagBlock, gy_max);
+  const size_t smem = rows_smem(ix.w, DP);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows<DP, false>), smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows<DP, false><<<grid, kDiagBlock, smem, s>>>(ix, d, thr, rc, nullptr, y0));
+  }
+  return cudaGetLastError();
+}
+
+template <int DW>
+cudaError_t rows4_launch(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                         int64_t gy_max) {
+  const int64_t ndiag = ix.M - (ix.excl + 1);
+  constexpr int NDG = kDiagBlock / (DW / 16);
+  const int64_t gy = std::min<int64_t>((ndiag + NDG - 1) / NDG, gy_max);
+  const size_t smem = rows4_smem(DW);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows4<DW>), smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows4<DW><<<grid, kDiagBlock, smem, s>>>(ix, ix.xW, d, thr, rc, y0));
+  }
+  return cudaGetLastError();
+}
+
+template <int DW>
+cudaError_t rows2_launch(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                         int64_t gy_max) {
+  const int64_t ndiag = ix.M - (ix.excl + 1);
+  constexpr int NDG = kDiagBlock / (DW / 16);
+  const int64_t gy = std::min<int64_t>((ndiag + NDG - 1) / NDG, gy_max);
+  const size_t smem = rows2_smem(ix.w, DW);
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows2<DW, false>), smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    dim3 grid{unsigned((ix.M + kSeg - 1) / kSeg), unsigned(std::min<int64_t>(65535, gy - y0)), 1u};
+    MOMENTI_LAUNCH("allpairs", s, k_allpairs_rows2<DW, false><<<grid, kDiagBlock, smem, s>>>(ix, ix.xW, d, thr, rc, nullptr, y0));
+  }
+  return cudaGetLastError();
+}
+
+bool aligned32(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 31u) == 0; }
+
+// Candidates for this index (0 when the recording sweep has no variants:
+// float64 input, no point-major copy).  The statistics forms read column
+// rows with 256-bit loads, so their rows must start on 32-byte boundaries
+// (the pool aligns far beyond that; checked, not assumed).
+int sweep_variants(const Index& ix) {
+  if (ix.xW && ix.isW && rows2_usable(ix) && aligned32(ix.xW) && aligned32(ix.isW)) return 2;
+  if (ix.isT && ix.xT && !ix.has_lo && aligned32(ix.xT) && aligned32(ix.isT))
+    return rows_fit(ix.w, ix.Dp) ? 3 : 2;
+  return 0;
+}
+
+// Variant v: wide: 0 statistics, 1 slid; D <= 16: 0 statistics with the
+// taller stage, 1 statistics with half of it, 2 slid.
+cudaError_t sweep_launch(const Index& ix, int v, int d, float thr, const ApRec& rc, cudaStream_t s,
+                         int64_t gy_max) {
+  if (ix.xW) {
+    if (ix.DW == 32) return v == 0 ? rows4_launch<32>(ix, d, thr, rc, s, gy_max) : rows2_launch<32>(ix, d, thr, rc, s, gy_max);
+    return v == 0 ? rows4_launch<64>(ix, d, thr, rc, s, gy_max) : rows2_launch<64>(ix, d, thr, rc, s, gy_max);
+  }
+  switch (ix.Dp) {
+    case 4:
+      if (v == 0) return rows3_launch<4, kRowSub3, 3>(ix, d, thr, rc, s, gy_max);
+      if (v == 1) return rows3_launch<4, kRowSub3 / 2, 3>(ix, d, thr, rc, s, gy_max);
+      return rows_slid_launch<4>(ix, d, thr, rc, s, gy_max);
+    case 8:
+      if (v == 0) return rows3_launch<8, kRowSub3, 3>(ix, d, thr, rc, s, gy_max);
+      if (v == 1) return rows3_launch<8, kRowSub3 / 2, 3>(ix, d, thr, rc, s, gy_max);
+      return rows_slid_launch<8>(ix, d, thr, rc, s, gy_max);
+    default:
+      if (v == 0) return rows3_launch<16, kRowSub3 / 2, 2>(ix, d, thr, rc, s, gy_max);
+      if (v == 1) return rows3_launch<16, kRowSub3 / 4, 2>(ix, d, thr, rc, s, gy_max);
+      return rows_slid_launch<16>(ix, d, thr, rc, s, gy_max);
+  }
+}
+
+struct TuneKey {
+  int dev, dp, lw, lm;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, dp, lw, lm) < std::tie(o.dev, o.dp, o.lw, o.lm);
+  }
+};
+std::mutex& tune_mu() {
+  static std::mutex m;
+  return m;
+}
+std::map<TuneKey, int>& tune_map() {
+  static std::map<TuneKey, int> t;
+  return t;
+}
+int ilog2(int64_t x) {
+  int l = 0;
+  while (x > 1) { x >>= 1; ++l; }
+  return l;
+}
+
+// The variant the sweep of this index runs: MOMENTI_SWEEP_VARIANT=v forces
+// one; MOMENTI_AUTOTUNE=0 takes variant 0; otherwise the cached choice for
+// (device, padded D, log2 w, log2 M), or, the first time, the fastest
+// candidate on a probe: every candidate runs three times over the grid's
+// first diagonal blocks (about four waves of CTAs, the longest diagonals)
+// with a negative threshold, which records nothing; the faster of the last
+// two runs counts (CUDA events on the sweep's stream).  Probes run one at a
+// time in the process.
+int sweep_variant(const Index& ix, int d, const ApRec& rc, cudaStream_t s) {
+  const int nv = sweep_variants(ix);
+  if (const char* f = std::getenv("MOMENTI_SWEEP_VARIANT"); f && f[0] >= '0' && f[0] <= '9')
+    return std::min(nv - 1, int(f[0] - '0'));
+  if (nv <= 1) return 0;
+  if (const char* e = std::getenv("MOMENTI_AUTOTUNE"); e && e[0] == '0') return 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TuneKey key{dev, ix.xW ? ix.DW : ix.Dp, ilog2(ix.w), ilog2(ix.M)};
+  {
+    std::lock_guard<std::mutex> g(tune_mu());
+    auto it = tune_map().find(key);
+    if (it != tune_map().end()) return it->second;
+  }
+  // one probe at a time in the process (probes of other threads would
+  // share the GPU with this one and distort its timings)
+  static std::mutex probe_mu;
+  std::lock_guard<std::mutex> probe_lock(probe_mu);
+  {
+    std::lock_guard<std::mutex> g(tune_mu());
+    auto it = tune_map().find(key);
+    if (it != tune_map().end()) return it->second;
+  }
+  const int64_t nbx = (ix.M + kSeg - 1) / kSeg;
+  const int64_t gy_probe = std::max<int64_t>(1, (int64_t(sm_count()) * 8 + nbx - 1) / nbx);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return 0;
+  }
+  int best = 0;
+  float best_ms = INFINITY;
+  std::string line;
+  for (int v = 0; v < nv; ++v) {
+    float ms = INFINITY;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {    // a warm-up, then the faster of two
+      float t = INFINITY;
+      ok = cudaEventRecord(e0, s) == cudaSuccess &&
+           sweep_launch(ix, v, d, -1.f, rc, s, gy_probe) == cudaSuccess &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+      if (rep > 0) ms = std::min(ms, t);
+    }
+    if (!ok) {
+      cudaGetLastError();       // a candidate that cannot launch is skipped
+      continue;
+    }
+    line += " v" + std::to_string(v) + "=" + std::to_string(ms);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> g(tune_mu());
+    tune_map().emplace(key, best);
+  }
+  if (const char* t = std::getenv("MOMENTI_TRACE"); t && t[0] == '1')
+    std::fprintf(stderr, "momenti trace: sweep autotune dp=%d w=%d M=%lld ms:%s -> v%d\n", key.dp, ix.w,
+                 (long long)ix.M, line.c_str(), best);
+  return best;
+}
+
+// Column table of the statistics sweep: isT[b][f] = 1/sigma (0 for flat
+// windows, 1 for padding dims) and cflag[b] = 1 when some dim of window b
+// is flat or its column centring offset may be large against its sigma.
+// The centring constant of a diagonal is the float32 mean of a column
+// window b' in [b - kRowSub3, b] (the stage's first column), so b is marked
+// when sigma^2 <= 1e-4 (sigma^2 + max |mean(b') - mean(b)|^2) there, the
+// condition the rows kernels apply to the offset they actually carry.
+__global__ void k_col_prep(Index ix) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= ix.M) return;
+  float* tab = ix.isT ? ix.isT : ix.isW;
+  const int DP = ix.isT ? ix.Dp : ix.DW;
+  int u = 0;
+  for (int f = 0; f < DP; ++f) {
+    float is = 1.f;
+    if (f < ix.D) {
+      const int64_t o = int64_t(f) * ix.M;
+      is = ix.inv_sig[o + b];
+      const float mb = ix.mu_hi[o + b];
+      float dmax = 0.f;
+      for (int64_t q = b > kRowSub3 ? b - kRowSub3 : 0; q <= b; ++q)
+        dmax = fmaxf(dmax, fabsf(ix.mu_hi[o + q] - mb));
+      const double sg = ix.sig[o + b], v = sg * sg, dm = double(dmax);
+      u |= (is == 0.f) || !(v > 1e-4 * (v + dm * dm));
+    }
+    tab[b * DP + f] = is;
+  }
+  ix.cflag[b] = uint8_t(u);
+}
+
 }  // namespace
+
+cudaError_t launch_col_prep(const Index& ix, cudaStream_t s) {
+  if (!ix.isT && !ix.isW) return cudaSuccess;
+  MOMENTI_LAUNCH("col_prep", s, k_col_prep<<<unsigned((ix.M + 255) / 256), 256, 0, s>>>(ix));
+  return cudaGetLastError();
+}
+
+bool sweep_batchable(const Index& ix) {
+  return !ix.xW && sweep_variants(ix) > 0;
+}
+
+cudaError_t launch_allpairs_batch(const std::vector<SweepJob>& jobs, cudaStream_t s) {
+  if (jobs.empty()) return cudaSuccess;
+  for (const auto& j : jobs)
+    if (!sweep_batchable(j.ix)) return cudaErrorInvalidValue;
+  // items of every job, largest series first; one persistent launch per
+  // padded dimension count (the kernel's register and shared-memory shape)
+  std::vector<int> order(jobs.size());
+  for (size_t q = 0; q < jobs.size(); ++q) order[q] = int(q);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jobs[x].ix.M > jobs[y].ix.M; });
+  SweepJob* djobs = nullptr;
+  cudaError_t e = cudaMallocAsync(&djobs, jobs.size() * sizeof(SweepJob), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(djobs, jobs.data(), jobs.size() * sizeof(SweepJob), cudaMemcpyHostToDevice, s);
+  for (int dp : {4, 8, 16}) {
+    std::vector<SweepItem> items;
+    for (int q : order) {
+      const Index& ix = jobs[q].ix;
+      if (ix.Dp != dp || ix.M - (ix.excl + 1) <= 0) continue;
+      const int64_t nbx = (ix.M + kSeg - 1) / kSeg;
+      const int64_t gy = (ix.M - (ix.excl + 1) + kDiagBlock - 1) / kDiagBlock;
+      for (int64_t by = 0; by < gy; ++by) {
+        const int64_t dlo = int64_t(ix.excl) + 1 + by * kDiagBlock;
+        for (int64_t bx = 0; bx < nbx && bx * kSeg < ix.M - dlo; ++bx)
+          items.push_back(SweepItem{uint32_t(q), uint32_t(bx), uint32_t(by)});
+      }
+    }
+    if (items.empty() || e != cudaSuccess) continue;
+    SweepItem* ditems = nullptr;
+    int* dnext = nullptr;
+    if ((e = cudaMallocAsync(&ditems, items.size() * sizeof(SweepItem), s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&dnext, sizeof(int), s)) != cudaSuccess) {
+      cudaFreeAsync(ditems, s);
+      break;
+    }
+    e = cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dnext, 0, sizeof(int), s);
+    const int per_sm = dp <= 8 ? 3 : 2;
+    const int64_t grid = std::min<int64_t>(int64_t(sm_count()) * per_sm, int64_t(items.size()));
+    const int nit = int(items.size());
+    if (e == cudaSuccess) {
+      if (dp == 4) {
+        const size_t smem = rows3_smem(4, kRowSub3);
+        e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows3_batch<4, kRowSub3, 3>), smem);
+        if (e == cudaSuccess)
+          MOMENTI_LAUNCH("allpairs_batch", s, k_allpairs_rows3_batch<4, kRowSub3, 3><<<unsigned(grid), kDiagBlock, smem, s>>>(djobs, ditems, nit, dnext));
+      } else if (dp == 8) {
+        const size_t smem = rows3_smem(8, kRowSub3);
+        e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows3_batch<8, kRowSub3, 3>), smem);
+        if (e == cudaSuccess)
+          MOMENTI_LAUNCH("allpairs_batch", s, k_allpairs_rows3_batch<8, kRowSub3, 3><<<unsigned(grid), kDiagBlock, smem, s>>>(djobs, ditems, nit, dnext));
+      } else {
+        const size_t smem = rows3_smem(16, kRowSub3 / 2);
+        e = allow_smem(reinterpret_cast<const void*>(k_allpairs_rows3_batch<16, kRowSub3 / 2, 2>), smem);
+        if (e == cudaSuccess)
+          MOMENTI_LAUNCH("allpairs_batch", s, k_allpairs_rows3_batch<16, kRowSub3 / 2, 2><<<unsigned(grid), kDiagBlock, smem, s>>>(djobs, ditems, nit, dnext));
+      }
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    cudaFreeAsync(ditems, s);
+    cudaFreeAsync(dnext, s);
+  }
+  cudaFreeAsync(djobs, s);
+  return e;
+}
 
 bool rows2_usable(const Index& ix) {
   return ix.xW && !ix.has_lo && (ix.DW == 32 || ix.DW == 64) &&
@@ -1287,6 +2124,10 @@ cudaError_t allpairs_dispatch(const Index& ix, int d, float thr, const ApRec& rc
                               cudaStream_t s) {
   const int64_t ndiag = ix.M - (ix.excl + 1);
   if (ndiag <= 0) return cudaSuccess;
+  if constexpr (!ROWMIN) {
+    if (sweep_variants(ix) > 0)
+      return sweep_launch(ix, sweep_variant(ix, d, rc, s), d, thr, rc, s, int64_t(1) << 40);
+  }
   if (rows2_usable(ix))
     return ix.DW == 32 ? rows2_dispatch<32, ROWMIN>(ix, d, thr, rc, rowmin, s)
                        : rows2_dispatch<64, ROWMIN>(ix, d, thr, rc, rowmin, s);

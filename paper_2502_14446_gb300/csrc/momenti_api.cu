@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <thread>
 #include <cmath>
 #include <cstdio>
@@ -217,6 +218,104 @@ struct SearchState {
 
 }  // namespace
 
+// The batching form's sweep service.  The workers of momenti_topk_batch
+// hand it the recording sweeps of their exact paths (batchable indexes:
+// float32, D <= 16).  Once every worker still running is waiting here, or
+// the oldest request has waited 2 ms, the pending sweeps run together in
+// one persistent launch on the service's stream, ordered after what each
+// requester queued on its own stream and before its next work there.
+class SweepBatcher {
+ public:
+  explicit SweepBatcher(int workers) : active_(workers) {}
+  ~SweepBatcher() {
+    if (stream_) cudaStreamDestroy(stream_);
+  }
+  SweepBatcher(const SweepBatcher&) = delete;
+  SweepBatcher& operator=(const SweepBatcher&) = delete;
+
+  cudaError_t sweep(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s) {
+    Req r;
+    r.job.ix = ix;
+    r.job.rc = rc;
+    r.job.thr = thr;
+    r.job.d = d;
+    r.s = s;
+    std::unique_lock<std::mutex> lk(mu_);
+    pending_.push_back(&r);
+    const auto t0 = std::chrono::steady_clock::now();
+    cv_.notify_all();
+    while (!r.done) {
+      const bool all_waiting = int(pending_.size()) >= active_;
+      const bool waited = std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2);
+      if (!flushing_ && !pending_.empty() && (all_waiting || waited)) {
+        flush(lk);
+        continue;
+      }
+      cv_.wait_for(lk, std::chrono::microseconds(500));
+    }
+    return r.err;
+  }
+
+  // A worker has no more series.
+  void worker_done() {
+    std::lock_guard<std::mutex> lk(mu_);
+    --active_;
+    cv_.notify_all();
+  }
+
+  uint64_t launches() const { return launches_; }
+
+ private:
+  struct Req {
+    SweepJob job;
+    cudaStream_t s = nullptr;
+    bool done = false;
+    cudaError_t err = cudaSuccess;
+  };
+
+  void flush(std::unique_lock<std::mutex>& lk) {
+    std::vector<Req*> batch;
+    batch.swap(pending_);
+    flushing_ = true;
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
+    if (!stream_) e = cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    std::vector<SweepJob> jobs;
+    for (Req* q : batch) {
+      if (e != cudaSuccess) break;
+      // the batch waits for the requester's queued work (counters, buffers)
+      e = cudaEventRecord(ev, q->s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_, ev, 0);
+      jobs.push_back(q->job);
+    }
+    if (e == cudaSuccess) e = launch_allpairs_batch(jobs, stream_);
+    // each requester's next work follows the launch
+    if (e == cudaSuccess) e = cudaEventRecord(ev, stream_);
+    for (Req* q : batch)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(q->s, ev, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    if (ev) cudaEventDestroy(ev);
+    lk.lock();
+    ++launches_;
+    for (Req* q : batch) {
+      q->err = e;
+      q->done = true;
+    }
+    flushing_ = false;
+    cv_.notify_all();
+  }
+
+  std::mutex mu_;
+  std::condition_variable cv_;
+  int active_;
+  bool flushing_ = false;
+  std::vector<Req*> pending_;
+  cudaStream_t stream_ = nullptr;
+  uint64_t launches_ = 0;
+};
+
 struct momenti_handle {
   momenti_params p{};
   std::string err;
@@ -255,6 +354,7 @@ struct momenti_handle {
   momenti_params built_p{};                 // parameters the index was built with
   size_t rec_host_cap = 0;                  // pinned record buffer (kept across rebuilds)
   std::unique_ptr<SearchState> search;      // the traversal in progress, if any
+  SweepBatcher* batcher = nullptr;          // the batching form's sweep service, if any
 };
 
 namespace {
@@ -509,17 +609,18 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
                double* max_err) {
   Index& ix = h->ix;
   const int k = h->p.k;
-  // First threshold.  TOP's k-th (tau0) when it is informative; a TOP that
-  // holds only background pairs (its k-th above a quarter of the largest
-  // possible dist_d, 2 d sqrt(w)) would let most pairs through the sweep's
-  // filters, so then, and on large series instead of a row-minima sweep
-  // (which evaluates every pair in full), the slices start at 5% of the
-  // largest dist_d and double.  Any start gives the same exact result.
+  // First threshold: TOP's k-th (tau0), else 1.2 x the 2k-th smallest row
+  // minimum of spaced windows.  On a large series (M^2 D > 4e11) a loose
+  // threshold costs a sweep in which most pairs pass the filters, and the
+  // row-minima sweep evaluates every pair in full: there, when TOP holds
+  // only background pairs (its k-th above a quarter of the largest possible
+  // dist_d, 2 d sqrt(w)) or is not full, the slices start at 5% of that
+  // largest value and double.  Any start gives the same exact result.
   const double dmax_all = 2.0 * double(d) * std::sqrt(double(ix.w));
   const double tau_low = 0.05 * dmax_all;
+  const bool large = double(ix.M) * double(ix.M) * double(ix.D) > 4e11;
   double tau = tau0;
-  if (tau > 0.25 * dmax_all) tau = std::min(tau, tau_low);
-  if (!(tau > 0) && double(ix.M) * double(ix.M) * double(ix.D) > 4e11) tau = tau_low;
+  if (large && (!(tau > 0) || tau > 0.25 * dmax_all)) tau = tau > 0 ? std::min(tau, tau_low) : tau_low;
   if (!(tau > 0)) {
     float* rowmin = nullptr;
     CK(pool_malloc(&rowmin, ix.M * 4, h->stream));
@@ -648,7 +749,10 @@ int exact_path(momenti_handle* h, int d, double tau0, momenti_motif* out, int32_
     ar.lo = lo;
     ar.hscale = float(kApBins) / (hi - lo);
     const auto tp0 = std::chrono::steady_clock::now();
-    CK(launch_allpairs(ix, d, hi, ar, h->stream));
+    if (h->batcher && sweep_batchable(ix))
+      CK(h->batcher->sweep(ix, d, hi, ar, h->stream));
+    else
+      CK(launch_allpairs(ix, d, hi, ar, h->stream));
     unsigned long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, dcnt, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(hist.data(), dhist, kApBins * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -823,8 +927,8 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     const uint64_t fixed = uint64_t(D) * n * (dtype == MOMENTI_F64 ? 8 : 4)  // series hi/lo
                            + uint64_t(D) * n * elem                          // transient staging
                            + uint64_t(D) * M * (8 + 8 + 4 + 4 + 4)           // stats
-                           + (D <= 16 ? uint64_t(16) * (3 * n + 3 * M) * 4 : 0)  // point-major copies
-                           + (D > 16 ? uint64_t(64) * n * 4 : 0)             // point-major wide copy
+                           + (D <= 16 ? uint64_t(16) * (3 * n + 4 * M) * 4 + M : 0)  // point-major copies
+                           + (D > 16 ? uint64_t(64) * (n + M) * 4 + M : 0)   // point-major wide copy, column table
                            + (D <= 16 && p.d >= 2 ? job_cap_for(M, D) * sizeof(BucketJob) : 0)
                            + (uint64_t(64) << 20);                           // small scratch
     const uint64_t per_rep = uint64_t(M) * D * (8 + 4 + 1)                   // keys, order, lcp
@@ -892,11 +996,17 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
     if (D > 16 && dtype == MOMENTI_F32) {       // the row-staged sweep of wide series
       ix.DW = D <= 32 ? 32 : 64;
       CK(dalloc(h, &ix.xW, size_t(ix.DW) * n));
+      CK(dalloc(h, &ix.isW, size_t(ix.DW) * M));
+      CK(dalloc(h, &ix.cflag, size_t(M)));
     }
     if (D <= 16) {
       ix.Dp = D <= 4 ? 4 : (D <= 8 ? 8 : 16);
       CK(dalloc(h, &ix.xT, size_t(ix.Dp) * n));
       CK(dalloc(h, &ix.stT, size_t(3) * ix.Dp * M));
+      if (!ix.has_lo) {
+        CK(dalloc(h, &ix.isT, size_t(ix.Dp) * M));
+        CK(dalloc(h, &ix.cflag, size_t(M)));
+      }
       if (ix.has_lo) CK(dalloc(h, &ix.xlT, size_t(ix.Dp) * n));
       if (w >= 32) {
         CK(dalloc(h, &ix.smT, size_t(ix.Dp) * n));
@@ -1001,6 +1111,7 @@ static int hash_all_impl(momenti_handle* h, const void* series, int32_t dtype, i
   if (staging) CK(cudaFreeAsync(staging, s));
   CK(launch_window_stats(ix, s));
   CK(launch_stats_point_major(ix, s));
+  CK(launch_col_prep(ix, s));
 
   // ---- hash functions ----
   int L_src = hx.L;
@@ -1538,10 +1649,20 @@ static int topk_batch_impl(int32_t B, const momenti_params* params, const void* 
   std::vector<int> status(size_t(B), MOMENTI_ERR_CUDA);
   std::vector<std::string> messages(static_cast<size_t>(B));
   std::atomic<int32_t> next{0};
+  // several workers: their exact-path sweeps share persistent launches
+  std::unique_ptr<SweepBatcher> batcher;
+  if (T > 1) batcher.reset(new (std::nothrow) SweepBatcher(T));
   auto worker = [&]() {
     cudaSetDevice(dev);
+    struct Done {                   // leaves the batcher on every exit
+      SweepBatcher* b;
+      ~Done() {
+        if (b) b->worker_done();
+      }
+    } done{batcher.get()};
     momenti_handle* h = new (std::nothrow) momenti_handle();
     if (!h) return;
+    h->batcher = batcher.get();
     bool stream_ok = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) == cudaSuccess;
     for (;;) {
       const int32_t q = next.fetch_add(1);
@@ -1577,7 +1698,11 @@ static int topk_batch_impl(int32_t B, const momenti_params* params, const void* 
     try {
       pool.emplace_back(worker);
     } catch (...) {
-      break;                        // fewer workers: the others take the rest
+      // fewer workers: the others take the rest (and the batcher stops
+      // waiting for the ones that never started)
+      for (int u = t; u < T; ++u)
+        if (batcher) batcher->worker_done();
+      break;
     }
   }
   worker();

@@ -40,7 +40,7 @@ def test_roofline_arithmetic():
     r = bench.roofline("allpairs", ms, steps, info, st, _Wl, steps, pk)
     excl = _Wl.w // 2
     pairs = (info["M"] - excl - 1) * (info["M"] - excl) / 2.0
-    work = 18.0 * info["D"] * pairs
+    work = 8.0 * info["D"] * pairs          # the minimal flop count per pair and dim
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(work * steps / (ms / 1e3) / 1e12)
     assert r["peak"] == pytest.approx(152 * 128 * 2 * 2070.0 * 1e6 / 1e12)

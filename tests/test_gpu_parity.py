@@ -255,6 +255,54 @@ def test_topk_exact_matches_oracle(mom, seed, n, D, w, d, k):
     assert_same_motifs(got, ref)
 
 
+@pytest.mark.parametrize("seed,n,D,w,d,k", [(21, 5000, 3, 64, 2, 3), (22, 4500, 8, 50, 3, 3),
+                                           (23, 4200, 12, 40, 4, 2), (24, 3000, 20, 48, 5, 2),
+                                           (25, 2600, 40, 32, 10, 2)])
+def test_topk_exact_float32_matches_oracle(mom, seed, n, D, w, d, k):
+    # float32 input takes the statistics sweeps: one lane per diagonal for
+    # D <= 16 (padded to 4, 8, 16 dims), 16 dims per lane beyond (32, 64);
+    # several row blocks of 2048 windows, diagonal blocks of 256 and a
+    # ragged tail of both
+    wl = synth.tiny(seed, n=n, D=D, w=w, d=d, k=k, n_motifs=2, dtype=np.float32)
+    h, _, _ = make(mom, wl, L=2)
+    got = h.topk_exact()
+    ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+    assert_same_motifs(got, ref)
+
+
+@pytest.mark.parametrize("D,variant", [(3, 0), (3, 1), (3, 2), (8, 1), (8, 2), (12, 0), (12, 1),
+                                       (12, 2), (20, 1), (40, 1)])
+def test_sweep_variants_record_the_same_pairs(mom, D, variant, monkeypatch):
+    # every form of the recording sweep the autotuner chooses from (the
+    # statistics form with two stage heights, the slid form; for wide
+    # series the statistics and slid wide forms) gives the exact top-k
+    monkeypatch.setenv("MOMENTI_SWEEP_VARIANT", str(variant))
+    wl = synth.tiny(30 + D, n=3500, D=D, w=48, d=max(1, D // 4), k=3, n_motifs=2, dtype=np.float32)
+    h, _, _ = make(mom, wl, L=2)
+    got = h.topk_exact()
+    ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+    assert_same_motifs(got, ref)
+
+
+@pytest.mark.parametrize("D", [6, 24])
+def test_topk_exact_float32_flat_windows(mom, D):
+    # constant runs longer than a window: flat windows are the zero vector,
+    # distance 0 to each other and sqrt(w) to any other window (so flat
+    # pairs lead the top-k), and a run's level offset makes the neighbouring
+    # windows' centring offsets large against their sigma; both take the
+    # sweep's exact branch
+    wl = synth.tiny(27, n=4000, D=D, w=40, d=2, k=4, n_motifs=1, dtype=np.float32)
+    T = wl.series.copy()
+    T[1, 1000:1150] = T[1, 1000]
+    T[4, 2500:2600] = 7.5 + T[4, 2500]
+    T[4, 3100:3180] = T[4, 3100]
+    wl = synth.Workload(wl.name, np.ascontiguousarray(T), wl.w, wl.d, wl.k, wl.delta)
+    h, _, _ = make(mom, wl, L=2)
+    got = h.topk_exact()
+    ref = O.exact_topk(wl.series, wl.w, wl.d, wl.k)
+    assert_same_motifs(got, ref)
+
+
 @pytest.mark.parametrize("seed", [1, 2, 4])
 def test_topk_follows_algorithm_1(mom, seed):
     wl = synth.tiny(seed, 1500, 3, 50, 2, k=2, n_motifs=2)
