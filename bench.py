@@ -83,6 +83,9 @@ def parse():
                     help="plain_fp32: D=8 n=1e5 w=300 (the default line); precision_form: "
                          "D=32 n=1e6 w=500 d=8 (minutes per step)")
     ap.add_argument("--r", type=float, default=0.0, help="quantisation width (0: Section 6.1 heuristic)")
+    ap.add_argument("--large-form", type=float, default=0.0, metavar="SECONDS",
+                    help="also run the large memory-bounded form at full size (D=64, n=1e7, "
+                         "64 GB limit): hashing, then the anytime search for this many seconds")
     ap.add_argument("--no-rsweep", action="store_true",
                     help="skip the parameter legs (r, K, L, delta sweeps, tensoring, scalability)")
     return ap.parse_args()
@@ -382,6 +385,7 @@ def run_momenti(args):
             sweeps = param_sweep_leg(mom, wl, series, stream, flush, prec)
             scal = scalability_leg(mom, dev, stream, flush, prec)
         batch = batch_leg(mom, args.batch_series, dev) if args.batch_series > 0 else None
+        large = large_form_leg(mom, dev, stream, prec, args.large_form) if args.large_form > 0 else None
         base = None if args.no_baseline else cpu_baseline(wl)
         # float64 error of each result: the float32 traversal distance
         # against the float64 re-verification (stats), and the float64
@@ -414,6 +418,7 @@ def run_momenti(args):
             "scalability": scal,
             "tensoring": tens,
             "batch_form": batch,
+            "large_form": large,
             "e2e": {"value": world * units_step / e2e_s, "unit": "subsequences/s",
                     "time_to_topk_s": e2e_s, "h2d_bytes_per_step": h_bytes,
                     "d2h_bytes_per_step": d_bytes},
@@ -518,6 +523,54 @@ def param_sweep_leg(mom, wl, series, stream, flush, prec):
                          "L_used": st["L"],
                          "matches_exact": None if gold is None else [(x["a"], x["b"]) for x in m] == gold})
         out[name] = rows
+    return out
+
+
+def large_form_leg(mom, dev, stream, prec, budget_s: float):
+    """The large memory-bounded form at full size (synth.large_form: D=64,
+    n=1e7, w=1000, d=16, k=10, delta=0.01, float32, 64 GB device-memory
+    limit).  The memory planner picks L; hash_all is timed with CUDA events
+    (second of two builds, series resident in HBM); then the anytime search
+    (Section 4) advances one repetition at a time for budget_s seconds and
+    reports where it stands: the cursor (i, j), how many candidates it
+    holds and the smallest miss bound among them.  The exact fallback of
+    this form (about 3e15 pair-dimension evaluations) is not run."""
+    import torch
+    from paper_2502_14446_gb300 import synth
+    wl = synth.large_form(0)
+    x = torch.from_numpy(wl.series).to(dev)
+    desc = (f"large_form: D={wl.D} n={wl.n} w={wl.w} d={wl.d} k={wl.k} delta={wl.delta} float32, "
+            f"{wl.mem_limit >> 30} GB limit, K=8, L planned")
+    p = mom.default_params(w=wl.w, d=wl.d, k=wl.k, delta=wl.delta, precision=prec,
+                           mem_limit=wl.mem_limit)
+    h = mom.Momenti(p)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.hash_all(x, stream=stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+    hash_ms = e0.elapsed_time(e1)
+    info = h.info()
+    h.search_begin()
+    t0 = time.perf_counter()
+    steps, ended = 0, False
+    while not ended and time.perf_counter() - t0 < budget_s:
+        ended = h.search_step(1)
+        steps += 1
+    cur, (i, j, ended) = h.search_current()
+    top = cur[wl.d]
+    planted = {(a, b) for a, b, _ in wl.planted}
+    out = {"workload": desc, "L_planned": info["L"], "K": info["K"], "r": info["r"],
+           "windows": info["M"], "hash_all_ms": hash_ms,
+           "hashed_per_s": info["M"] * 64 * info["L"] / (hash_ms / 1e3),
+           "search_s": time.perf_counter() - t0, "repetitions_processed": steps,
+           "cursor": [i, j, bool(ended)], "candidates": len(top),
+           "planted_among_candidates": sum((m["a"], m["b"]) in planted for m in top),
+           "smallest_miss_bound": min((m["fail_bound"] for m in top), default=None)}
+    h.close()
+    del x
     return out
 
 

@@ -212,6 +212,7 @@ struct SearchState {
   int i = 0, j0 = 0, d_cur = 0;
   int last_i = 0, last_j = 0;     // the last repetition processed (1-based j), 0 0 before any
   int switch_level = 0;
+  double prev_rep_ms = 0.0;       // predicted cost of one repetition at the previous level's probe
   bool ended = false;             // STOP for every d, the cost switch, or the loop's end
   momenti_stats st{};
 };
@@ -488,9 +489,9 @@ double predict_rep_ms(const Index& ix, uint64_t tiles, uint64_t sub_checks, uint
 double predict_exact_ms(const Index& ix, int passes) {
   double ps_pair;                                  // all-pairs kernel, per pair
   if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 5.0;
-  else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 11.0;
+  else if (ix.xT && !ix.has_lo && ix.Dp == 8) ps_pair = 7.5;
   else if (ix.xT && !ix.has_lo && ix.Dp == 16) ps_pair = 40.0;
-  else if (ix.xW && rows2_usable(ix)) ps_pair = 1.6 * double(ix.DW);
+  else if (ix.xW && rows2_usable(ix)) ps_pair = 1.5 * double(ix.DW);
   else if (ix.D <= 32) ps_pair = 8.0 * double(ix.D);
   else ps_pair = 31.0 * double(ix.D);
   const double pairs = 0.5 * double(ix.M) * double(ix.M);
@@ -1460,13 +1461,22 @@ static int search_step_impl(momenti_handle* h, int64_t max_reps, int32_t* ended)
       x.pool.tau_trunc = std::min(x.pool.tau_trunc, double(x.tau));
     }
     if (probe && !S.ended) {
-      // the rest of this level, and the lower levels (shorter prefixes
-      // collide more: each costs at least as much as this one), against
-      // the exact path of every open d
+      // the rest of this level, and the lower levels, against the exact
+      // path of every open d.  Shorter prefixes collide more, so each lower
+      // level costs at least as much as this one; it is taken to grow by
+      // the factor g this level's probe grew by over the previous level's,
+      // kept within [1, 4]
       const uint64_t verified = n_events - std::min<uint64_t>(n_events, cnt[3]);
       const double rep = predict_rep_ms(ix, used_sub ? 0 : tiles, used_sub ? tiles : 0, n_events,
                                         verified, nrec);
-      const double rest = double(L - 1) * rep + double(i - 1) * double(L) * rep;
+      const double g = S.prev_rep_ms > 0.0 ? std::min(4.0, std::max(1.0, rep / S.prev_rep_ms)) : 1.0;
+      S.prev_rep_ms = rep;
+      double lower = 0.0, gl = 1.0;
+      for (int l = i - 1; l >= 1; --l) {
+        gl *= g;
+        lower += gl;
+      }
+      const double rest = double(L - 1) * rep + lower * double(L) * rep;
       double exact = 0.0;
       for (auto& x : ds)
         if (!x.done) exact += predict_exact_ms(ix, int(x.pool.top.size()) == k ? 1 : 2);
