@@ -63,6 +63,8 @@ DOMINANT = ("proj_hash_tc", "collide", "subbucket", "sort_*", "allpairs", "proj_
             "verify_events")
 # kernels whose roofline is reported beside the dominant one
 SECONDARY = ("sort_*", "proj_hash_tc", "allpairs")
+# the kernels of collision counting (step a7), reported together as "collision"
+COLLISION = ("collide", "bucket_jobs", "subbucket", "subwarp")
 
 
 def parse():
@@ -197,6 +199,17 @@ def sm_count(device=None) -> int:
     return torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count
 
 
+def reps_processed(st, K, L):
+    """(level, repetition) cells the traversal processed in one search:
+    levels K down to the stopping level, where STOP held at (i, j) or the
+    cost switch ended the search after its one-repetition probe."""
+    if st["stop_i"] > 0:
+        return (K - st["stop_i"]) * L + st["stop_j"]
+    if st["switch_level"] > 0:
+        return (K - st["switch_level"]) * L + 1
+    return K * L
+
+
 def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
     """Roofline object of one kernel from its live CUDA-event time over the
     timed steps: achieved = algorithmic work of the timed launches / their
@@ -214,6 +227,11 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
       sort_*          20 bytes per index entry (window, dim, repetition):
                       its 8-byte key read, the sorted 12-byte (key, window)
                       written; every kernel of the index sort together
+      collision       12 bytes per index entry per (level, repetition)
+                      processed (8-byte key, 4-byte window of the sorted
+                      order) and 16 D bytes per compared bucket pair (the
+                      keys of both windows in every dim); the kernels of
+                      COLLISION together
     """
     if not k_n or k_ms <= 0:
         return None
@@ -239,6 +257,11 @@ def roofline(kernel, k_ms, k_n, info, st, wl, steps, pk, sms=152):
         bound, unit = "alu", "TFLOP/s"
         achieved = work / secs / 1e12
         peak, src = sm_peak, sm_src
+    elif kernel == "collision":
+        work = (12.0 * M * D * reps_processed(st, K, L) + 16.0 * D * st["n_pair_checks"]) * steps
+        bound, unit = "hbm", "GB/s"
+        achieved = work / secs / 1e9
+        peak, src = pk["hbm_gbs"], pk["src"] + " copy bandwidth"
     elif kernel == "sort_*":
         work = 20.0 * M * D * L * steps
         bound, unit = "hbm", "GB/s"
@@ -292,7 +315,8 @@ def run_momenti(args):
     # device time of each candidate kernel over one step: the dominant one is
     # timed live in the timed steps; the others' rooflines come from this step
     per_kernel = {}
-    candidates = DOMINANT + SECONDARY if args.kernel == "auto" else SECONDARY + (args.kernel,)
+    candidates = (DOMINANT + SECONDARY + COLLISION if args.kernel == "auto"
+                  else SECONDARY + (args.kernel,))
     for kname in dict.fromkeys(candidates):
         mom.time_kernel(kname)
         _, st_k = step()
@@ -358,6 +382,14 @@ def run_momenti(args):
             if r2 is not None:
                 r2["timed"] = "one untimed step before the timed region"
                 others[kname] = r2
+        if all(k in per_kernel for k in COLLISION):
+            ms = sum(per_kernel[k][0] for k in COLLISION)
+            n = sum(per_kernel[k][1] for k in COLLISION)
+            r2 = roofline("collision", ms, n, info, per_kernel["collide"][2], wl, 1, pk, sms)
+            if r2 is not None:
+                r2["timed"] = "one untimed step per kernel before the timed region"
+                r2["kernels"] = list(COLLISION)
+                others["collision"] = r2
         plain = None
         if not args.no_fp32 and prec != mom.PREC_FP32:
             h32 = mom.Momenti(params_for(mom, wl, mom.PREC_FP32, args.r))

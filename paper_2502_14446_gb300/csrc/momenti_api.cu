@@ -486,6 +486,17 @@ double predict_rep_ms(const Index& ix, uint64_t tiles, uint64_t sub_checks, uint
                  verify_ns * double(verified) + 100.0 * double(records));
 }
 
+// Recording sweeps the exact path is predicted to cost: one from a full
+// TOP's k-th; without it, on a large series the slices start low and
+// double (about two), otherwise the row-minima sweep, which computes every
+// pair's distances in full (measured at about three recording sweeps at
+// D = 8), comes first.
+int exact_sweeps(const Index& ix, bool top_full) {
+  if (top_full) return 1;
+  const bool large = double(ix.M) * double(ix.M) * double(ix.D) > 4e11;
+  return large ? 2 : 4;
+}
+
 double predict_exact_ms(const Index& ix, int passes) {
   double ps_pair;                                  // all-pairs kernel, per pair
   if (ix.xT && !ix.has_lo && ix.Dp == 4) ps_pair = 5.0;
@@ -1479,7 +1490,7 @@ static int search_step_impl(momenti_handle* h, int64_t max_reps, int32_t* ended)
       const double rest = double(L - 1) * rep + lower * double(L) * rep;
       double exact = 0.0;
       for (auto& x : ds)
-        if (!x.done) exact += predict_exact_ms(ix, int(x.pool.top.size()) == k ? 1 : 2);
+        if (!x.done) exact += predict_exact_ms(ix, exact_sweeps(ix, int(x.pool.top.size()) == k));
       if (rest > exact) {
         S.switch_level = i;
         S.ended = true;

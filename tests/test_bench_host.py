@@ -83,3 +83,20 @@ def test_clock_sampler_end_to_end(tmp_path, monkeypatch):
     time.sleep(1.0)
     out = c.stop()
     assert out == {"sm_mhz": 2065.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 2}
+
+
+def test_collision_roofline_arithmetic():
+    # 12 B per index entry per (level, repetition) processed plus 16 D B per
+    # compared bucket pair, over the summed time of the collision kernels
+    pk = {"hbm_gbs": 6779.0, "tflops": 1933.3, "tflops_sustained": 1727.1,
+          "sm_max_mhz": 2070.0, "src": "measured"}
+    info = {"M": 99701, "D": 8, "L": 200, "K": 8}
+    assert bench.reps_processed({"stop_i": 0, "stop_j": 0, "switch_level": 1}, 8, 200) == 7 * 200 + 1
+    assert bench.reps_processed({"stop_i": 3, "stop_j": 17, "switch_level": 0}, 8, 200) == 5 * 200 + 17
+    assert bench.reps_processed({"stop_i": 0, "stop_j": 0, "switch_level": 0}, 8, 200) == 8 * 200
+    st = {"stop_i": 0, "stop_j": 0, "switch_level": 1, "n_pair_checks": 10 ** 9}
+    r = bench.roofline("collision", 20.0, 300, info, st, _Wl, 1, pk)
+    work = 12.0 * 99701 * 8 * 1401 + 16.0 * 8 * 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(work / 0.020 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6779.0)
