@@ -389,6 +389,10 @@ def run_momenti(args):
             if r2 is not None:
                 r2["timed"] = "one untimed step per kernel before the timed region"
                 r2["kernels"] = list(COLLISION)
+                r2["note"] = ("the unit counts a 16 D-byte key gather per compared bucket pair; "
+                              "the kernels load each window's keys once per 32-window tile or "
+                              "warp and compare them in registers, so achieved can exceed the "
+                              "copy bandwidth")
                 others["collision"] = r2
         plain = None
         if not args.no_fp32 and prec != mom.PREC_FP32:
