@@ -280,23 +280,30 @@ class SweepBatcher {
     flushing_ = true;
     lk.unlock();
     cudaError_t e = cudaSuccess;
-    if (!stream_) e = cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
     cudaEvent_t ev = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    std::vector<SweepJob> jobs;
-    for (Req* q : batch) {
-      if (e != cudaSuccess) break;
-      // the batch waits for the requester's queued work (counters, buffers)
-      e = cudaEventRecord(ev, q->s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_, ev, 0);
-      jobs.push_back(q->job);
+    // every request of the batch is answered, whatever happens here (a
+    // host allocation that fails reports an error to each requester)
+    try {
+      if (!stream_) e = cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      std::vector<SweepJob> jobs;
+      for (Req* q : batch) {
+        if (e != cudaSuccess) break;
+        // the batch waits for the requester's queued work (counters, buffers)
+        e = cudaEventRecord(ev, q->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_, ev, 0);
+        jobs.push_back(q->job);
+      }
+      if (e == cudaSuccess) e = launch_allpairs_batch(jobs, stream_);
+      // each requester's next work follows the launch
+      if (e == cudaSuccess) e = cudaEventRecord(ev, stream_);
+      for (Req* q : batch)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q->s, ev, 0);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    } catch (...) {
+      if (stream_) cudaStreamSynchronize(stream_);
+      e = cudaErrorMemoryAllocation;
     }
-    if (e == cudaSuccess) e = launch_allpairs_batch(jobs, stream_);
-    // each requester's next work follows the launch
-    if (e == cudaSuccess) e = cudaEventRecord(ev, stream_);
-    for (Req* q : batch)
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(q->s, ev, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
     if (ev) cudaEventDestroy(ev);
     lk.lock();
     ++launches_;
