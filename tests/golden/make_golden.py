@@ -8,6 +8,7 @@ Definition (top-k multidimensional motifs, Section 3.1) as
 
 Usage: python tests/golden/make_golden.py plain_small plain_fp32 batch_small guarantee
        python tests/golden/make_golden.py precision_form large_form   (n = 2e5 prefixes)
+       python tests/golden/make_golden.py stop   (Algorithm 1 stopped by STOP, full bench workload)
 
 batch_small is the batching form at reduced lengths (6 series, n
 log-uniform in [1500, 5000]); its file holds one record per series.
@@ -108,6 +109,41 @@ def make_prefix(name: str, seed: int = 0):
     print(path, f"{dt:.1f}s")
 
 
+# Algorithm 1 stopped by Algorithm 2 on the full bench workload: the
+# plain float32 form (D=8, n=1e5, w=300, d=3, delta=0.05) asked for its
+# k = 5 closest motifs, with the fixed width r = 8 of the paper's r
+# experiment and the seed-0 hash draws (K=8, L=200) that the GPU test sets
+# through set_hash_params; the oracle's hashing and traversal in the
+# paper's loop order, no exact fallback
+STOP = {"k": 5, "r": 8.0, "L": 200, "K": 8}
+
+
+def make_stop(seed: int = 0):
+    wl = synth.plain_fp32(seed)
+    T = wl.series.astype("float64")
+    A, U = synth.hash_draws(wl.D, STOP["L"], STOP["K"], wl.w, seed)
+    t0 = time.time()
+    keys, _ = O.hash_all(T, wl.w, A, U, STOP["r"])
+    Z = [O.znorm_windows(T[f], wl.w) for f in range(wl.D)]
+    top, stop, n_dist, _ = O.momenti_traverse(keys, lambda a, b: O._pair_distances(Z, a, b),
+                                              wl.d, STOP["k"], wl.delta, STOP["r"],
+                                              O.exclusion_zone(wl.w), STOP["K"])
+    dt = time.time() - t0
+    rec = {
+        "workload": "plain_fp32", "seed": seed, "D": wl.D, "n": wl.n, "w": wl.w, "d": wl.d,
+        "delta": wl.delta, **STOP, "hash_seed": seed,
+        "stop": list(stop) if stop else None, "n_dist": n_dist,
+        "fail_bound": (O.failure_bound(top[-1][4], stop[0], stop[1], STOP["K"], STOP["L"], wl.d,
+                                       STOP["r"]) if stop else None),
+        "motifs": [[m[0], m[1], m[2], list(m[3]), m[4]] for m in top],
+        "oracle": "hash_all + momenti_traverse", "oracle_seconds": dt,
+    }
+    path = os.path.join(OUT, f"stop_plain_fp32_k{STOP['k']}_r{int(STOP['r'])}_seed{seed}.json")
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(path, f"{dt:.1f}s")
+
+
 if __name__ == "__main__":
     for nm in sys.argv[1:] or ["plain_small"]:
         if nm == "batch_small":
@@ -116,5 +152,7 @@ if __name__ == "__main__":
             make_guarantee()
         elif nm in PREFIX:
             make_prefix(nm)
+        elif nm == "stop":
+            make_stop()
         else:
             make(nm)
