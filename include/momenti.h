@@ -273,7 +273,15 @@ int momenti_search_finish(momenti_handle* h, momenti_motif* out, int32_t* n_out,
 
 /* The final fallback of Algorithm 1 alone: the exact top-k over all pairs (the quantity
  * of Definition top-k), on the GPU, float64 re-verified.  Same outputs and
- * errors as momenti_topk. */
+ * errors as momenti_topk.
+ *
+ * For a float32 series the all-pairs sweep has several forms that record
+ * the same pairs; the first sweep of an index times them on a part of the
+ * grid and keeps the fastest per (device, padded D, log2 w, log2 M) for the
+ * process.  Environment: MOMENTI_AUTOTUNE=0 takes the default form,
+ * MOMENTI_SWEEP_VARIANT=v (a digit) forces form v, MOMENTI_TRACE=1 prints
+ * the choice, one line per traversal chunk and one per exact-path sweep to
+ * stderr. */
 int momenti_topk_exact(momenti_handle* h, momenti_motif* out, int32_t* n_out);
 
 /* Eq. zned per dimension and Definition distdims for m given pairs
