@@ -292,6 +292,17 @@ cudaError_t launch_allpairs(const Index& ix, int d, float thr, const ApRec& rc, 
 // Whether the row-staged sweep of wide series (16 < D <= 64) takes this index
 // (a point-major copy, and its staged rows fit a CTA's shared memory).
 bool rows2_usable(const Index& ix);
+// ---- k_wide64_*.cu: the 64-dimension sweeps, each instantiated in a
+// translation unit of its own (they dominate the build; units compile in
+// parallel).  gy_max cuts the grid to its first diagonal blocks.
+cudaError_t launch_rows4_64(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                            int64_t gy_max);
+cudaError_t launch_rows2_64(const Index& ix, int d, float thr, const ApRec& rc, cudaStream_t s,
+                            int64_t gy_max);
+cudaError_t launch_rows2_64_rowmin(const Index& ix, int d, float* rowmin, cudaStream_t s);
+cudaError_t launch_wide64(const Index& ix, int d, float thr, const ApRec& rc, float* rowmin,
+                          bool rowmin_mode, cudaStream_t s);
+
 // One series' recording sweep inside a batched launch.
 struct SweepJob {
   Index ix;

@@ -92,7 +92,7 @@ def test_header_names_every_timed_kernel():
     csrc = os.path.join(ROOT, "paper_2502_14446_gb300", "csrc")
     used = set()
     for fn in os.listdir(csrc):
-        if fn.endswith(".cu"):
+        if fn.endswith(".cu") or fn.endswith(".cuh"):
             used |= set(re.findall(r'MOMENTI_LAUNCH\("([a-z0-9_]+)"', open(os.path.join(csrc, fn)).read()))
     text = open(os.path.join(ROOT, "include", "momenti.h")).read()
     block = re.search(r"Kernel names:(.*?)\*/", text, re.S).group(1)
