@@ -41,9 +41,11 @@ the design notes of the repository):
 * r is (max - min) / 256 over projections of evenly spaced sample windows
   onto the K vectors of repetition 0 of every dimension.
 
-Parity status of each function is stated in its docstring; every function
-here is pinned by a test against the paper or the mathematics (closed forms,
-brute force on tiny inputs, Monte Carlo, hand-evaluated tables).
+Every function here is pinned, directly or through the function that uses
+it, by the tests of tests/test_oracle.py (and the stored records by
+tests/test_golden.py) against the paper or the mathematics: closed forms,
+brute force on tiny inputs, Monte Carlo, hand-evaluated tables, and the
+printed example of Section 4.  No function is unpinned.
 """
 from __future__ import annotations
 
